@@ -1,0 +1,173 @@
+"""FP64 CPU oracle of the SIC Vlasov-Poisson step (arXiv:1506.07207).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use this package; the product path never imports,
+links or runs it, and it shares no code with the CUDA path.
+
+The arithmetic lives in ``sic_oracle.c`` (plain double-precision loops, one
+function per definition of the paper); this module compiles it with gcc on
+first use and wraps it with ctypes.  ``theory`` holds the closed-form
+dispersion relations used as pins, ``fits`` the rate fitter.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sic_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libsic_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: no fused multiply-add contraction, so x86 and Arm hosts
+# give the same bits.
+CFLAGS = ["-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``sic_oracle.c`` into ``_build/libsic_oracle.so``; return its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            bp = ctypes.POINTER(ctypes.c_uint8)
+            lib.orc_deposit.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ip, bp, ip, dp, dp, dp]
+            lib.orc_deposit.restype = ctypes.c_int
+            lib.orc_field.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
+            lib.orc_field.restype = None
+            lib.orc_gather.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_long,
+                                       dp, dp]
+            lib.orc_gather.restype = None
+            lib.orc_field_energy.argtypes = [ctypes.c_int, ctypes.c_double, dp]
+            lib.orc_field_energy.restype = ctypes.c_double
+            lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ip, bp, ip, ctypes.c_long, dp, dp, dp,
+                                    ctypes.c_int, dp, dp, dp]
+            lib.orc_run.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _sheets(counts, closed, winding):
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    closed = np.ascontiguousarray(closed, dtype=np.uint8)
+    winding = np.ascontiguousarray(winding, dtype=np.int32)
+    if not (counts.shape == closed.shape == winding.shape):
+        raise ValueError("counts, closed and winding need one entry per sheet")
+    return counts, closed, winding
+
+
+def deposit(nx, L, counts, closed, winding, x, w):
+    """Charge per cell (Eq. overlap and Eq. rho_sum, times dx)."""
+    lib = _load()
+    counts, closed, winding = _sheets(counts, closed, winding)
+    x, w = _f64(x), _f64(w)
+    if x.shape != w.shape or x.size != int(counts.sum()):
+        raise ValueError("x and w need one entry per tracer")
+    out = np.zeros(int(nx), dtype=np.float64)
+    rc = lib.orc_deposit(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
+                         _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
+                         _ptr(x, ctypes.c_double), _ptr(w, ctypes.c_double),
+                         _ptr(out, ctypes.c_double))
+    if rc:
+        raise ValueError("every sheet needs at least two tracers")
+    return out
+
+
+def density(nx, L, counts, closed, winding, x, w):
+    """Cell-averaged number density n_j = charge_j / dx."""
+    return deposit(nx, L, counts, closed, winding, x, w) / (float(L) / int(nx))
+
+
+def field(nx, L, charge):
+    """(rho, E) from the per-cell charge: neutralised density and node field."""
+    lib = _load()
+    charge = _f64(charge)
+    rho = np.zeros(int(nx))
+    E = np.zeros(int(nx))
+    lib.orc_field(int(nx), float(L), _ptr(charge, ctypes.c_double),
+                  _ptr(rho, ctypes.c_double), _ptr(E, ctypes.c_double))
+    return rho, E
+
+
+def gather(nx, L, E, x):
+    """Linear-weighting gather of the node field E at positions x."""
+    lib = _load()
+    E, x = _f64(E), _f64(x)
+    out = np.zeros_like(x)
+    lib.orc_gather(int(nx), float(L), _ptr(E, ctypes.c_double), x.size,
+                   _ptr(x, ctypes.c_double), _ptr(out, ctypes.c_double))
+    return out
+
+
+def field_energy(nx, L, E):
+    """W_E = 1/2 sum_j E_j^2 dx."""
+    return _load().orc_field_energy(int(nx), float(L), _ptr(_f64(E), ctypes.c_double))
+
+
+def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
+        half_step_init=True, record_E=False):
+    """Leapfrog SIC run; returns dict(x, v, E, hist[, E_hist]).
+
+    hist has n_steps+1 rows [W_E, KE, P, Q_total]; KE and P are time-centred
+    on each step (NaN on the last row).
+    """
+    lib = _load()
+    counts, closed, winding = _sheets(counts, closed, winding)
+    x = np.array(x, dtype=np.float64, copy=True)
+    v = np.array(v, dtype=np.float64, copy=True)
+    w = _f64(w)
+    n = x.size
+    hist = np.zeros((n_steps + 1, 4))
+    e_hist = np.zeros((n_steps + 1, int(nx))) if record_E else None
+    E = np.zeros(int(nx))
+    rc = lib.orc_run(int(nx), float(L), float(dt), float(qm), int(bool(half_step_init)),
+                     counts.size, _ptr(counts, ctypes.c_int32), _ptr(closed, ctypes.c_uint8),
+                     _ptr(winding, ctypes.c_int32), n, _ptr(x, ctypes.c_double),
+                     _ptr(v, ctypes.c_double), _ptr(w, ctypes.c_double), int(n_steps),
+                     _ptr(hist, ctypes.c_double), _ptr(e_hist, ctypes.c_double),
+                     _ptr(E, ctypes.c_double))
+    if rc:
+        raise ValueError("every sheet needs at least two tracers")
+    out = dict(x=x, v=v, E=E, hist=hist)
+    if record_E:
+        out["E_hist"] = e_hist
+    return out
+
+
+def run_problem(p, n_steps=None, record_E=False):
+    """``run`` on a problem from ``paper_1506_07207_gb300.inputs``."""
+    return run(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
+               p.n_steps if n_steps is None else n_steps, qm=p.qm,
+               half_step_init=p.half_step_init, record_E=record_E)

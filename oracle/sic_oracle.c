@@ -1,0 +1,263 @@
+/*
+ * sic_oracle.c -- plain FP64 CPU oracle of the simplex-in-cell (SIC) step for
+ * the 1D periodic Vlasov-Poisson system (Kates-Harbeck, Totorica, Zrake & Abel,
+ * arXiv:1506.07207).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call this
+ * file: only the tests, the package's smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or helper with the
+ * CUDA path.  It is deliberately slow and literal: every function is one of the
+ * paper's definitions written out as plain loops in double precision, with no
+ * blocking, fusion, fixed point or reordering.
+ *
+ * Conventions (the paper leaves these open; the readings used are):
+ *   - Units: C = 1 in the Poisson equation of Sec. 2.1, so with E = -dPhi/dx
+ *     the field obeys dE/dx = rho and a tracer accelerates by qm * E
+ *     (qm = charge-to-mass factor, +1 in the paper's sign convention).
+ *   - rho = n - mean(n): the neutralising background is the computed mean
+ *     density (Sec. 2.1, "mean density is set to zero").
+ *   - Mesh: cell j covers [j dx, (j+1) dx), left-closed; rho is a cell
+ *     average (Eq. rho_sum with V~ = dx); E lives on the nodes x_j = j dx and
+ *     is the exact integral of rho from node to node, shifted to zero mean
+ *     (periodic potential).
+ *   - Segment charge q_s = (w_i + w_{i+1}) / 2 (Sec. 2.5 uses the mean of the
+ *     two tracer charges; for equal tracer weights it is the tracer weight).
+ *   - A segment of zero length puts its whole charge in the cell holding its
+ *     point (the footnote of Sec. 2.3 only asks that charge be kept).
+ *   - Closed sheets close with the segment (x_N, x_1 + winding * L): the
+ *     periodic identification x_{N+1} = x_1 of Sec. 2.3 taken on the unwrapped
+ *     line.
+ *   - Time integration (not stated in the paper): leapfrog kick-drift,
+ *     v^{n+1/2} = v^{n-1/2} + dt qm E^n(x^n), x^{n+1} = x^n + dt v^{n+1/2}.
+ *   - Gather: linear weighting between the two nodes around a tracer
+ *     (Sec. 2.3, end: forces gathered "using linear weighting").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Periodic reduction of an (unbounded) cell number into [0, nx). */
+static int wrap_cell(long m, int nx)
+{
+    long r = m % (long)nx;
+    if (r < 0)
+        r += nx;
+    return (int)r;
+}
+
+/*
+ * Charge of one box-function particle spread over the cells it overlaps.
+ *
+ * Sec. 2.3: the particle between tracers at xa and xb is the box function
+ * b(x) = 1/|xa - xb| on (min, max); Eq. overlap gives its overlap with cell j
+ * as the integral of b over the cell, and Eq. rho_sum weights that overlap by
+ * the particle's charge q.  With periodic boundaries every image of a cell
+ * counts, so the loop runs over the unwrapped cells m touched by [a, b] and
+ * folds m into [0, nx).  The clip is taken in physical units; cells one past
+ * each end are visited too so that rounding of a/dx or b/dx cannot lose a cell
+ * (their clipped length is then <= 0 and they are skipped).
+ */
+static void deposit_segment(double xa, double xb, double q, int nx, double dx,
+                            double *charge)
+{
+    double a = xa < xb ? xa : xb;
+    double b = xa < xb ? xb : xa;
+    long ma = (long)floor(a / dx);
+    long mb = (long)floor(b / dx);
+    if (b == a) {
+        charge[wrap_cell(ma, nx)] += q;
+        return;
+    }
+    double len = b - a;
+    for (long m = ma - 1; m <= mb + 1; ++m) {
+        double lo = a > m * dx ? a : m * dx;
+        double hi = b < (m + 1) * dx ? b : (m + 1) * dx;
+        if (hi > lo)
+            charge[wrap_cell(m, nx)] += q * (hi - lo) / len;
+    }
+}
+
+/*
+ * Total charge per cell of all sheets (Eq. rho_sum times the cell volume).
+ *
+ * A sheet is an ordered run of tracers (Sec. 2.2, "Implications of the Sheet
+ * Topology"); every adjacent pair is a particle (Sec. 2.3).  counts[s] tracers
+ * of sheet s follow each other in x[] and w[].  closed[s] != 0 adds the
+ * closing particle (last, first + winding[s] * L).
+ * Returns 0, or -1 for a sheet with fewer than two tracers.
+ */
+int orc_deposit(int nx, double L, int n_sheets, const int32_t *counts,
+                const uint8_t *closed, const int32_t *winding,
+                const double *x, const double *w, double *charge)
+{
+    double dx = L / nx;
+    memset(charge, 0, sizeof(double) * (size_t)nx);
+    long base = 0;
+    for (int s = 0; s < n_sheets; ++s) {
+        long n = counts[s];
+        if (n < 2)
+            return -1;
+        for (long i = 0; i + 1 < n; ++i) {
+            double q = 0.5 * (w[base + i] + w[base + i + 1]);
+            deposit_segment(x[base + i], x[base + i + 1], q, nx, dx, charge);
+        }
+        if (closed[s]) {
+            double q = 0.5 * (w[base + n - 1] + w[base]);
+            double xb = x[base] + (double)winding[s] * L;
+            deposit_segment(x[base + n - 1], xb, q, nx, dx, charge);
+        }
+        base += n;
+    }
+    return 0;
+}
+
+/*
+ * Field solve (Sec. 2.1 with C = 1): n_j = charge_j / dx, rho_j = n_j - mean(n),
+ * dE/dx = rho integrated exactly across each cell: E'_0 = 0,
+ * E'_{j+1} = E'_j + dx rho_j; E_j = E'_j - mean(E').  rho and E may be NULL.
+ */
+void orc_field(int nx, double L, const double *charge, double *rho, double *E)
+{
+    double dx = L / nx;
+    double *n = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *r = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *e = (double *)malloc(sizeof(double) * (size_t)nx);
+    double nbar = 0.0;
+    for (int j = 0; j < nx; ++j) {
+        n[j] = charge[j] / dx;
+        nbar += n[j];
+    }
+    nbar /= nx;
+    for (int j = 0; j < nx; ++j)
+        r[j] = n[j] - nbar;
+    e[0] = 0.0;
+    for (int j = 0; j + 1 < nx; ++j)
+        e[j + 1] = e[j] + dx * r[j];
+    double emean = 0.0;
+    for (int j = 0; j < nx; ++j)
+        emean += e[j];
+    emean /= nx;
+    for (int j = 0; j < nx; ++j) {
+        if (rho)
+            rho[j] = r[j];
+        if (E)
+            E[j] = e[j] - emean;
+    }
+    free(n);
+    free(r);
+    free(e);
+}
+
+/* Linear-weighting gather of the node field at one position (Sec. 2.3). */
+static double gather_one(int nx, double dx, const double *E, double x)
+{
+    double u = x / dx;
+    double m = floor(u);
+    double f = u - m;
+    int j = wrap_cell((long)m, nx);
+    int j1 = j + 1 == nx ? 0 : j + 1;
+    return (1.0 - f) * E[j] + f * E[j1];
+}
+
+void orc_gather(int nx, double L, const double *E, long n, const double *x,
+                double *ex)
+{
+    double dx = L / nx;
+    for (long i = 0; i < n; ++i)
+        ex[i] = gather_one(nx, dx, E, x[i]);
+}
+
+/* Field energy W_E = 1/2 * integral of E^2 over the box, on the nodes. */
+double orc_field_energy(int nx, double L, const double *E)
+{
+    double dx = L / nx;
+    double s = 0.0;
+    for (int j = 0; j < nx; ++j)
+        s += E[j] * E[j];
+    return 0.5 * dx * s;
+}
+
+/*
+ * Leapfrog run of n_steps SIC steps (solve, gather, move of Sec. 2.3; only
+ * the scatter differs from PIC).
+ *
+ * On entry x, v hold x^0 and v^0 (or v^{-1/2} when half_step_init is 0).
+ * With half_step_init != 0 the velocities are first moved back half a step,
+ * v^{-1/2} = v^0 - dt/2 qm E^0(x^0).  Step n kicks with E^n at x^n, drifts,
+ * then deposits and solves for E^{n+1}.
+ *
+ * hist (n_steps+1 rows of 4 doubles, may be NULL) gets for every step n:
+ *   [W_E^n, KE^n, P^n, total charge]
+ * with KE^n = 1/2 sum m (v_{n-1/2}^2 + v_{n+1/2}^2)/2 and
+ * P^n = sum m (v_{n-1/2} + v_{n+1/2})/2 (time-centred on step n), mass
+ * m_i = w_i / qm.  Row n_steps has W_E of the final field and NaN for KE, P.
+ * e_hist (n_steps+1 rows of nx, may be NULL) gets every E^n.
+ * On exit x = x^{n_steps}, v = v^{n_steps-1/2}, E_out = E^{n_steps} (may be NULL).
+ */
+int orc_run(int nx, double L, double dt, double qm, int half_step_init,
+            int n_sheets, const int32_t *counts, const uint8_t *closed,
+            const int32_t *winding, long n_tracers, double *x, double *v,
+            const double *w, int n_steps, double *hist, double *e_hist,
+            double *E_out)
+{
+    double *charge = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *E = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *ex = (double *)malloc(sizeof(double) * (size_t)n_tracers);
+    int rc = orc_deposit(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+    if (rc)
+        goto done;
+    orc_field(nx, L, charge, NULL, E);
+    if (half_step_init) {
+        orc_gather(nx, L, E, n_tracers, x, ex);
+        for (long i = 0; i < n_tracers; ++i)
+            v[i] -= 0.5 * dt * qm * ex[i];
+    }
+    for (int step = 0; step <= n_steps; ++step) {
+        double qtot = 0.0;
+        for (int j = 0; j < nx; ++j)
+            qtot += charge[j];
+        if (e_hist)
+            memcpy(e_hist + (size_t)step * nx, E, sizeof(double) * (size_t)nx);
+        double we = orc_field_energy(nx, L, E);
+        if (step == n_steps) {
+            if (hist) {
+                double *h = hist + 4 * (size_t)step;
+                h[0] = we;
+                h[1] = NAN;
+                h[2] = NAN;
+                h[3] = qtot;
+            }
+            break;
+        }
+        orc_gather(nx, L, E, n_tracers, x, ex);
+        double ke = 0.0, p = 0.0;
+        for (long i = 0; i < n_tracers; ++i) {
+            double m = w[i] / qm;
+            double vold = v[i];
+            double vnew = vold + dt * qm * ex[i];
+            ke += 0.5 * m * 0.5 * (vold * vold + vnew * vnew);
+            p += m * 0.5 * (vold + vnew);
+            v[i] = vnew;
+            x[i] += dt * vnew;
+        }
+        if (hist) {
+            double *h = hist + 4 * (size_t)step;
+            h[0] = we;
+            h[1] = ke;
+            h[2] = p;
+            h[3] = qtot;
+        }
+        rc = orc_deposit(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+        if (rc)
+            goto done;
+        orc_field(nx, L, charge, NULL, E);
+    }
+    if (E_out)
+        memcpy(E_out, E, sizeof(double) * (size_t)nx);
+done:
+    free(charge);
+    free(E);
+    free(ex);
+    return rc;
+}

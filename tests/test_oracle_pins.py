@@ -1,0 +1,293 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code: exact rational brute
+force over all periodic images, closed forms (inverse Lagrangian map, cosine
+sums, leapfrog frequency, kinetic dispersion roots), invariants and symmetries.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fits, theory
+from paper_1506_07207_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_closed_forms.json")
+
+
+# ---------------------------------------------------------------- deposit ----
+
+def _brute_force_charge(nx, L, counts, closed, winding, x, w):
+    """Exact rational charge per cell: every segment clipped against every
+    periodic image of every cell (Eq. overlap summed as in Eq. rho_sum)."""
+    L = Fraction(L)
+    dx = L / nx
+    out = [Fraction(0)] * nx
+    base = 0
+    for n, c, wd in zip(counts, closed, winding):
+        segs = [(base + i, base + i + 1, 0) for i in range(n - 1)]
+        if c:
+            segs.append((base + n - 1, base, int(wd)))
+        for i, j, wrap in segs:
+            xa = Fraction(float(x[i]))
+            xb = Fraction(float(x[j])) + wrap * L
+            q = (Fraction(float(w[i])) + Fraction(float(w[j]))) / 2
+            a, b = min(xa, xb), max(xa, xb)
+            if a == b:
+                cell = math.floor(a / dx) % nx
+                out[cell] += q
+                continue
+            m_lo = math.floor(a / L) - 1
+            m_hi = math.floor(b / L) + 1
+            for cell in range(nx):
+                for m in range(m_lo, m_hi + 1):
+                    lo = max(a, cell * dx + m * L)
+                    hi = min(b, (cell + 1) * dx + m * L)
+                    if hi > lo:
+                        out[cell] += q * (hi - lo) / (b - a)
+        base += n
+    return np.array([float(v) for v in out])
+
+
+def _dyadic(rng, n, scale, denom=64):
+    return rng.integers(-4 * denom, 4 * denom, size=n) / denom * scale
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_deposit_matches_exact_rationals(seed):
+    rng = np.random.default_rng(seed)
+    nx = int(rng.choice([3, 4, 5, 8, 7]))
+    L = float(rng.choice([1.0, 2.0, 8.0, 0.5]))
+    n_sheets = int(rng.integers(1, 4))
+    counts = rng.integers(2, 6, size=n_sheets).astype(np.int32)
+    closed = rng.integers(0, 2, size=n_sheets).astype(np.uint8)
+    winding = (rng.integers(-1, 3, size=n_sheets) * closed).astype(np.int32)
+    n = int(counts.sum())
+    x = _dyadic(rng, n, L / 4)
+    # edge-aligned points, a zero-length segment and a multi-box segment
+    x[0] = 0.0
+    if n > 2:
+        x[2] = x[1]
+    if n > 3:
+        x[3] = x[2] + 2.5 * L
+    w = rng.integers(1, 9, size=n) / 8.0
+    got = oracle.deposit(nx, L, counts, closed, winding, x, w)
+    want = _brute_force_charge(nx, L, counts, closed, winding, x, w)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13 * max(1.0, np.abs(want).max()))
+
+
+def test_single_segment_cases():
+    nx, L = 4, 4.0              # dx = 1
+    one = np.array([2], np.int32)
+    op = np.array([0], np.uint8)
+    z = np.array([0], np.int32)
+    w = np.array([1.0, 1.0])
+    # inside one cell
+    np.testing.assert_array_equal(oracle.deposit(nx, L, one, op, z, [1.25, 1.75], w), [0, 1, 0, 0])
+    # exactly three whole cells, reversed order
+    got = oracle.deposit(nx, L, one, op, z, [4.0, 1.0], w)
+    np.testing.assert_allclose(got, [0, 1 / 3, 1 / 3, 1 / 3], rtol=1e-15)
+    # zero length on an edge: left-closed cells take it
+    np.testing.assert_array_equal(oracle.deposit(nx, L, one, op, z, [2.0, 2.0], w), [0, 0, 1, 0])
+    # wrapping across x = 0 from below
+    got = oracle.deposit(nx, L, one, op, z, [-0.5, 0.5], w)
+    np.testing.assert_allclose(got, [0.5, 0, 0, 0.5], rtol=1e-15)
+    # twice around the box: every cell gets a quarter
+    got = oracle.deposit(nx, L, one, op, z, [0.3, 8.3], w)
+    np.testing.assert_allclose(got, [0.25] * 4, rtol=1e-14)
+
+
+# ------------------------------------------------------- field and gather ----
+
+def test_uniform_sheet_gives_zero_field():
+    nx, L, n = 16, 2.0, 64
+    x = np.arange(n) * (L / n)
+    w = np.full(n, L / n)
+    c = oracle.deposit(nx, L, [n], [1], [1], x, w)
+    rho, E = oracle.field(nx, L, c)
+    assert np.all(c == c[0])
+    assert np.all(rho == 0.0) and np.all(E == 0.0)
+
+
+def test_field_of_cosine_density_closed_form():
+    nx, L, A = 64, 3.0, 0.37
+    dx = L / nx
+    for m in (1, 2, 5, 31):
+        th = 2 * np.pi * m / nx
+        n = 1.0 + A * np.cos(th * np.arange(nx))
+        rho, E = oracle.field(nx, L, n * dx)
+        # E'_j = dx A sum_{i<j} cos(th i) = dx A [sin(th(j-1/2)) + sin(th/2)] / (2 sin(th/2));
+        # the constant drops out with the mean and sin(th(j-1/2)) has zero mean.
+        want = dx * A * np.sin(th * (np.arange(nx) - 0.5)) / (2 * np.sin(th / 2))
+        np.testing.assert_allclose(rho, A * np.cos(th * np.arange(nx)), atol=1e-14)
+        np.testing.assert_allclose(E, want, atol=1e-14)
+
+
+def test_monotone_sheet_field_from_inverse_map():
+    """One monotone cold sheet: the charge left of x is the inverse of the
+    piecewise-linear Lagrangian map, so E at the nodes follows without any
+    overlap arithmetic (closed form of Sec. 2.3 for a sheet that never folds)."""
+    nx, n, k, amp = 32, 200, 1.0, 0.3
+    L = 2 * np.pi / k
+    q = np.arange(n) * (L / n)
+    x = q + amp * np.sin(k * q) + 0.123
+    w = np.full(n, L / n)
+    c = oracle.deposit(nx, L, [n], [1], [1], x, w)
+    _, E = oracle.field(nx, L, c)
+    # cumulative charge as a function of x, extended periodically
+    xe = np.concatenate([x - L, x, x + L, [x[0] + 2 * L]])
+    le = np.concatenate([q - L, q, q + L, [2 * L]])
+    edges = np.arange(nx + 1) * (L / nx)
+    lcum = np.interp(edges, xe, le)
+    charge = np.diff(lcum)
+    np.testing.assert_allclose(c, charge, rtol=1e-12)
+    Ep = np.concatenate([[0.0], np.cumsum(charge - L / nx)])[:nx]
+    np.testing.assert_allclose(E, Ep - Ep.mean(), atol=1e-12)
+
+
+def test_gather_linear_weighting():
+    nx, L = 8, 4.0
+    E = np.array([0.0, 1.0, -2.0, 3.0, 0.5, 0.25, -1.0, 2.0])
+    x = np.array([0.0, 0.5, 1.0, 0.25, 3.75, 4.0, -0.25, 8.5])
+    # dx = 0.5: node hits, a midpoint, quarter points and the periodic wrap
+    want = [0.0, 1.0, -2.0, 0.5, 0.5 * 2.0 + 0.5 * 0.0, 0.0,
+            0.5 * 2.0 + 0.5 * 0.0, 1.0]
+    np.testing.assert_allclose(oracle.gather(nx, L, E, x), want, rtol=1e-15)
+
+
+def test_one_leapfrog_step_by_hand():
+    nx, n, k = 16, 64, 1.0
+    L = 2 * np.pi / k
+    q = np.arange(n) * (L / n)
+    x0 = q + 0.2 * np.sin(k * q)
+    v0 = 0.1 * np.cos(k * q)
+    w = np.full(n, L / n)
+    dt, qm = 0.3, 1.7
+    # field at t=0 from the inverse-map closed form (see the test above)
+    xe = np.concatenate([x0 - L, x0, x0 + L, [x0[0] + 2 * L]])
+    le = np.concatenate([q - L, q, q + L, [2 * L]])
+    charge = np.diff(np.interp(np.arange(nx + 1) * (L / nx), xe, le))
+    Ep = np.concatenate([[0.0], np.cumsum(charge - L / nx)])[:nx]
+    E0 = Ep - Ep.mean()
+    nodes = np.arange(nx + 1) * (L / nx)
+    Ex = np.interp(np.mod(x0, L), nodes, np.append(E0, E0[0]))
+    v1 = v0 + dt * qm * Ex
+    x1 = x0 + dt * v1
+    r = oracle.run(nx, L, dt, [n], [1], [1], x0, v0, w, 1, qm=qm, half_step_init=False)
+    np.testing.assert_allclose(r["v"], v1, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r["x"], x1, rtol=1e-12, atol=1e-14)
+    # the half step back at start-up: v^{-1/2} = v^0 - dt/2 qm E^0(x^0)
+    r = oracle.run(nx, L, dt, [n], [1], [1], x0, v0, w, 0, qm=qm, half_step_init=True)
+    np.testing.assert_allclose(r["v"], v0 - 0.5 * dt * qm * Ex, rtol=1e-12, atol=1e-14)
+
+
+# -------------------------------------------------------------- invariants ----
+
+def test_invariants_translation_mirror_charge():
+    p = inputs.tiny_problem(seed=7, n_sheets=5, max_tracers=40, nx=16, L=2.0)
+    dx = p.L / p.nx
+    c = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, p.x, p.w)
+    rho, E = oracle.field(p.nx, p.L, c)
+    # charge conservation: the mesh holds the sum of the segment charges
+    qs = 0.0
+    base = 0
+    for n, cl in zip(p.counts, p.closed):
+        ww = p.w[base:base + n]
+        qs += 0.5 * (ww[:-1] + ww[1:]).sum() + (0.5 * (ww[-1] + ww[0]) if cl else 0.0)
+        base += n
+    assert abs(c.sum() - qs) <= 1e-13 * qs
+    assert abs(rho.sum()) < 1e-12 * np.abs(rho).max() * p.nx
+    assert abs(E.sum()) < 1e-12 * np.abs(E).max() * p.nx
+    # translation by exactly one cell (dx is a power of two here) rolls the mesh
+    c1 = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, p.x + dx, p.w)
+    np.testing.assert_allclose(c1, np.roll(c, 1), rtol=1e-12, atol=1e-14)
+    # mirror x -> L - x reverses every sheet's direction (winding -> -winding)
+    cm = oracle.deposit(p.nx, p.L, p.counts, p.closed, -p.winding, p.L - p.x, p.w)
+    np.testing.assert_allclose(cm, c[::-1], rtol=1e-12, atol=1e-14)
+    _, Em = oracle.field(p.nx, p.L, cm)
+    np.testing.assert_allclose(Em, -np.roll(E[::-1], 1), rtol=1e-10, atol=1e-13)
+
+
+# ------------------------------------------------------------ dynamics pins ----
+
+def test_langmuir_closed_forms():
+    """Sec. 3.1: a cold sheet oscillates at omega_p (leapfrog: (2/dt) asin(dt/2))
+    with field energy (amp^2 L / 4) cos^2(omega t) for x = q + amp sin(k q)."""
+    p = inputs.langmuir()
+    r = oracle.run_problem(p, record_E=True)
+    t = np.arange(p.n_steps + 1) * p.dt
+    amp = p.params["amp"]
+    assert abs(r["hist"][0, 0] / (amp * amp * p.L / 4) - 1) < 1e-4
+    # over the first 10 plasma times the coarse (Nx = 64) grid tracks omega to 1e-3
+    m1 = fits.mode(r["E_hist"][:101], 1)
+    assert abs(fits.oscillation_omega(t[:101], m1.imag) / theory.leapfrog_omega(p.dt) - 1) < 1e-3
+    # total charge is conserved
+    assert np.ptp(r["hist"][:, 3]) <= 1e-12 * r["hist"][0, 3]
+    # the grid error vanishes as dx -> 0: Nx = 1024 holds omega over 500 steps
+    pf = inputs.langmuir(nx=1024)
+    rf = oracle.run_problem(pf, record_E=True)
+    wf = fits.oscillation_omega(t, fits.mode(rf["E_hist"], 1).imag)
+    assert abs(wf / theory.leapfrog_omega(p.dt) - 1) < 2e-4
+    et = rf["hist"][:-1, 0] + rf["hist"][:-1, 1]
+    assert np.ptp(et) / et.mean() < 0.01
+
+
+def test_dispersion_function_against_library():
+    special = pytest.importorskip("scipy.special")
+    pts = [0.3 + 0.2j, 2 - 0.2j, 5 + 1j, 19 + 11j, -3 + 0.01j, 0.5 - 3j, 1e-3 + 1e-3j,
+           2.7 - 0.3j, 7 + 0.5j, 30 + 20j]
+    for z in pts:
+        ref = special.wofz(z)
+        assert abs(theory.faddeeva(z) - ref) <= 1e-9 * abs(ref), z
+
+
+def test_theory_roots_and_paper_closed_forms():
+    g = json.load(open(GOLDEN))
+    # Landau root for the unit Maxwellian at k = 0.5
+    w = theory.landau_root(0.5)
+    lit = g["landau_linear_root_k0.5_unit_maxwellian"]
+    assert abs(w.real - lit["omega_real"]) < 1e-4 and abs(w.imag - lit["gamma"]) < 1e-4
+    eps = theory.kinetic_dielectric(w, 0.5, [(1.0, 0.0, 1.0)])
+    assert abs(eps) < 1e-10
+    # Sec. 3.2: the cold maximum growth is omega_p/2 (per-beam omega_p) at k v0 = sqrt(3)/2 omega_p
+    wb = math.sqrt(0.5)
+    kmax = math.sqrt(3) / 2 * wb / 2.4
+    assert abs(theory.cold_two_stream_rate(kmax, 2.4) - g["two_stream_max_growth"]["ratio_to_omega_p"] * wb) < 1e-12
+    ks = np.linspace(0.01, 0.4, 400)
+    assert max(theory.cold_two_stream_rate(k, 2.4) for k in ks) <= wb / 2 + 1e-12
+    # Sec. 3.2: stable beyond k = sqrt(2) omega_p / v0
+    kc = g["two_stream_instability_threshold"]["sqrt2"] * wb / 2.4
+    assert theory.cold_two_stream_rate(kc * 1.001, 2.4) == 0.0
+    assert theory.cold_two_stream_rate(kc * 0.999, 2.4) > 0.0
+    # a warm beam grows a little slower than the cold one
+    gw = theory.warm_two_stream_rate(0.2, 2.4, 0.1)
+    gc = theory.cold_two_stream_rate(0.2, 2.4)
+    assert 0.995 * gc < gw < gc
+
+
+@pytest.mark.slow
+def test_landau_damping_rate():
+    """Sec. 3.3 set-up at the linear Landau configuration: the field energy
+    peaks decay at 2 gamma with gamma the kinetic root (within 2 %)."""
+    p = inputs.landau_linear()
+    r = oracle.run_problem(p)
+    t = np.arange(p.n_steps + 1) * p.dt
+    g = fits.damping_rate(t, r["hist"][:, 0], 2.0, 30.0)
+    assert abs(g / theory.landau_root(0.5).imag - 1) < 0.02
+    assert np.ptp(r["hist"][:, 3]) <= 1e-12 * r["hist"][0, 3]
+
+
+def test_two_stream_growth_rate():
+    """Sec. 3.2: the fundamental of a small perturbation grows at the kinetic
+    rate of two Maxwellian beams (within 1 %)."""
+    p = inputs.two_stream(2.4, 0.1, 0.2, nx=64, n_sheets=32, n_tracers=512, eps=1e-5,
+                          t_end=28.0)
+    r = oracle.run_problem(p, record_E=True)
+    t = np.arange(p.n_steps + 1) * p.dt
+    a = np.abs(fits.mode(r["E_hist"], 1))
+    g = fits.growth_rate(t, a, 10.0, 28.0)
+    assert abs(g / theory.warm_two_stream_rate(0.2, 2.4, 0.1) - 1) < 0.01
