@@ -1,0 +1,181 @@
+/*
+ * sic.h -- C ABI of the GB300-native simplex-in-cell (SIC) library.
+ *
+ * The library advances the 1D periodic Vlasov-Poisson system with the method
+ * of Kates-Harbeck, Totorica, Zrake & Abel (arXiv:1506.07207): phase space is
+ * carried by sheets of ordered tracers (Sec. 2.2); each pair of adjacent
+ * tracers is a particle whose charge is spread uniformly between them (the box
+ * function of Sec. 2.3) and deposited on the charge mesh by exact overlap
+ * integration (Eq. overlap, Eq. rho_sum); the field solve, linear gather and
+ * push are those of a PIC code (Sec. 2.3, last paragraphs).
+ *
+ * Conventions (the paper leaves these open):
+ *   - Normalised units, C = 1 in the Poisson equation of Sec. 2.1: with
+ *     E = -dPhi/dx, dE/dx = n - mean(n) and a tracer accelerates by
+ *     charge_to_mass * E.  The neutralising background is the computed mean
+ *     density.
+ *   - Cells j = 0..nx-1 cover [j dx, (j+1) dx), dx = box_length / nx, left
+ *     closed.  rho is the cell average; E lives on the nodes x_j = j dx.
+ *   - Segment charge q_s = (w_i + w_{i+1}) / 2.  A zero-length segment puts
+ *     its whole charge in the cell holding its point.
+ *   - A closed sheet is closed by the segment (x_N, x_1 + winding * L).
+ *   - Leapfrog: v^{n+1/2} = v^{n-1/2} + dt qm E^n(x^n), x^{n+1} = x^n + dt v^{n+1/2}.
+ *
+ * Precision: positions are held as unwrapped 32.32 fixed point in cell units,
+ * velocities and push arithmetic in FP32, charge in int64 fixed point (total
+ * charge is conserved bit-exactly and the deposit is independent of the order
+ * of the atomic adds); the field solve is exact integer arithmetic with one
+ * final rounding.  Results are bit-identical however the work is split
+ * across thread blocks or batched with other simulations.
+ *
+ * Memory: every pointer argument named *_host is caller-owned host memory that
+ * the call only reads or writes during the call.  All device state is owned by
+ * the library and freed by sic_destroy.  Calls on one simulation must not run
+ * concurrently; distinct simulations are independent.  Every function returns
+ * SIC_OK (0) or a negative SIC_E* code; sic_strerror names it.  After a
+ * SIC_ECUDA the simulation must be destroyed.
+ */
+#ifndef SIC_H
+#define SIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIC_OK 0
+#define SIC_EINVAL (-1)        /* bad size, NaN/Inf input, nx out of range, ... */
+#define SIC_ENOMEM (-2)        /* device or host allocation failed */
+#define SIC_ECUDA (-3)         /* a CUDA call failed */
+#define SIC_ERANGE (-4)        /* a position left the fixed-point range (|x/dx| >= 2^30) */
+#define SIC_ESEGMENT_LONG (-5) /* strict mode: a segment is longer than the box */
+#define SIC_ETIMEOUT (-6)      /* a bounded device wait gave up */
+#define SIC_EBUSY (-7)         /* server: budget or slots exhausted */
+
+/* Largest mesh the deposit kernels stage in shared memory. */
+#define SIC_NX_MAX 8192
+/* Largest tracer count of one simulation (positions are indexed by int64,
+ * the cap keeps per-simulation fixed-point sums far from overflow). */
+#define SIC_TRACERS_MAX (1LL << 28)
+
+typedef struct sic_sim sic_sim;
+
+/*
+ * Problem statement (Sec. 2.2-2.3): M sheets of ordered tracers on a periodic
+ * box [0, box_length) split into nx cells, stepped with time step dt.
+ * tracers_per_sheet[s] >= 2 consecutive tracers form sheet s; sheet_closed[s]
+ * != 0 adds the closing segment (last, first + sheet_winding[s] * L)
+ * (periodic identification of Sec. 2.3).  sheet_winding may be NULL for all
+ * zero windings; it is ignored for open sheets.
+ */
+typedef struct {
+    int32_t nx;                        /* cells, 2..SIC_NX_MAX */
+    double box_length;                 /* L > 0 */
+    double dt;                         /* > 0 */
+    int32_t n_sheets;                  /* M >= 1 */
+    const int32_t *tracers_per_sheet;  /* [M], each >= 2 */
+    const uint8_t *sheet_closed;       /* [M] */
+    const int32_t *sheet_winding;      /* [M] or NULL */
+    double charge_to_mass;             /* qm, finite and != 0; the paper's sign is +1 */
+    int32_t half_step_init;            /* 1: v^{-1/2} = v^0 - dt/2 qm E^0(x^0) at create */
+    int32_t strict_segments;           /* 1: sic_step fails with SIC_ESEGMENT_LONG when a
+                                          segment exceeds the box (Sec. 3.2 notes the run
+                                          cannot continue then); 0: deposit it anyway,
+                                          every periodic image counting */
+    int32_t history_len;               /* rows of the per-step diagnostic ring, >= 1 */
+    void *stream;                      /* cudaStream_t the simulation runs on, NULL = its own */
+} sic_config;
+
+/* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum
+ * are monitored; W_E is the potential energy E_pot of the paper's figures). */
+typedef struct {
+    int64_t step;          /* steps taken since create */
+    double t;              /* step * dt */
+    double field_energy;   /* W_E = 1/2 sum_j E_j^2 dx of the current field */
+    double kinetic_energy; /* KE of the last kick, time-centred: 1/2 sum m (v-^2 + v+^2)/2 */
+    double momentum;       /* sum m (v- + v+)/2 of the last kick; m = w / qm */
+    int64_t charge_fixed;  /* total mesh charge in fixed-point units (constant) */
+    double charge_unit;    /* charge of one fixed-point unit */
+    double max_segment;    /* longest segment of the last deposit, in box lengths */
+} sic_diag;
+
+/*
+ * Create a simulation from host arrays of length sum(tracers_per_sheet):
+ * positions x (unwrapped, any real value), velocities v and charge weights
+ * w > 0, all finite.  The inputs are copied; the initial charge is deposited
+ * and the field solved (and the half step applied if asked).
+ */
+int sic_create(const sic_config *cfg, const double *x_host, const double *v_host,
+               const double *w_host, sic_sim **out);
+
+/*
+ * Create M closed horizontal sheets of winding 1 (the "horizontal" set-up of
+ * Sec. 3.3) that all share one position template: sheet s has tracers at
+ * x_template[0..n-1] with velocity v_sheet[s] and weight w_sheet[s] each.
+ * cfg->tracers_per_sheet, sheet_closed and sheet_winding are ignored.  Only
+ * the template and the per-sheet values cross the bus.
+ */
+int sic_create_horizontal(const sic_config *cfg, int32_t n_template,
+                          const double *x_template_host, const double *v_sheet_host,
+                          const double *w_sheet_host, sic_sim **out);
+
+/*
+ * Deposit the current tracer positions (Eq. overlap, Eq. rho_sum) and solve
+ * the field.  Outputs, each nullable, host, nx entries: the fixed-point charge
+ * per cell (units of sic_diag.charge_unit) and the neutralised density
+ * rho_j = n_j - mean(n).
+ */
+int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host);
+
+/* The node field E_j (host, nx entries) of the latest deposit. */
+int sic_field(sic_sim *sim, double *E_host);
+
+/* Gather, kick and drift every tracer with the current field; no deposit. */
+int sic_push(sic_sim *sim);
+
+/* n_steps full steps: fused gather-kick-drift-deposit, then the field solve. */
+int sic_step(sic_sim *sim, int32_t n_steps);
+
+/* One of the two kernels of a step: phase 1 = fused gather-kick-drift-deposit,
+ * phase 2 = seams, field solve and history row.  Phase 1 then phase 2 equals
+ * sic_step(sim, 1); callers use it to interleave their own work or to time
+ * the phases on the simulation's stream. */
+int sic_step_phase(sic_sim *sim, int32_t phase);
+
+/* Advance several simulations together, n_steps[i] steps each; the work of
+ * all of them shares each kernel launch.  Results equal separate sic_step
+ * calls bit for bit. */
+int sic_step_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps);
+
+int sic_diagnostics(sic_sim *sim, sic_diag *out);
+
+/* Per-step history [rows][4] = {W_E, KE, P, charge_fixed} of the last
+ * min(rows, history_len) steps, oldest first; returns the row count via *rows. */
+int sic_history(sic_sim *sim, double *hist_host, int32_t *rows);
+
+/* Copy the tracers back: unwrapped positions and current velocities
+ * (v^{n-1/2} after n steps), host, sum(tracers_per_sheet) entries each. */
+int sic_get_state(sic_sim *sim, double *x_host, double *v_host);
+
+/* Device addresses of the state for zero-copy consumers:
+ * positions int64 (2^-32 cell units), velocities float (cells per step),
+ * tracer i of sheet s at sheet_offset[s] + i.  Valid until sic_destroy. */
+int sic_device_state(sic_sim *sim, int64_t **pos_dev, float **vel_dev,
+                     const int64_t **sheet_offset_host);
+
+/* Synchronise the simulation's stream. */
+int sic_sync(sic_sim *sim);
+
+void sic_destroy(sic_sim *sim);
+
+const char *sic_strerror(int code);
+
+/* Kernel launches issued by this process since load (for launch accounting). */
+int64_t sic_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIC_H */

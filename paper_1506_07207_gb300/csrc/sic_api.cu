@@ -1,0 +1,884 @@
+// sic_api.cu -- host runtime behind the C ABI of include/sic.h.
+//
+// Owns each simulation's device memory (one stream-ordered allocation), the
+// work-item plan (consecutive tracers of one sheet per item, balanced over a
+// persistent grid of SMs x resident blocks), CUDA-graph capture of the
+// per-step kernel pair, and batching of several simulations into shared
+// launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sic.h"
+#include "sic_internal.h"
+
+using namespace sic;
+
+namespace {
+
+constexpr int kGraphSteps = 8;      // steps captured in one graph
+constexpr int kItemCost = 256;      // fixed cost of a work item, in tracer units
+constexpr double kTwo32 = 4294967296.0;
+
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t at = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return at;
+    }
+};
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        return 1;
+    return n;
+}
+
+NxDiv make_div(int nx)
+{
+    NxDiv d;
+    d.nx = nx;
+    int l = 0;
+    while ((1 << l) < nx)
+        ++l;
+    const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - (uint64_t)nx)) / (uint64_t)nx + 1;
+    d.magic = (uint32_t)m;
+    d.shift = l - 1;
+    d.offset = nx * ((1 << 30) / nx + 1);
+    return d;
+}
+
+// x / dx as 32.32 fixed point
+int64_t to_fixed(double xc)
+{
+    const double c = std::floor(xc);
+    const double f = xc - c;
+    return (int64_t)c * (int64_t)4294967296LL + (int64_t)std::llround(f * kTwo32);
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+struct sic_sim {
+    int nx = 0;
+    double L = 0, dt = 0, dx = 0, qm = 1;
+    int strict = 0, hist_len = 1, half_step_init = 0;
+    bool per_q = false;
+    int M = 0;
+    std::vector<int32_t> counts;
+    std::vector<uint8_t> closed;
+    std::vector<int32_t> winding;
+    std::vector<int64_t> sheet_off;
+    std::vector<int32_t> sheet_qh;
+    int64_t n_tracers = 0, n_alloc = 0;
+    double sigma = 1.0;
+    std::vector<WorkItem> items;
+    int grid = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *dmem = nullptr;
+    SimDev h{};
+    SimDev *d_desc = nullptr;
+    WorkItem *d_items = nullptr;
+    int32_t *d_cta = nullptr;
+    FieldJob *d_job = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t steps_done = 0;
+    cudaError_t last = cudaSuccess;
+};
+
+namespace {
+
+int fail_cuda(sic_sim *s, cudaError_t e)
+{
+    if (s)
+        s->last = e;
+    return SIC_ECUDA;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess)                    \
+            return fail_cuda(sim, e_);            \
+    } while (0)
+
+int validate(const sic_config *c, bool need_sheets)
+{
+    if (!c)
+        return SIC_EINVAL;
+    if (c->nx < 2 || c->nx > SIC_NX_MAX)
+        return SIC_EINVAL;
+    if (!is_finite(c->box_length) || c->box_length <= 0)
+        return SIC_EINVAL;
+    if (!is_finite(c->dt) || c->dt <= 0)
+        return SIC_EINVAL;
+    if (c->n_sheets < 1)
+        return SIC_EINVAL;
+    if (!is_finite(c->charge_to_mass) || c->charge_to_mass == 0)
+        return SIC_EINVAL;
+    if (c->history_len < 1)
+        return SIC_EINVAL;
+    if (need_sheets) {
+        if (!c->tracers_per_sheet || !c->sheet_closed)
+            return SIC_EINVAL;
+        int64_t total = 0;
+        for (int s = 0; s < c->n_sheets; ++s) {
+            if (c->tracers_per_sheet[s] < 2)
+                return SIC_EINVAL;
+            total += c->tracers_per_sheet[s];
+        }
+        if (total > SIC_TRACERS_MAX)
+            return SIC_EINVAL;
+    }
+    return SIC_OK;
+}
+
+// Test knobs: SIC_ITEM_TILES (tiles per work item, default 1) and SIC_GRID
+// (blocks of the deposit kernel).  Neither changes any result: the mesh is an
+// integer sum and every per-item reduction runs in a fixed order.
+int env_int(const char *name, int dflt)
+{
+    const char *v = std::getenv(name);
+    if (!v || !*v)
+        return dflt;
+    const int x = std::atoi(v);
+    return x > 0 ? x : dflt;
+}
+
+// Split every sheet into items of at most SIC_ITEM_TILES tiles, link the seams.
+void plan_items(sic_sim *sim)
+{
+    const int item = SIC_K1_TILE * env_int("SIC_ITEM_TILES", 1);
+    sim->items.clear();
+    for (int s = 0; s < sim->M; ++s) {
+        const int n = sim->counts[s];
+        const int first = (int)sim->items.size();
+        for (int k = 0; k * item < n; ++k) {
+            WorkItem w{};
+            w.sim = 0;
+            w.local = (int)sim->items.size();
+            w.t0 = sim->sheet_off[s] + (int64_t)k * item;
+            w.count = std::min(item, n - k * item);
+            w.qh = sim->per_q ? 0 : sim->sheet_qh[s];
+            w.seam_next = -1;
+            w.seam_shift = 0;
+            sim->items.push_back(w);
+        }
+        const int last = (int)sim->items.size() - 1;
+        for (int i = first; i < last; ++i)
+            sim->items[i].seam_next = i + 1;
+        if (sim->closed[s]) {
+            sim->items[last].seam_next = first;
+            sim->items[last].seam_shift = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
+        }
+    }
+}
+
+// Contiguous runs of items per block, balanced by tracer count.
+std::vector<int32_t> partition(const std::vector<WorkItem> &items, int grid)
+{
+    const int n = (int)items.size();
+    std::vector<int64_t> start(n + 1, 0);
+    for (int i = 0; i < n; ++i)
+        start[i + 1] = start[i] + items[i].count + kItemCost;
+    const int64_t total = start[n];
+    std::vector<int32_t> cta(grid + 1);
+    int i = 0;
+    for (int b = 0; b <= grid; ++b) {
+        const int64_t target = (int64_t)((__int128)total * b / grid);
+        while (i < n && start[i] < target)
+            ++i;
+        cta[b] = i;
+    }
+    cta[grid] = n;
+    return cta;
+}
+
+int pick_grid(int n_items, int nx_max, bool per_q)
+{
+    int per_sm = k1_blocks_per_sm(nx_max, true, true, per_q);
+    if (per_sm < 1)
+        per_sm = 1;
+    return std::max(1, std::min(n_items, env_int("SIC_GRID", num_sms() * per_sm)));
+}
+
+cudaError_t launch_step(sic_sim *sim)
+{
+    cudaError_t e = launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, true,
+                                        sim->per_q, 1.0f, 1, sim->stream);
+    if (e != cudaSuccess)
+        return e;
+    return launch_field(sim->d_desc, sim->d_job, 1, sim->nx, 1, sim->stream);
+}
+
+cudaError_t launch_deposit_field(sic_sim *sim)
+{
+    cudaError_t e = launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, false, true,
+                                        sim->per_q, 0.0f, 0, sim->stream);
+    if (e != cudaSuccess)
+        return e;
+    return launch_field(sim->d_desc, sim->d_job, 1, sim->nx, 0, sim->stream);
+}
+
+int check_device_errors(sic_sim *sim)
+{
+    SimScalars sc;
+    CK(cudaMemcpyAsync(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    if (sc.err & SIC_ERR_RANGE)
+        return SIC_ERANGE;
+    if (sc.err & SIC_ERR_SEGLONG)
+        return SIC_ESEGMENT_LONG;
+    return SIC_OK;
+}
+
+// Fixed-point charge scale: every segment charge below 2^29 units, a power of two.
+double choose_sigma(double max_w)
+{
+    double sigma = std::ldexp(1.0, (int)std::floor(std::log2(std::ldexp(1.0, 29) / max_w)));
+    while (std::llround(max_w * sigma * 0.5) * 2 > (1LL << 29))
+        sigma *= 0.5;
+    return sigma;
+}
+
+// Common part of both constructors: sizes, device layout, descriptor.
+// Expects counts, closed, winding, per_q, sigma and sheet_qh to be set.
+int setup(sic_sim *sim, const sic_config *cfg)
+{
+    sim->nx = cfg->nx;
+    sim->L = cfg->box_length;
+    sim->dt = cfg->dt;
+    sim->dx = cfg->box_length / cfg->nx;
+    sim->qm = cfg->charge_to_mass;
+    sim->strict = cfg->strict_segments ? 1 : 0;
+    sim->hist_len = cfg->history_len;
+    sim->half_step_init = cfg->half_step_init ? 1 : 0;
+    sim->sheet_off.assign(sim->M, 0);
+    int64_t off = 0;
+    for (int s = 0; s < sim->M; ++s) {
+        sim->sheet_off[s] = off;
+        off += (sim->counts[s] + SIC_ALIGN_TRACERS - 1) / SIC_ALIGN_TRACERS * SIC_ALIGN_TRACERS;
+    }
+    sim->n_alloc = std::max<int64_t>(off, SIC_ALIGN_TRACERS);
+
+    if (cfg->stream) {
+        sim->stream = (cudaStream_t)cfg->stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking));
+        sim->own_stream = true;
+    }
+    plan_items(sim);
+    const int n_items = (int)sim->items.size();
+    sim->grid = pick_grid(n_items, sim->nx, sim->per_q);
+    std::vector<int32_t> cta = partition(sim->items, sim->grid);
+
+    Layout lay;
+    const int nx = sim->nx;
+    const size_t oU = lay.take(8 * (size_t)sim->n_alloc);
+    const size_t oV = lay.take(4 * (size_t)sim->n_alloc);
+    const size_t oQ = sim->per_q ? lay.take(4 * (size_t)sim->n_alloc) : 0;
+    const size_t oMesh = lay.take(8 * (size_t)nx);
+    const size_t oLast = lay.take(8 * (size_t)nx);
+    const size_t oEk = lay.take(8 * (size_t)nx);
+    const size_t oE64 = lay.take(8 * (size_t)nx);
+    const size_t oRho = lay.take(8 * (size_t)nx);
+    const size_t oItems = lay.take(sizeof(WorkItem) * (size_t)n_items);
+    const size_t oEF = lay.take(8 * (size_t)n_items);
+    const size_t oEL = lay.take(8 * (size_t)n_items);
+    const size_t oDiag = lay.take(sizeof(ItemDiag) * (size_t)n_items);
+    const size_t oHist = lay.take(32 * (size_t)sim->hist_len);
+    const size_t oSc = lay.take(sizeof(SimScalars));
+    const size_t oDesc = lay.take(sizeof(SimDev));
+    const size_t oCta = lay.take(4 * (size_t)(sim->grid + 1));
+    const size_t oJob = lay.take(sizeof(FieldJob));
+    cudaError_t e = cudaMallocAsync(&sim->dmem, lay.off, sim->stream);
+    if (e == cudaErrorMemoryAllocation)
+        return SIC_ENOMEM;
+    CK(e);
+    char *b = (char *)sim->dmem;
+    CK(cudaMemsetAsync(b, 0, lay.off, sim->stream));
+
+    SimDev &h = sim->h;
+    h.U = (int64_t *)(b + oU);
+    h.V = (float *)(b + oV);
+    h.Qh = sim->per_q ? (const int32_t *)(b + oQ) : nullptr;
+    h.mesh = (unsigned long long *)(b + oMesh);
+    h.mesh_last = (long long *)(b + oLast);
+    h.Ek = (float2 *)(b + oEk);
+    h.E64 = (double *)(b + oE64);
+    h.rho64 = (double *)(b + oRho);
+    h.items = (const WorkItem *)(b + oItems);
+    h.edge_first = (int64_t *)(b + oEF);
+    h.edge_last = (int64_t *)(b + oEL);
+    h.item_diag = (ItemDiag *)(b + oDiag);
+    h.hist = (double *)(b + oHist);
+    h.sc = (SimScalars *)(b + oSc);
+    h.n_items = n_items;
+    h.hist_len = sim->hist_len;
+    h.div = make_div(nx);
+    const double nx2 = (double)nx * (double)nx;
+    h.E_scale = 1.0 / (nx2 * sim->sigma);
+    h.e_scale = sim->qm * sim->dt * sim->dt / sim->dx * h.E_scale;
+    h.rho_scale = 1.0 / ((double)nx * sim->sigma * sim->dx);
+    h.half_dx = 0.5 * sim->dx;
+    const double vu = sim->dx / sim->dt;  // physical velocity of one cell per step
+    h.ke_scale = vu * vu / (2.0 * sim->sigma * sim->qm);
+    h.p_scale = vu / (sim->sigma * sim->qm);
+    h.strict = sim->strict;
+    sim->d_desc = (SimDev *)(b + oDesc);
+    sim->d_items = (WorkItem *)(b + oItems);
+    sim->d_cta = (int32_t *)(b + oCta);
+    sim->d_job = (FieldJob *)(b + oJob);
+    FieldJob job{0, 0};
+    CK(cudaMemcpyAsync(sim->d_desc, &h, sizeof(SimDev), cudaMemcpyHostToDevice, sim->stream));
+    CK(cudaMemcpyAsync(sim->d_items, sim->items.data(), sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice,
+                       sim->stream));
+    CK(cudaMemcpyAsync(sim->d_cta, cta.data(), 4 * cta.size(), cudaMemcpyHostToDevice, sim->stream));
+    CK(cudaMemcpyAsync(sim->d_job, &job, sizeof(job), cudaMemcpyHostToDevice, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));  // host staging buffers go out of scope
+    return SIC_OK;
+}
+
+// Initial deposit + field, then the optional half kick back.
+int initialise(sic_sim *sim)
+{
+    CK(launch_deposit_field(sim));
+    if (sim->half_step_init)
+        CK(launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, false, sim->per_q,
+                               -0.5f, 0, sim->stream));
+    const int rc = check_device_errors(sim);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sic_create(const sic_config *cfg, const double *x_host, const double *v_host, const double *w_host,
+               sic_sim **out)
+{
+    if (!out)
+        return SIC_EINVAL;
+    *out = nullptr;
+    int rc = validate(cfg, true);
+    if (rc)
+        return rc;
+    if (!x_host || !v_host || !w_host)
+        return SIC_EINVAL;
+    const double dx = cfg->box_length / cfg->nx;
+    int64_t n = 0;
+    for (int s = 0; s < cfg->n_sheets; ++s)
+        n += cfg->tracers_per_sheet[s];
+    double max_w = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!is_finite(x_host[i]) || !is_finite(v_host[i]) || !is_finite(w_host[i]) || w_host[i] <= 0)
+            return SIC_EINVAL;
+        if (std::fabs(x_host[i] / dx) >= (double)(1 << 29))
+            return SIC_ERANGE;
+        if (std::fabs(v_host[i] * cfg->dt / dx) >= (double)(1 << 20))
+            return SIC_EINVAL;
+        max_w = std::max(max_w, w_host[i]);
+    }
+    sic_sim *sim = new (std::nothrow) sic_sim;
+    if (!sim)
+        return SIC_ENOMEM;
+    sim->M = cfg->n_sheets;
+    sim->counts.assign(cfg->tracers_per_sheet, cfg->tracers_per_sheet + sim->M);
+    sim->closed.assign(cfg->sheet_closed, cfg->sheet_closed + sim->M);
+    sim->winding.assign(sim->M, 0);
+    for (int s = 0; s < sim->M; ++s) {
+        sim->closed[s] = sim->closed[s] ? 1 : 0;
+        if (cfg->sheet_winding && sim->closed[s])
+            sim->winding[s] = cfg->sheet_winding[s];
+    }
+    sim->n_tracers = n;
+    // weights: one value per sheet when every tracer of every sheet agrees
+    sim->per_q = false;
+    {
+        int64_t base = 0;
+        for (int s = 0; s < sim->M && !sim->per_q; ++s) {
+            for (int i = 1; i < sim->counts[s]; ++i)
+                if (w_host[base + i] != w_host[base]) {
+                    sim->per_q = true;
+                    break;
+                }
+            base += sim->counts[s];
+        }
+    }
+    sim->sigma = choose_sigma(max_w);
+    sim->sheet_qh.assign(sim->M, 0);
+    {
+        int64_t base = 0;
+        for (int s = 0; s < sim->M; ++s) {
+            sim->sheet_qh[s] = (int32_t)std::llround(w_host[base] * sim->sigma * 0.5);
+            base += sim->counts[s];
+        }
+    }
+    rc = setup(sim, cfg);
+    if (rc) {
+        sic_destroy(sim);
+        return rc;
+    }
+    {
+        std::vector<int64_t> U(sim->n_alloc, 0);
+        std::vector<float> V(sim->n_alloc, 0.f);
+        std::vector<int32_t> Q(sim->per_q ? sim->n_alloc : 0, 0);
+        const double vscale = cfg->dt / dx;
+        int64_t base = 0;
+        for (int s = 0; s < sim->M; ++s) {
+            const int64_t o = sim->sheet_off[s];
+            for (int i = 0; i < sim->counts[s]; ++i) {
+                U[o + i] = to_fixed(x_host[base + i] / dx);
+                V[o + i] = (float)(v_host[base + i] * vscale);
+                if (sim->per_q)
+                    Q[o + i] = (int32_t)std::llround(w_host[base + i] * sim->sigma * 0.5);
+            }
+            base += sim->counts[s];
+        }
+        cudaError_t e = cudaMemcpyAsync(sim->h.U, U.data(), 8 * U.size(), cudaMemcpyHostToDevice, sim->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sim->h.V, V.data(), 4 * V.size(), cudaMemcpyHostToDevice, sim->stream);
+        if (e == cudaSuccess && sim->per_q)
+            e = cudaMemcpyAsync((void *)sim->h.Qh, Q.data(), 4 * Q.size(), cudaMemcpyHostToDevice, sim->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(sim->stream);
+        if (e != cudaSuccess) {
+            sic_destroy(sim);
+            return SIC_ECUDA;
+        }
+    }
+    rc = initialise(sim);
+    if (rc) {
+        sic_destroy(sim);
+        return rc;
+    }
+    *out = sim;
+    return SIC_OK;
+}
+
+int sic_create_horizontal(const sic_config *cfg, int32_t n_template, const double *x_template_host,
+                          const double *v_sheet_host, const double *w_sheet_host, sic_sim **out)
+{
+    if (!out)
+        return SIC_EINVAL;
+    *out = nullptr;
+    int rc = validate(cfg, false);
+    if (rc)
+        return rc;
+    if (n_template < 2 || !x_template_host || !v_sheet_host || !w_sheet_host)
+        return SIC_EINVAL;
+    if ((int64_t)n_template * cfg->n_sheets > SIC_TRACERS_MAX)
+        return SIC_EINVAL;
+    const double dx = cfg->box_length / cfg->nx;
+    for (int i = 0; i < n_template; ++i) {
+        if (!is_finite(x_template_host[i]))
+            return SIC_EINVAL;
+        if (std::fabs(x_template_host[i] / dx) >= (double)(1 << 29))
+            return SIC_ERANGE;
+    }
+    double max_w = 0;
+    for (int s = 0; s < cfg->n_sheets; ++s) {
+        if (!is_finite(v_sheet_host[s]) || !is_finite(w_sheet_host[s]) || w_sheet_host[s] <= 0)
+            return SIC_EINVAL;
+        if (std::fabs(v_sheet_host[s] * cfg->dt / dx) >= (double)(1 << 20))
+            return SIC_EINVAL;
+        max_w = std::max(max_w, w_sheet_host[s]);
+    }
+    sic_sim *sim = new (std::nothrow) sic_sim;
+    if (!sim)
+        return SIC_ENOMEM;
+    sim->M = cfg->n_sheets;
+    sim->counts.assign(sim->M, n_template);
+    sim->closed.assign(sim->M, 1);
+    sim->winding.assign(sim->M, 1);
+    sim->n_tracers = (int64_t)n_template * sim->M;
+    sim->per_q = false;
+    sim->sigma = choose_sigma(max_w);
+    sim->sheet_qh.assign(sim->M, 0);
+    for (int s = 0; s < sim->M; ++s)
+        sim->sheet_qh[s] = (int32_t)std::llround(w_sheet_host[s] * sim->sigma * 0.5);
+    rc = setup(sim, cfg);
+    if (rc) {
+        sic_destroy(sim);
+        return rc;
+    }
+    std::vector<int64_t> ut(n_template);
+    for (int i = 0; i < n_template; ++i)
+        ut[i] = to_fixed(x_template_host[i] / dx);
+    std::vector<float> vs(sim->M);
+    for (int s = 0; s < sim->M; ++s)
+        vs[s] = (float)(v_sheet_host[s] * cfg->dt / dx);
+    void *tmp = nullptr;
+    const size_t bytes = 8 * (size_t)n_template + 8 * (size_t)sim->M + 4 * (size_t)sim->M + 64;
+    cudaError_t e = cudaMallocAsync(&tmp, bytes, sim->stream);
+    if (e == cudaSuccess) {
+        char *t = (char *)tmp;
+        int64_t *d_ut = (int64_t *)t;
+        int64_t *d_off = (int64_t *)(t + 8 * (size_t)n_template);
+        float *d_vs = (float *)(t + 8 * (size_t)n_template + 8 * (size_t)sim->M);
+        e = cudaMemcpyAsync(d_ut, ut.data(), 8 * ut.size(), cudaMemcpyHostToDevice, sim->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_off, sim->sheet_off.data(), 8 * sim->sheet_off.size(), cudaMemcpyHostToDevice,
+                                sim->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_vs, vs.data(), 4 * vs.size(), cudaMemcpyHostToDevice, sim->stream);
+        if (e == cudaSuccess)
+            e = launch_expand_horizontal(sim->h.U, sim->h.V, d_ut, n_template, d_vs, d_off, sim->M, sim->stream);
+        cudaError_t e2 = cudaFreeAsync(tmp, sim->stream);
+        if (e == cudaSuccess)
+            e = e2;
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(sim->stream);
+    }
+    if (e != cudaSuccess) {
+        sic_destroy(sim);
+        return e == cudaErrorMemoryAllocation ? SIC_ENOMEM : SIC_ECUDA;
+    }
+    rc = initialise(sim);
+    if (rc) {
+        sic_destroy(sim);
+        return rc;
+    }
+    *out = sim;
+    return SIC_OK;
+}
+
+int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host)
+{
+    if (!sim)
+        return SIC_EINVAL;
+    CK(launch_deposit_field(sim));
+    if (mesh_fixed_host)
+        CK(cudaMemcpyAsync(mesh_fixed_host, sim->h.mesh_last, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost,
+                           sim->stream));
+    if (rho_host)
+        CK(cudaMemcpyAsync(rho_host, sim->h.rho64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
+    return check_device_errors(sim);
+}
+
+int sic_field(sic_sim *sim, double *E_host)
+{
+    if (!sim || !E_host)
+        return SIC_EINVAL;
+    CK(cudaMemcpyAsync(E_host, sim->h.E64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
+    return check_device_errors(sim);
+}
+
+int sic_push(sic_sim *sim)
+{
+    if (!sim)
+        return SIC_EINVAL;
+    CK(launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, false, sim->per_q, 1.0f,
+                           1, sim->stream));
+    return SIC_OK;
+}
+
+int sic_step(sic_sim *sim, int32_t n_steps)
+{
+    if (!sim || n_steps < 0)
+        return SIC_EINVAL;
+    if (n_steps >= kGraphSteps && !sim->gexec) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i)
+            e = launch_step(sim);
+        cudaError_t e2 = cudaStreamEndCapture(sim->stream, &g);
+        if (e != cudaSuccess)
+            return fail_cuda(sim, e);
+        CK(e2);
+        e = cudaGraphInstantiate(&sim->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        // the captured launches were counted at capture time; undo that
+        count_launches(-2 * kGraphSteps);
+    }
+    int32_t left = n_steps;
+    while (left >= kGraphSteps && sim->gexec) {
+        CK(cudaGraphLaunch(sim->gexec, sim->stream));
+        count_launches(2 * kGraphSteps);
+        left -= kGraphSteps;
+    }
+    for (; left > 0; --left)
+        CK(launch_step(sim));
+    sim->steps_done += n_steps;
+    return SIC_OK;
+}
+
+int sic_step_phase(sic_sim *sim, int32_t phase)
+{
+    if (!sim || (phase != 1 && phase != 2))
+        return SIC_EINVAL;
+    if (phase == 1)
+        CK(launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, true, sim->per_q,
+                               1.0f, 1, sim->stream));
+    else {
+        CK(launch_field(sim->d_desc, sim->d_job, 1, sim->nx, 1, sim->stream));
+        sim->steps_done += 1;
+    }
+    return SIC_OK;
+}
+
+int sic_step_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)
+{
+    if (!sims || n_sims < 1 || !n_steps)
+        return SIC_EINVAL;
+    for (int i = 0; i < n_sims; ++i) {
+        if (!sims[i] || n_steps[i] < 0)
+            return SIC_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (sims[k] == sims[i])
+                return SIC_EINVAL;
+    }
+    sic_sim *sim = sims[0];
+    cudaStream_t bs = sim->stream;
+    // order the batch stream after every member's stream
+    std::vector<cudaEvent_t> ev;
+    for (int i = 1; i < n_sims; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ev.push_back(e);
+        CK(cudaEventRecord(e, sims[i]->stream));
+        CK(cudaStreamWaitEvent(bs, e, 0));
+    }
+    std::vector<int32_t> left(n_steps, n_steps + n_sims);
+    std::vector<int> active;
+    for (int i = 0; i < n_sims; ++i)
+        if (left[i] > 0)
+            active.push_back(i);
+    const int sms = num_sms();
+    while (!active.empty()) {
+        int32_t k = INT32_MAX;
+        int nx_max = 2;
+        for (int i : active) {
+            k = std::min(k, left[i]);
+            nx_max = std::max(nx_max, sims[i]->nx);
+        }
+        std::vector<SimDev> table;
+        std::vector<WorkItem> items;
+        std::vector<FieldJob> jobs;
+        for (int slot = 0; slot < (int)active.size(); ++slot) {
+            sic_sim *s = sims[active[slot]];
+            table.push_back(s->h);
+            for (WorkItem w : s->items) {
+                w.sim = slot;
+                items.push_back(w);
+            }
+            jobs.push_back(FieldJob{slot, 0});
+        }
+        // per-tracer and per-sheet charge take different kernel variants
+        std::vector<WorkItem> items_q, items_u;
+        for (const WorkItem &w : items)
+            (sims[active[w.sim]]->per_q ? items_q : items_u).push_back(w);
+        int per_sm_u = std::max(1, k1_blocks_per_sm(nx_max, true, true, false));
+        int per_sm_q = std::max(1, k1_blocks_per_sm(nx_max, true, true, true));
+        int grid_u = items_u.empty() ? 0 : std::max(1, std::min((int)items_u.size(), sms * per_sm_u));
+        int grid_q = items_q.empty() ? 0 : std::max(1, std::min((int)items_q.size(), sms * per_sm_q));
+        std::vector<int32_t> cta_u = grid_u ? partition(items_u, grid_u) : std::vector<int32_t>();
+        std::vector<int32_t> cta_q = grid_q ? partition(items_q, grid_q) : std::vector<int32_t>();
+        Layout lay;
+        const size_t oT = lay.take(sizeof(SimDev) * table.size());
+        const size_t oIu = lay.take(sizeof(WorkItem) * items_u.size());
+        const size_t oIq = lay.take(sizeof(WorkItem) * items_q.size());
+        const size_t oCu = lay.take(4 * cta_u.size());
+        const size_t oCq = lay.take(4 * cta_q.size());
+        const size_t oJ = lay.take(sizeof(FieldJob) * jobs.size());
+        void *buf = nullptr;
+        CK(cudaMallocAsync(&buf, lay.off, bs));
+        char *b = (char *)buf;
+        CK(cudaMemcpyAsync(b + oT, table.data(), sizeof(SimDev) * table.size(), cudaMemcpyHostToDevice, bs));
+        if (!items_u.empty()) {
+            CK(cudaMemcpyAsync(b + oIu, items_u.data(), sizeof(WorkItem) * items_u.size(), cudaMemcpyHostToDevice,
+                               bs));
+            CK(cudaMemcpyAsync(b + oCu, cta_u.data(), 4 * cta_u.size(), cudaMemcpyHostToDevice, bs));
+        }
+        if (!items_q.empty()) {
+            CK(cudaMemcpyAsync(b + oIq, items_q.data(), sizeof(WorkItem) * items_q.size(), cudaMemcpyHostToDevice,
+                               bs));
+            CK(cudaMemcpyAsync(b + oCq, cta_q.data(), 4 * cta_q.size(), cudaMemcpyHostToDevice, bs));
+        }
+        CK(cudaMemcpyAsync(b + oJ, jobs.data(), sizeof(FieldJob) * jobs.size(), cudaMemcpyHostToDevice, bs));
+        const SimDev *d_table = (const SimDev *)(b + oT);
+        for (int32_t st = 0; st < k; ++st) {
+            if (grid_u)
+                CK(launch_push_deposit(d_table, (const WorkItem *)(b + oIu), (const int32_t *)(b + oCu), grid_u,
+                                       nx_max, true, true, false, 1.0f, 1, bs));
+            if (grid_q)
+                CK(launch_push_deposit(d_table, (const WorkItem *)(b + oIq), (const int32_t *)(b + oCq), grid_q,
+                                       nx_max, true, true, true, 1.0f, 1, bs));
+            CK(launch_field(d_table, (const FieldJob *)(b + oJ), (int)jobs.size(), nx_max, 1, bs));
+        }
+        CK(cudaFreeAsync(buf, bs));
+        // host copies are pageable: wait before they go out of scope
+        CK(cudaStreamSynchronize(bs));
+        std::vector<int> next;
+        for (int i : active) {
+            left[i] -= k;
+            sims[i]->steps_done += k;
+            if (left[i] > 0)
+                next.push_back(i);
+        }
+        active.swap(next);
+    }
+    cudaEvent_t done;
+    CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    CK(cudaEventRecord(done, bs));
+    for (int i = 1; i < n_sims; ++i)
+        CK(cudaStreamWaitEvent(sims[i]->stream, done, 0));
+    cudaEventDestroy(done);
+    for (cudaEvent_t e : ev)
+        cudaEventDestroy(e);
+    return SIC_OK;
+}
+
+int sic_diagnostics(sic_sim *sim, sic_diag *out)
+{
+    if (!sim || !out)
+        return SIC_EINVAL;
+    int rc = check_device_errors(sim);
+    if (rc)
+        return rc;
+    SimScalars sc;
+    CK(cudaMemcpy(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    out->step = sc.step;
+    out->t = (double)sc.step * sim->dt;
+    out->field_energy = sc.we;
+    out->kinetic_energy = NAN;
+    out->momentum = NAN;
+    if (sc.step > 0) {
+        double row[4];
+        const int64_t r = (sc.step - 1) % sim->hist_len;
+        CK(cudaMemcpy(row, sim->h.hist + 4 * r, sizeof(row), cudaMemcpyDeviceToHost));
+        out->kinetic_energy = row[1];
+        out->momentum = row[2];
+    }
+    out->charge_fixed = sc.q_total;
+    out->charge_unit = 1.0 / sim->sigma;
+    out->max_segment = (double)sc.maxseg / kTwo32 / (double)sim->nx;
+    return SIC_OK;
+}
+
+int sic_history(sic_sim *sim, double *hist_host, int32_t *rows)
+{
+    if (!sim || !hist_host || !rows)
+        return SIC_EINVAL;
+    int rc = check_device_errors(sim);
+    if (rc)
+        return rc;
+    SimScalars sc;
+    CK(cudaMemcpy(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    const int64_t n = std::min<int64_t>(sc.step, sim->hist_len);
+    std::vector<double> ring(4 * (size_t)sim->hist_len);
+    CK(cudaMemcpy(ring.data(), sim->h.hist, 8 * ring.size(), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t step = sc.step - n + i;
+        std::memcpy(hist_host + 4 * i, ring.data() + 4 * (step % sim->hist_len), 32);
+    }
+    *rows = (int32_t)n;
+    return SIC_OK;
+}
+
+int sic_get_state(sic_sim *sim, double *x_host, double *v_host)
+{
+    if (!sim)
+        return SIC_EINVAL;
+    int rc = check_device_errors(sim);
+    if (rc)
+        return rc;
+    std::vector<int64_t> U(sim->n_alloc);
+    std::vector<float> V(sim->n_alloc);
+    CK(cudaMemcpy(U.data(), sim->h.U, 8 * U.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(V.data(), sim->h.V, 4 * V.size(), cudaMemcpyDeviceToHost));
+    const double xs = sim->dx / kTwo32, vs = sim->dx / sim->dt;
+    int64_t base = 0;
+    for (int s = 0; s < sim->M; ++s) {
+        const int64_t o = sim->sheet_off[s];
+        for (int i = 0; i < sim->counts[s]; ++i) {
+            if (x_host)
+                x_host[base + i] = (double)U[o + i] * xs;
+            if (v_host)
+                v_host[base + i] = (double)V[o + i] * vs;
+        }
+        base += sim->counts[s];
+    }
+    return SIC_OK;
+}
+
+int sic_device_state(sic_sim *sim, int64_t **pos_dev, float **vel_dev, const int64_t **sheet_offset_host)
+{
+    if (!sim)
+        return SIC_EINVAL;
+    if (pos_dev)
+        *pos_dev = sim->h.U;
+    if (vel_dev)
+        *vel_dev = sim->h.V;
+    if (sheet_offset_host)
+        *sheet_offset_host = sim->sheet_off.data();
+    return SIC_OK;
+}
+
+int sic_sync(sic_sim *sim)
+{
+    if (!sim)
+        return SIC_EINVAL;
+    return check_device_errors(sim);
+}
+
+void sic_destroy(sic_sim *sim)
+{
+    if (!sim)
+        return;
+    if (sim->stream)
+        cudaStreamSynchronize(sim->stream);
+    if (sim->gexec)
+        cudaGraphExecDestroy(sim->gexec);
+    if (sim->dmem) {
+        cudaFreeAsync(sim->dmem, sim->stream);
+        cudaStreamSynchronize(sim->stream);
+    }
+    if (sim->own_stream && sim->stream)
+        cudaStreamDestroy(sim->stream);
+    delete sim;
+}
+
+const char *sic_strerror(int code)
+{
+    switch (code) {
+    case SIC_OK:
+        return "ok";
+    case SIC_EINVAL:
+        return "invalid argument";
+    case SIC_ENOMEM:
+        return "out of memory";
+    case SIC_ECUDA:
+        return "CUDA error";
+    case SIC_ERANGE:
+        return "position outside the fixed-point range";
+    case SIC_ESEGMENT_LONG:
+        return "segment longer than the box";
+    case SIC_ETIMEOUT:
+        return "device wait timed out";
+    case SIC_EBUSY:
+        return "no capacity";
+    default:
+        return "unknown error";
+    }
+}
+
+int64_t sic_launch_count(void) { return sic::launches(); }
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+"""ctypes binding of the SIC C ABI (include/sic.h), same names, argument marshalling only.
+
+Importing this module loads ``_build/libsic.so``; it raises ImportError when
+the library has not been built: there is no CPU fallback.  Every step of the
+path runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsic.so")
+
+SIC_OK = 0
+SIC_EINVAL = -1
+SIC_ENOMEM = -2
+SIC_ECUDA = -3
+SIC_ERANGE = -4
+SIC_ESEGMENT_LONG = -5
+SIC_ETIMEOUT = -6
+SIC_EBUSY = -7
+SIC_NX_MAX = 8192
+
+# every symbol include/sic.h declares
+EXPORTS = [
+    "sic_create", "sic_create_horizontal", "sic_deposit", "sic_field", "sic_push", "sic_step",
+    "sic_step_phase", "sic_step_batch", "sic_diagnostics", "sic_history", "sic_get_state", "sic_device_state",
+    "sic_sync", "sic_destroy", "sic_strerror", "sic_launch_count",
+]
+
+
+class sic_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("box_length", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("n_sheets", ctypes.c_int32),
+        ("tracers_per_sheet", ctypes.POINTER(ctypes.c_int32)),
+        ("sheet_closed", ctypes.POINTER(ctypes.c_uint8)),
+        ("sheet_winding", ctypes.POINTER(ctypes.c_int32)),
+        ("charge_to_mass", ctypes.c_double),
+        ("half_step_init", ctypes.c_int32),
+        ("strict_segments", ctypes.c_int32),
+        ("history_len", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class sic_diag(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64),
+        ("t", ctypes.c_double),
+        ("field_energy", ctypes.c_double),
+        ("kinetic_energy", ctypes.c_double),
+        ("momentum", ctypes.c_double),
+        ("charge_fixed", ctypes.c_int64),
+        ("charge_unit", ctypes.c_double),
+        ("max_segment", ctypes.c_double),
+    ]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"SIC CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    dp, ip, lp, vp = P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int64), ctypes.c_void_p
+    simp = vp
+    sig = {
+        "sic_create": ([P(sic_config), dp, dp, dp, P(simp)], ctypes.c_int),
+        "sic_create_horizontal": ([P(sic_config), ctypes.c_int32, dp, dp, dp, P(simp)], ctypes.c_int),
+        "sic_deposit": ([simp, lp, dp], ctypes.c_int),
+        "sic_field": ([simp, dp], ctypes.c_int),
+        "sic_push": ([simp], ctypes.c_int),
+        "sic_step": ([simp, ctypes.c_int32], ctypes.c_int),
+        "sic_step_phase": ([simp, ctypes.c_int32], ctypes.c_int),
+        "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
+        "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
+        "sic_history": ([simp, dp, ip], ctypes.c_int),
+        "sic_get_state": ([simp, dp, dp], ctypes.c_int),
+        "sic_device_state": ([simp, P(vp), P(vp), P(vp)], ctypes.c_int),
+        "sic_sync": ([simp], ctypes.c_int),
+        "sic_destroy": ([simp], None),
+        "sic_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "sic_launch_count": ([], ctypes.c_int64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = load_library()
+
+
+class SicError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_lib.sic_strerror(code).decode()} ({code})")
+
+
+def _check(code: int, what: str):
+    if code != SIC_OK:
+        raise SicError(code, what)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def sic_strerror(code: int) -> str:
+    return _lib.sic_strerror(code).decode()
+
+
+def sic_launch_count() -> int:
+    return int(_lib.sic_launch_count())
+
+
+def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
+            half_step_init=True, strict=False, history_len=1, stream=None):
+    cfg = sic_config()
+    cfg.nx = int(nx)
+    cfg.box_length = float(L)
+    cfg.dt = float(dt)
+    cfg.n_sheets = int(n_sheets)
+    keep = []
+    if counts is not None:
+        c = np.ascontiguousarray(counts, dtype=np.int32)
+        cl = np.ascontiguousarray(closed, dtype=np.uint8)
+        wd = np.ascontiguousarray(winding if winding is not None else np.zeros(n_sheets), dtype=np.int32)
+        keep += [c, cl, wd]
+        cfg.tracers_per_sheet = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        cfg.sheet_closed = cl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        cfg.sheet_winding = wd.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    cfg.charge_to_mass = float(qm)
+    cfg.half_step_init = int(bool(half_step_init))
+    cfg.strict_segments = int(bool(strict))
+    cfg.history_len = int(history_len)
+    cfg.stream = ctypes.c_void_p(int(stream) if stream else 0)
+    return cfg, keep
+
+
+class Sim:
+    """One simulation held on the GPU (wraps a ``sic_sim*``)."""
+
+    def __init__(self, handle, nx, n_tracers, counts):
+        self._h = handle
+        self.nx = int(nx)
+        self.n_tracers = int(n_tracers)
+        self.counts = np.asarray(counts, dtype=np.int64)
+
+    # -- construction -------------------------------------------------------
+    @classmethod
+    def sic_create(cls, nx, L, dt, counts, closed, winding, x, v, w, qm=1.0, half_step_init=True,
+                   strict=False, history_len=1, stream=None):
+        counts = np.ascontiguousarray(counts, dtype=np.int32)
+        cfg, keep = _config(nx, L, dt, counts.size, counts, closed, winding, qm, half_step_init,
+                            strict, history_len, stream)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        n = int(counts.sum())
+        if x.size != n or v.size != n or w.size != n:
+            raise ValueError("x, v and w need one entry per tracer")
+        h = ctypes.c_void_p()
+        _check(_lib.sic_create(ctypes.byref(cfg), _dptr(x), _dptr(v), _dptr(w), ctypes.byref(h)),
+               "sic_create")
+        return cls(h, nx, n, counts)
+
+    @classmethod
+    def sic_create_horizontal(cls, nx, L, dt, x_template, v_sheet, w_sheet, qm=1.0,
+                              half_step_init=True, strict=False, history_len=1, stream=None):
+        xt = np.ascontiguousarray(x_template, dtype=np.float64)
+        vs = np.ascontiguousarray(v_sheet, dtype=np.float64)
+        ws = np.ascontiguousarray(w_sheet, dtype=np.float64)
+        if vs.shape != ws.shape:
+            raise ValueError("v_sheet and w_sheet need one entry per sheet")
+        cfg, keep = _config(nx, L, dt, vs.size, None, None, None, qm, half_step_init, strict,
+                            history_len, stream)
+        h = ctypes.c_void_p()
+        _check(_lib.sic_create_horizontal(ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs), _dptr(ws),
+                                          ctypes.byref(h)), "sic_create_horizontal")
+        return cls(h, nx, xt.size * vs.size, np.full(vs.size, xt.size))
+
+    @classmethod
+    def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None):
+        """Create from an ``inputs.Problem`` (compact form when it has one)."""
+        hl = history_len if history_len is not None else max(1, p.n_steps)
+        if horizontal is None:
+            horizontal = p.is_horizontal
+        if horizontal:
+            return cls.sic_create_horizontal(p.nx, p.L, p.dt, p.x_template, p.v_sheet, p.w_sheet,
+                                             qm=p.qm, half_step_init=p.half_step_init, strict=strict,
+                                             history_len=hl, stream=stream)
+        return cls.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
+                              qm=p.qm, half_step_init=p.half_step_init, strict=strict,
+                              history_len=hl, stream=stream)
+
+    # -- the C ABI, one method per entry point ------------------------------
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("simulation destroyed")
+        return self._h
+
+    def sic_deposit(self):
+        mesh = np.zeros(self.nx, dtype=np.int64)
+        rho = np.zeros(self.nx, dtype=np.float64)
+        _check(_lib.sic_deposit(self.handle, mesh.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                _dptr(rho)), "sic_deposit")
+        return mesh, rho
+
+    def sic_field(self):
+        E = np.zeros(self.nx, dtype=np.float64)
+        _check(_lib.sic_field(self.handle, _dptr(E)), "sic_field")
+        return E
+
+    def sic_push(self):
+        _check(_lib.sic_push(self.handle), "sic_push")
+
+    def sic_step(self, n_steps: int):
+        _check(_lib.sic_step(self.handle, int(n_steps)), "sic_step")
+
+    def sic_step_phase(self, phase: int):
+        _check(_lib.sic_step_phase(self.handle, int(phase)), "sic_step_phase")
+
+    def sic_diagnostics(self) -> dict:
+        d = sic_diag()
+        _check(_lib.sic_diagnostics(self.handle, ctypes.byref(d)), "sic_diagnostics")
+        return {name: getattr(d, name) for name, _ in sic_diag._fields_}
+
+    def sic_history(self, history_len: int):
+        buf = np.zeros((history_len, 4), dtype=np.float64)
+        rows = ctypes.c_int32()
+        _check(_lib.sic_history(self.handle, _dptr(buf), ctypes.byref(rows)), "sic_history")
+        return buf[: rows.value]
+
+    def sic_get_state(self):
+        x = np.zeros(self.n_tracers, dtype=np.float64)
+        v = np.zeros(self.n_tracers, dtype=np.float64)
+        _check(_lib.sic_get_state(self.handle, _dptr(x), _dptr(v)), "sic_get_state")
+        return x, v
+
+    def sic_device_state(self):
+        """(positions int64*, velocities float*, sheet offsets) as integer addresses."""
+        pu, pv, po = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(_lib.sic_device_state(self.handle, ctypes.byref(pu), ctypes.byref(pv),
+                                     ctypes.byref(po)), "sic_device_state")
+        offs = np.ctypeslib.as_array(ctypes.cast(po, ctypes.POINTER(ctypes.c_int64)),
+                                     shape=(self.counts.size,)).copy()
+        return pu.value, pv.value, offs
+
+    def sic_sync(self):
+        _check(_lib.sic_sync(self.handle), "sic_sync")
+
+    def sic_destroy(self):
+        if self._h is not None:
+            _lib.sic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.sic_destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.sic_destroy()
+
+
+def sic_step_batch(sims, n_steps):
+    arr = (ctypes.c_void_p * len(sims))(*[s.handle for s in sims])
+    steps = np.ascontiguousarray(n_steps, dtype=np.int32)
+    if steps.size != len(sims):
+        raise ValueError("one step count per simulation")
+    _check(_lib.sic_step_batch(arr, len(sims), steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "sic_step_batch")

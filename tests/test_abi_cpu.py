@@ -1,0 +1,91 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports every
+symbol include/sic.h declares, and rejects bad input before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sic.h")
+
+
+@pytest.fixture(scope="module")
+def sic():
+    from paper_1506_07207_gb300 import build
+    build.build()
+    from paper_1506_07207_gb300 import sic as binding
+    return binding
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sic_[a-z_]+)\s*\(", text)))
+
+
+def test_header_symbols_are_exported(sic):
+    names = _declared()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(sic.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(sic.EXPORTS) == names
+
+
+def test_library_is_built_for_sm103a(sic):
+    # the fatbinary names its target; no other architecture is embedded
+    blob = open(sic.LIB_PATH, "rb").read()
+    assert b"sm_103a" in blob
+
+
+def test_strerror(sic):
+    assert sic.sic_strerror(0) == "ok"
+    for code in range(-7, 0):
+        assert sic.sic_strerror(code) not in ("ok", "unknown error")
+    assert sic.sic_strerror(-99) == "unknown error"
+
+
+def _base(**kw):
+    args = dict(nx=8, L=1.0, dt=0.1, counts=[4], closed=[1], winding=[1],
+                x=np.arange(4) / 4.0, v=np.zeros(4), w=np.full(4, 0.25))
+    args.update(kw)
+    return args
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=1), dict(nx=8193), dict(L=0.0), dict(L=float("nan")), dict(dt=-1.0),
+    dict(counts=[1], x=[0.0], v=[0.0], w=[1.0]),
+    dict(x=np.array([0.0, float("inf"), 0.5, 0.7])),
+    dict(v=np.array([0.0, float("nan"), 0.0, 0.0])),
+    dict(w=np.array([0.25, 0.0, 0.25, 0.25])),
+    dict(w=np.array([0.25, -1.0, 0.25, 0.25])),
+])
+def test_invalid_input_is_rejected(sic, bad):
+    a = _base(**bad)
+    with pytest.raises(sic.SicError) as e:
+        sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                           a["x"], a["v"], a["w"])
+    assert e.value.code == sic.SIC_EINVAL
+
+
+def test_position_out_of_fixed_point_range(sic):
+    a = _base(x=np.array([0.0, 0.25, 0.5, 2.0 ** 27]))   # 2^30 cells
+    with pytest.raises(sic.SicError) as e:
+        sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                           a["x"], a["v"], a["w"])
+    assert e.value.code == sic.SIC_ERANGE
+
+
+def test_bad_config_fields(sic):
+    a = _base()
+    for kw in (dict(qm=0.0), dict(history_len=0), dict(qm=float("inf"))):
+        with pytest.raises(sic.SicError) as e:
+            sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                               a["x"], a["v"], a["w"], **kw)
+        assert e.value.code == sic.SIC_EINVAL
+    with pytest.raises(sic.SicError):
+        sic.Sim.sic_create_horizontal(8, 1.0, 0.1, [0.0], [0.0], [1.0])   # one tracer
+    with pytest.raises(sic.SicError):
+        sic.Sim.sic_create_horizontal(8, 1.0, 0.1, [0.0, 0.5], [0.0], [-1.0])
