@@ -182,6 +182,8 @@ def main():
     ap.add_argument("--workload", default="two_stream")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--e2e-runs", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -259,9 +261,9 @@ def main():
 
     # end to end through the C ABI: host arrays in, a full run, state out
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         x, v, w = p.x, p.v, p.w
-        e2e_steps = p.n_steps
+        e2e_steps = args.e2e_steps
         times = []
         for _ in range(args.e2e_runs):
             torch.cuda.synchronize()
