@@ -134,14 +134,11 @@ int sic_field(sic_sim *sim, double *E_host);
 /* Gather, kick and drift every tracer with the current field; no deposit. */
 int sic_push(sic_sim *sim);
 
-/* n_steps full steps: fused gather-kick-drift-deposit, then the field solve. */
+/* n_steps full steps; each is one kernel launch: fused gather-kick-drift-deposit
+ * over every segment, then the field solve by the block that finishes last.
+ * Asynchronous on the simulation's stream: errors found on the device are
+ * returned by the next synchronising call (sic_sync, sic_diagnostics, ...). */
 int sic_step(sic_sim *sim, int32_t n_steps);
-
-/* One of the two kernels of a step: phase 1 = fused gather-kick-drift-deposit,
- * phase 2 = seams, field solve and history row.  Phase 1 then phase 2 equals
- * sic_step(sim, 1); callers use it to interleave their own work or to time
- * the phases on the simulation's stream. */
-int sic_step_phase(sic_sim *sim, int32_t phase);
 
 /* Advance several simulations together, n_steps[i] steps each; the work of
  * all of them shares each kernel launch.  Results equal separate sic_step

@@ -1,10 +1,10 @@
 // sic_api.cu -- host runtime behind the C ABI of include/sic.h.
 //
 // Owns each simulation's device memory (one stream-ordered allocation), the
-// work-item plan (consecutive tracers of one sheet per item, balanced over a
-// persistent grid of SMs x resident blocks), CUDA-graph capture of the
-// per-step kernel pair, and batching of several simulations into shared
-// launches.
+// work-item plan (up to 256 consecutive tracers of one sheet per item, one
+// warp's task; contiguous runs of items per block, balanced over a
+// persistent grid of SMs x resident blocks), CUDA-graph capture of the step kernel, and
+// batching of several simulations into shared launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,8 +22,8 @@ using namespace sic;
 
 namespace {
 
-constexpr int kGraphSteps = 8;      // steps captured in one graph
-constexpr int kItemCost = 256;      // fixed cost of a work item, in tracer units
+constexpr int kGraphSteps = 8;  // steps captured in one graph
+constexpr int kItemCost = 16;   // fixed cost of a work item, in tracer units
 constexpr double kTwo32 = 4294967296.0;
 
 struct Layout {
@@ -70,6 +70,47 @@ int64_t to_fixed(double xc)
 
 bool is_finite(double x) { return std::isfinite(x); }
 
+// Test knob: SIC_GRID overrides the block count of the step kernel.  It does
+// not change any result: the mesh is an integer sum and every reduction runs
+// in a fixed order independent of the blocks.
+int env_int(const char *name, int dflt)
+{
+    const char *v = std::getenv(name);
+    if (!v || !*v)
+        return dflt;
+    const int x = std::atoi(v);
+    return x > 0 ? x : dflt;
+}
+
+// Device-side launch plan: table of simulations, items, block ranges, tickets.
+struct Plan {
+    void *mem = nullptr;
+    LaunchArgs args{};
+    int grid = 0;
+    bool per_q = false;
+    bool pow2 = false;
+};
+
+// Contiguous runs of items per block, balanced by tracer count.
+std::vector<int32_t> partition(const std::vector<WorkItem> &items, int grid)
+{
+    const int n = (int)items.size();
+    std::vector<int64_t> start(n + 1, 0);
+    for (int i = 0; i < n; ++i)
+        start[i + 1] = start[i] + items[i].count + kItemCost;
+    const int64_t total = start[n];
+    std::vector<int32_t> cta(grid + 1);
+    int i = 0;
+    for (int b = 0; b <= grid; ++b) {
+        const int64_t target = (int64_t)((__int128)total * b / grid);
+        while (i < n && start[i] < target)
+            ++i;
+        cta[b] = i;
+    }
+    cta[grid] = n;
+    return cta;
+}
+
 }  // namespace
 
 struct sic_sim {
@@ -86,17 +127,12 @@ struct sic_sim {
     int64_t n_tracers = 0, n_alloc = 0;
     double sigma = 1.0;
     std::vector<WorkItem> items;
-    int grid = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *dmem = nullptr;
     SimDev h{};
-    SimDev *d_desc = nullptr;
-    WorkItem *d_items = nullptr;
-    int32_t *d_cta = nullptr;
-    FieldJob *d_job = nullptr;
+    Plan plan;
     cudaGraphExec_t gexec = nullptr;
-    int64_t steps_done = 0;
     cudaError_t last = cudaSuccess;
 };
 
@@ -106,7 +142,7 @@ int fail_cuda(sic_sim *s, cudaError_t e)
 {
     if (s)
         s->last = e;
-    return SIC_ECUDA;
+    return e == cudaErrorMemoryAllocation ? SIC_ENOMEM : SIC_ECUDA;
 }
 
 #define CK(call)                                  \
@@ -147,26 +183,14 @@ int validate(const sic_config *c, bool need_sheets)
     return SIC_OK;
 }
 
-// Test knobs: SIC_ITEM_TILES (tiles per work item, default 1) and SIC_GRID
-// (blocks of the deposit kernel).  Neither changes any result: the mesh is an
-// integer sum and every per-item reduction runs in a fixed order.
-int env_int(const char *name, int dflt)
-{
-    const char *v = std::getenv(name);
-    if (!v || !*v)
-        return dflt;
-    const int x = std::atoi(v);
-    return x > 0 ? x : dflt;
-}
-
-// Split every sheet into items of at most SIC_ITEM_TILES tiles, link the seams.
+// Split every sheet into items of at most 256 tracers (one warp's task);
+// each item knows the tracer after its last one (its halo).
 void plan_items(sic_sim *sim)
 {
-    const int item = SIC_K1_TILE * env_int("SIC_ITEM_TILES", 1);
+    const int item = SIC_K1_WARP_TRACERS;
     sim->items.clear();
     for (int s = 0; s < sim->M; ++s) {
         const int n = sim->counts[s];
-        const int first = (int)sim->items.size();
         for (int k = 0; k * item < n; ++k) {
             WorkItem w{};
             w.sim = 0;
@@ -174,71 +198,122 @@ void plan_items(sic_sim *sim)
             w.t0 = sim->sheet_off[s] + (int64_t)k * item;
             w.count = std::min(item, n - k * item);
             w.qh = sim->per_q ? 0 : sim->sheet_qh[s];
-            w.seam_next = -1;
-            w.seam_shift = 0;
+            const bool last = (k + 1) * item >= n;
+            if (!last) {
+                w.halo = w.t0 + w.count;
+                w.halo_shift = 0;
+            } else if (sim->closed[s]) {
+                w.halo = sim->sheet_off[s];
+                w.halo_shift = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
+            } else {
+                w.halo = -1;
+                w.halo_shift = 0;
+            }
             sim->items.push_back(w);
         }
-        const int last = (int)sim->items.size() - 1;
-        for (int i = first; i < last; ++i)
-            sim->items[i].seam_next = i + 1;
-        if (sim->closed[s]) {
-            sim->items[last].seam_next = first;
-            sim->items[last].seam_shift = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
+    }
+}
+
+void free_plan(Plan &p, cudaStream_t s)
+{
+    if (p.mem)
+        cudaFreeAsync(p.mem, s);
+    p.mem = nullptr;
+}
+
+// Build the device plan of one launch over several simulations (slot order).
+// Every member must share the charge mode; pow2 only if every nx is a power
+// of two.
+cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
+{
+    std::vector<SimDev> table;
+    std::vector<WorkItem> items;
+    int nx_max = 2;
+    bool pow2 = true;
+    for (int slot = 0; slot < n; ++slot) {
+        sic_sim *m = sims[slot];
+        table.push_back(m->h);
+        nx_max = std::max(nx_max, m->nx);
+        pow2 = pow2 && ((m->nx & (m->nx - 1)) == 0);
+        for (WorkItem w : m->items) {
+            w.sim = slot;
+            items.push_back(w);
         }
     }
-}
-
-// Contiguous runs of items per block, balanced by tracer count.
-std::vector<int32_t> partition(const std::vector<WorkItem> &items, int grid)
-{
-    const int n = (int)items.size();
-    std::vector<int64_t> start(n + 1, 0);
-    for (int i = 0; i < n; ++i)
-        start[i + 1] = start[i] + items[i].count + kItemCost;
-    const int64_t total = start[n];
-    std::vector<int32_t> cta(grid + 1);
-    int i = 0;
-    for (int b = 0; b <= grid; ++b) {
-        const int64_t target = (int64_t)((__int128)total * b / grid);
-        while (i < n && start[i] < target)
-            ++i;
-        cta[b] = i;
-    }
-    cta[grid] = n;
-    return cta;
-}
-
-int pick_grid(int n_items, int nx_max, bool per_q)
-{
-    int per_sm = k1_blocks_per_sm(nx_max, true, true, per_q);
+    const bool per_q = sims[0]->per_q;
+    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
     if (per_sm < 1)
         per_sm = 1;
-    return std::max(1, std::min(n_items, env_int("SIC_GRID", num_sms() * per_sm)));
-}
-
-cudaError_t launch_step(sic_sim *sim)
-{
-    cudaError_t e = launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, true,
-                                        sim->per_q, 1.0f, 1, sim->stream);
+    const int by_items = ((int)items.size() + SIC_K1_WARPS - 1) / SIC_K1_WARPS;
+    const int grid = std::max(1, std::min(by_items, env_int("SIC_GRID", num_sms() * per_sm)));
+    std::vector<int32_t> cta = partition(items, grid);
+    std::vector<int32_t> slot_end(n, 0);
+    for (int i = 0; i < (int)items.size(); ++i)
+        slot_end[items[i].sim] = i + 1;
+    std::vector<int32_t> expected(n, 0);
+    for (int b = 0; b < grid; ++b) {
+        int last_slot = -1;
+        for (int i = cta[b]; i < cta[b + 1]; ++i)
+            if (items[i].sim != last_slot) {
+                last_slot = items[i].sim;
+                expected[last_slot] += 1;
+            }
+    }
+    Layout lay;
+    const size_t oT = lay.take(sizeof(SimDev) * table.size());
+    const size_t oI = lay.take(sizeof(WorkItem) * items.size());
+    const size_t oC = lay.take(4 * cta.size());
+    const size_t oS = lay.take(4 * slot_end.size());
+    const size_t oE = lay.take(4 * expected.size());
+    const size_t oK = lay.take(4 * (size_t)n);
+    cudaError_t e = cudaMallocAsync(&p.mem, lay.off, s);
     if (e != cudaSuccess)
         return e;
-    return launch_field(sim->d_desc, sim->d_job, 1, sim->nx, 1, sim->stream);
-}
-
-cudaError_t launch_deposit_field(sic_sim *sim)
-{
-    cudaError_t e = launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, false, true,
-                                        sim->per_q, 0.0f, 0, sim->stream);
+    char *b = (char *)p.mem;
+    e = cudaMemcpyAsync(b + oT, table.data(), sizeof(SimDev) * table.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oI, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oC, cta.data(), 4 * cta.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oS, slot_end.data(), 4 * slot_end.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oE, expected.data(), 4 * expected.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)n, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
     if (e != cudaSuccess)
         return e;
-    return launch_field(sim->d_desc, sim->d_job, 1, sim->nx, 0, sim->stream);
+    p.args.sims = (const SimDev *)(b + oT);
+    p.args.items = (const WorkItem *)(b + oI);
+    p.args.cta_begin = (const int32_t *)(b + oC);
+    p.args.slot_end = (const int32_t *)(b + oS);
+    p.args.expected = (const int32_t *)(b + oE);
+    p.args.tickets = (unsigned *)(b + oK);
+    p.args.nx_max = nx_max;
+    p.grid = grid;
+    p.per_q = per_q;
+    p.pow2 = pow2;
+    return cudaSuccess;
 }
 
-int check_device_errors(sic_sim *sim)
+cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int record, cudaStream_t s)
+{
+    LaunchArgs a = p.args;
+    a.kick_scale = kick_scale;
+    a.drift = drift;
+    a.record = record;
+    return launch_step_kernel(a, p.grid, mode, p.per_q, p.pow2, s);
+}
+
+int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
 {
     SimScalars sc;
     CK(cudaMemcpyAsync(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost, sim->stream));
     CK(cudaStreamSynchronize(sim->stream));
+    if (out)
+        *out = sc;
     if (sc.err & SIC_ERR_RANGE)
         return SIC_ERANGE;
     if (sc.err & SIC_ERR_SEGLONG)
@@ -255,7 +330,7 @@ double choose_sigma(double max_w)
     return sigma;
 }
 
-// Common part of both constructors: sizes, device layout, descriptor.
+// Common part of both constructors: sizes, device layout, descriptor, plan.
 // Expects counts, closed, winding, per_q, sigma and sheet_qh to be set.
 int setup(sic_sim *sim, const sic_config *cfg)
 {
@@ -283,48 +358,38 @@ int setup(sic_sim *sim, const sic_config *cfg)
     }
     plan_items(sim);
     const int n_items = (int)sim->items.size();
-    sim->grid = pick_grid(n_items, sim->nx, sim->per_q);
-    std::vector<int32_t> cta = partition(sim->items, sim->grid);
 
     Layout lay;
     const int nx = sim->nx;
-    const size_t oU = lay.take(8 * (size_t)sim->n_alloc);
-    const size_t oV = lay.take(4 * (size_t)sim->n_alloc);
+    const size_t oU0 = lay.take(8 * (size_t)sim->n_alloc);
+    const size_t oU1 = lay.take(8 * (size_t)sim->n_alloc);
+    const size_t oV0 = lay.take(4 * (size_t)sim->n_alloc);
+    const size_t oV1 = lay.take(4 * (size_t)sim->n_alloc);
     const size_t oQ = sim->per_q ? lay.take(4 * (size_t)sim->n_alloc) : 0;
     const size_t oMesh = lay.take(8 * (size_t)nx);
     const size_t oLast = lay.take(8 * (size_t)nx);
     const size_t oEk = lay.take(8 * (size_t)nx);
     const size_t oE64 = lay.take(8 * (size_t)nx);
     const size_t oRho = lay.take(8 * (size_t)nx);
-    const size_t oItems = lay.take(sizeof(WorkItem) * (size_t)n_items);
-    const size_t oEF = lay.take(8 * (size_t)n_items);
-    const size_t oEL = lay.take(8 * (size_t)n_items);
-    const size_t oDiag = lay.take(sizeof(ItemDiag) * (size_t)n_items);
+    const size_t oAcc = lay.take(sizeof(SimAccum));
     const size_t oHist = lay.take(32 * (size_t)sim->hist_len);
     const size_t oSc = lay.take(sizeof(SimScalars));
-    const size_t oDesc = lay.take(sizeof(SimDev));
-    const size_t oCta = lay.take(4 * (size_t)(sim->grid + 1));
-    const size_t oJob = lay.take(sizeof(FieldJob));
-    cudaError_t e = cudaMallocAsync(&sim->dmem, lay.off, sim->stream);
-    if (e == cudaErrorMemoryAllocation)
-        return SIC_ENOMEM;
-    CK(e);
+    CK(cudaMallocAsync(&sim->dmem, lay.off, sim->stream));
     char *b = (char *)sim->dmem;
     CK(cudaMemsetAsync(b, 0, lay.off, sim->stream));
 
     SimDev &h = sim->h;
-    h.U = (int64_t *)(b + oU);
-    h.V = (float *)(b + oV);
+    h.U[0] = (int64_t *)(b + oU0);
+    h.U[1] = (int64_t *)(b + oU1);
+    h.V[0] = (float *)(b + oV0);
+    h.V[1] = (float *)(b + oV1);
     h.Qh = sim->per_q ? (const int32_t *)(b + oQ) : nullptr;
     h.mesh = (unsigned long long *)(b + oMesh);
     h.mesh_last = (long long *)(b + oLast);
     h.Ek = (float2 *)(b + oEk);
     h.E64 = (double *)(b + oE64);
     h.rho64 = (double *)(b + oRho);
-    h.items = (const WorkItem *)(b + oItems);
-    h.edge_first = (int64_t *)(b + oEF);
-    h.edge_last = (int64_t *)(b + oEL);
-    h.item_diag = (ItemDiag *)(b + oDiag);
+    h.acc = (SimAccum *)(b + oAcc);
     h.hist = (double *)(b + oHist);
     h.sc = (SimScalars *)(b + oSc);
     h.n_items = n_items;
@@ -339,29 +404,19 @@ int setup(sic_sim *sim, const sic_config *cfg)
     h.ke_scale = vu * vu / (2.0 * sim->sigma * sim->qm);
     h.p_scale = vu / (sim->sigma * sim->qm);
     h.strict = sim->strict;
-    sim->d_desc = (SimDev *)(b + oDesc);
-    sim->d_items = (WorkItem *)(b + oItems);
-    sim->d_cta = (int32_t *)(b + oCta);
-    sim->d_job = (FieldJob *)(b + oJob);
-    FieldJob job{0, 0};
-    CK(cudaMemcpyAsync(sim->d_desc, &h, sizeof(SimDev), cudaMemcpyHostToDevice, sim->stream));
-    CK(cudaMemcpyAsync(sim->d_items, sim->items.data(), sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice,
-                       sim->stream));
-    CK(cudaMemcpyAsync(sim->d_cta, cta.data(), 4 * cta.size(), cudaMemcpyHostToDevice, sim->stream));
-    CK(cudaMemcpyAsync(sim->d_job, &job, sizeof(job), cudaMemcpyHostToDevice, sim->stream));
-    CK(cudaStreamSynchronize(sim->stream));  // host staging buffers go out of scope
+    h.pow2 = (nx & (nx - 1)) == 0;
+    sic_sim *one[1] = {sim};
+    CK(build_plan(sim->plan, one, 1, sim->stream));
     return SIC_OK;
 }
 
 // Initial deposit + field, then the optional half kick back.
 int initialise(sic_sim *sim)
 {
-    CK(launch_deposit_field(sim));
+    CK(launch(sim->plan, MODE_DEPOSIT, 0.0f, 0, 0, sim->stream));
     if (sim->half_step_init)
-        CK(launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, false, sim->per_q,
-                               -0.5f, 0, sim->stream));
-    const int rc = check_device_errors(sim);
-    return rc;
+        CK(launch(sim->plan, MODE_PUSH, -0.5f, 0, 0, sim->stream));
+    return check_device_errors(sim);
 }
 
 }  // namespace
@@ -449,16 +504,16 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
             }
             base += sim->counts[s];
         }
-        cudaError_t e = cudaMemcpyAsync(sim->h.U, U.data(), 8 * U.size(), cudaMemcpyHostToDevice, sim->stream);
+        cudaError_t e = cudaMemcpyAsync(sim->h.U[0], U.data(), 8 * U.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sim->h.V, V.data(), 4 * V.size(), cudaMemcpyHostToDevice, sim->stream);
+            e = cudaMemcpyAsync(sim->h.V[0], V.data(), 4 * V.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess && sim->per_q)
             e = cudaMemcpyAsync((void *)sim->h.Qh, Q.data(), 4 * Q.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(sim->stream);
         if (e != cudaSuccess) {
             sic_destroy(sim);
-            return SIC_ECUDA;
+            return e == cudaErrorMemoryAllocation ? SIC_ENOMEM : SIC_ECUDA;
         }
     }
     rc = initialise(sim);
@@ -537,7 +592,8 @@ int sic_create_horizontal(const sic_config *cfg, int32_t n_template, const doubl
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_vs, vs.data(), 4 * vs.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess)
-            e = launch_expand_horizontal(sim->h.U, sim->h.V, d_ut, n_template, d_vs, d_off, sim->M, sim->stream);
+            e = launch_expand_horizontal(sim->h.U[0], sim->h.V[0], d_ut, n_template, d_vs, d_off, sim->M,
+                                         sim->stream);
         cudaError_t e2 = cudaFreeAsync(tmp, sim->stream);
         if (e == cudaSuccess)
             e = e2;
@@ -561,7 +617,7 @@ int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host)
 {
     if (!sim)
         return SIC_EINVAL;
-    CK(launch_deposit_field(sim));
+    CK(launch(sim->plan, MODE_DEPOSIT, 0.0f, 0, 0, sim->stream));
     if (mesh_fixed_host)
         CK(cudaMemcpyAsync(mesh_fixed_host, sim->h.mesh_last, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost,
                            sim->stream));
@@ -582,8 +638,7 @@ int sic_push(sic_sim *sim)
 {
     if (!sim)
         return SIC_EINVAL;
-    CK(launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, false, sim->per_q, 1.0f,
-                           1, sim->stream));
+    CK(launch(sim->plan, MODE_PUSH, 1.0f, 1, 0, sim->stream));
     return SIC_OK;
 }
 
@@ -596,7 +651,7 @@ int sic_step(sic_sim *sim, int32_t n_steps)
         CK(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i)
-            e = launch_step(sim);
+            e = launch(sim->plan, MODE_STEP, 1.0f, 1, 1, sim->stream);
         cudaError_t e2 = cudaStreamEndCapture(sim->stream, &g);
         if (e != cudaSuccess)
             return fail_cuda(sim, e);
@@ -604,32 +659,16 @@ int sic_step(sic_sim *sim, int32_t n_steps)
         e = cudaGraphInstantiate(&sim->gexec, g, 0);
         cudaGraphDestroy(g);
         CK(e);
-        // the captured launches were counted at capture time; undo that
-        count_launches(-2 * kGraphSteps);
+        count_launches(-kGraphSteps);  // captured, not run
     }
     int32_t left = n_steps;
     while (left >= kGraphSteps && sim->gexec) {
         CK(cudaGraphLaunch(sim->gexec, sim->stream));
-        count_launches(2 * kGraphSteps);
+        count_launches(kGraphSteps);
         left -= kGraphSteps;
     }
     for (; left > 0; --left)
-        CK(launch_step(sim));
-    sim->steps_done += n_steps;
-    return SIC_OK;
-}
-
-int sic_step_phase(sic_sim *sim, int32_t phase)
-{
-    if (!sim || (phase != 1 && phase != 2))
-        return SIC_EINVAL;
-    if (phase == 1)
-        CK(launch_push_deposit(sim->d_desc, sim->d_items, sim->d_cta, sim->grid, sim->nx, true, true, sim->per_q,
-                               1.0f, 1, sim->stream));
-    else {
-        CK(launch_field(sim->d_desc, sim->d_job, 1, sim->nx, 1, sim->stream));
-        sim->steps_done += 1;
-    }
+        CK(launch(sim->plan, MODE_STEP, 1.0f, 1, 1, sim->stream));
     return SIC_OK;
 }
 
@@ -656,83 +695,31 @@ int sic_step_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)
         CK(cudaStreamWaitEvent(bs, e, 0));
     }
     std::vector<int32_t> left(n_steps, n_steps + n_sims);
-    std::vector<int> active;
-    for (int i = 0; i < n_sims; ++i)
-        if (left[i] > 0)
-            active.push_back(i);
-    const int sms = num_sms();
-    while (!active.empty()) {
+    while (true) {
+        // members with steps left, per charge mode (the two modes take
+        // different kernel variants)
         int32_t k = INT32_MAX;
-        int nx_max = 2;
-        for (int i : active) {
-            k = std::min(k, left[i]);
-            nx_max = std::max(nx_max, sims[i]->nx);
-        }
-        std::vector<SimDev> table;
-        std::vector<WorkItem> items;
-        std::vector<FieldJob> jobs;
-        for (int slot = 0; slot < (int)active.size(); ++slot) {
-            sic_sim *s = sims[active[slot]];
-            table.push_back(s->h);
-            for (WorkItem w : s->items) {
-                w.sim = slot;
-                items.push_back(w);
+        std::vector<sic_sim *> grp[2];
+        for (int i = 0; i < n_sims; ++i)
+            if (left[i] > 0) {
+                k = std::min(k, left[i]);
+                grp[sims[i]->per_q ? 1 : 0].push_back(sims[i]);
             }
-            jobs.push_back(FieldJob{slot, 0});
-        }
-        // per-tracer and per-sheet charge take different kernel variants
-        std::vector<WorkItem> items_q, items_u;
-        for (const WorkItem &w : items)
-            (sims[active[w.sim]]->per_q ? items_q : items_u).push_back(w);
-        int per_sm_u = std::max(1, k1_blocks_per_sm(nx_max, true, true, false));
-        int per_sm_q = std::max(1, k1_blocks_per_sm(nx_max, true, true, true));
-        int grid_u = items_u.empty() ? 0 : std::max(1, std::min((int)items_u.size(), sms * per_sm_u));
-        int grid_q = items_q.empty() ? 0 : std::max(1, std::min((int)items_q.size(), sms * per_sm_q));
-        std::vector<int32_t> cta_u = grid_u ? partition(items_u, grid_u) : std::vector<int32_t>();
-        std::vector<int32_t> cta_q = grid_q ? partition(items_q, grid_q) : std::vector<int32_t>();
-        Layout lay;
-        const size_t oT = lay.take(sizeof(SimDev) * table.size());
-        const size_t oIu = lay.take(sizeof(WorkItem) * items_u.size());
-        const size_t oIq = lay.take(sizeof(WorkItem) * items_q.size());
-        const size_t oCu = lay.take(4 * cta_u.size());
-        const size_t oCq = lay.take(4 * cta_q.size());
-        const size_t oJ = lay.take(sizeof(FieldJob) * jobs.size());
-        void *buf = nullptr;
-        CK(cudaMallocAsync(&buf, lay.off, bs));
-        char *b = (char *)buf;
-        CK(cudaMemcpyAsync(b + oT, table.data(), sizeof(SimDev) * table.size(), cudaMemcpyHostToDevice, bs));
-        if (!items_u.empty()) {
-            CK(cudaMemcpyAsync(b + oIu, items_u.data(), sizeof(WorkItem) * items_u.size(), cudaMemcpyHostToDevice,
-                               bs));
-            CK(cudaMemcpyAsync(b + oCu, cta_u.data(), 4 * cta_u.size(), cudaMemcpyHostToDevice, bs));
-        }
-        if (!items_q.empty()) {
-            CK(cudaMemcpyAsync(b + oIq, items_q.data(), sizeof(WorkItem) * items_q.size(), cudaMemcpyHostToDevice,
-                               bs));
-            CK(cudaMemcpyAsync(b + oCq, cta_q.data(), 4 * cta_q.size(), cudaMemcpyHostToDevice, bs));
-        }
-        CK(cudaMemcpyAsync(b + oJ, jobs.data(), sizeof(FieldJob) * jobs.size(), cudaMemcpyHostToDevice, bs));
-        const SimDev *d_table = (const SimDev *)(b + oT);
-        for (int32_t st = 0; st < k; ++st) {
-            if (grid_u)
-                CK(launch_push_deposit(d_table, (const WorkItem *)(b + oIu), (const int32_t *)(b + oCu), grid_u,
-                                       nx_max, true, true, false, 1.0f, 1, bs));
-            if (grid_q)
-                CK(launch_push_deposit(d_table, (const WorkItem *)(b + oIq), (const int32_t *)(b + oCq), grid_q,
-                                       nx_max, true, true, true, 1.0f, 1, bs));
-            CK(launch_field(d_table, (const FieldJob *)(b + oJ), (int)jobs.size(), nx_max, 1, bs));
-        }
-        CK(cudaFreeAsync(buf, bs));
-        // host copies are pageable: wait before they go out of scope
-        CK(cudaStreamSynchronize(bs));
-        std::vector<int> next;
-        for (int i : active) {
-            left[i] -= k;
-            sims[i]->steps_done += k;
+        if (grp[0].empty() && grp[1].empty())
+            break;
+        Plan plans[2];
+        for (int g = 0; g < 2; ++g)
+            if (!grp[g].empty())
+                CK(build_plan(plans[g], grp[g].data(), (int)grp[g].size(), bs));
+        for (int32_t st = 0; st < k; ++st)
+            for (int g = 0; g < 2; ++g)
+                if (plans[g].mem)
+                    CK(launch(plans[g], MODE_STEP, 1.0f, 1, 1, bs));
+        for (int g = 0; g < 2; ++g)
+            free_plan(plans[g], bs);
+        for (int i = 0; i < n_sims; ++i)
             if (left[i] > 0)
-                next.push_back(i);
-        }
-        active.swap(next);
+                left[i] -= k;
     }
     cudaEvent_t done;
     CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -749,11 +736,10 @@ int sic_diagnostics(sic_sim *sim, sic_diag *out)
 {
     if (!sim || !out)
         return SIC_EINVAL;
-    int rc = check_device_errors(sim);
+    SimScalars sc;
+    int rc = check_device_errors(sim, &sc);
     if (rc)
         return rc;
-    SimScalars sc;
-    CK(cudaMemcpy(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost));
     out->step = sc.step;
     out->t = (double)sc.step * sim->dt;
     out->field_energy = sc.we;
@@ -776,11 +762,10 @@ int sic_history(sic_sim *sim, double *hist_host, int32_t *rows)
 {
     if (!sim || !hist_host || !rows)
         return SIC_EINVAL;
-    int rc = check_device_errors(sim);
+    SimScalars sc;
+    int rc = check_device_errors(sim, &sc);
     if (rc)
         return rc;
-    SimScalars sc;
-    CK(cudaMemcpy(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost));
     const int64_t n = std::min<int64_t>(sc.step, sim->hist_len);
     std::vector<double> ring(4 * (size_t)sim->hist_len);
     CK(cudaMemcpy(ring.data(), sim->h.hist, 8 * ring.size(), cudaMemcpyDeviceToHost));
@@ -796,13 +781,15 @@ int sic_get_state(sic_sim *sim, double *x_host, double *v_host)
 {
     if (!sim)
         return SIC_EINVAL;
-    int rc = check_device_errors(sim);
+    SimScalars sc;
+    int rc = check_device_errors(sim, &sc);
     if (rc)
         return rc;
+    const int b = sc.buf & 1;
     std::vector<int64_t> U(sim->n_alloc);
     std::vector<float> V(sim->n_alloc);
-    CK(cudaMemcpy(U.data(), sim->h.U, 8 * U.size(), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(V.data(), sim->h.V, 4 * V.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(U.data(), sim->h.U[b], 8 * U.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(V.data(), sim->h.V[b], 4 * V.size(), cudaMemcpyDeviceToHost));
     const double xs = sim->dx / kTwo32, vs = sim->dx / sim->dt;
     int64_t base = 0;
     for (int s = 0; s < sim->M; ++s) {
@@ -822,10 +809,15 @@ int sic_device_state(sic_sim *sim, int64_t **pos_dev, float **vel_dev, const int
 {
     if (!sim)
         return SIC_EINVAL;
+    SimScalars sc;
+    int rc = check_device_errors(sim, &sc);
+    if (rc)
+        return rc;
+    const int b = sc.buf & 1;
     if (pos_dev)
-        *pos_dev = sim->h.U;
+        *pos_dev = sim->h.U[b];
     if (vel_dev)
-        *vel_dev = sim->h.V;
+        *vel_dev = sim->h.V[b];
     if (sheet_offset_host)
         *sheet_offset_host = sim->sheet_off.data();
     return SIC_OK;
@@ -846,8 +838,10 @@ void sic_destroy(sic_sim *sim)
         cudaStreamSynchronize(sim->stream);
     if (sim->gexec)
         cudaGraphExecDestroy(sim->gexec);
-    if (sim->dmem) {
-        cudaFreeAsync(sim->dmem, sim->stream);
+    if (sim->stream) {
+        free_plan(sim->plan, sim->stream);
+        if (sim->dmem)
+            cudaFreeAsync(sim->dmem, sim->stream);
         cudaStreamSynchronize(sim->stream);
     }
     if (sim->own_stream && sim->stream)

@@ -1,19 +1,21 @@
 // sic_internal.h -- device-side layout shared by the kernels and the host runtime.
 //
 // State of one simulation in HBM (all arrays device-resident for its lifetime):
-//   U[n_alloc]   int64  tracer position, unwrapped, 32.32 fixed point in cell
-//                       units (x / dx * 2^32); sheets start on 32-tracer
-//                       boundaries so every thread's tracers are 16-byte aligned.
-//   V[n_alloc]   float  velocity in cells per step (v dt / dx).
-//   Qh[n_alloc]  int32  half charge of each tracer in fixed-point units (only
-//                       when weights differ inside a sheet; otherwise every
-//                       work item carries its sheet's value).
-//   mesh[nx]     u64    int64 charge accumulator the deposit adds into.
-//   mesh_last    int64  charge of the latest completed deposit.
-//   Ek[nx]       float2 (Ek_j, Ek_{j+1} - Ek_j): the kick per step
-//                       qm E_j dt^2 / dx at node j, paired for one load.
-//   E64[nx]      double the node field E_j in physical units.
-//   rho64[nx]    double the neutralised density of the latest deposit.
+//   U[2][n_alloc] int64  tracer position, unwrapped, 32.32 fixed point in cell
+//                        units (x / dx * 2^32); two buffers, a step reads one
+//                        and writes the other (sc->buf names the current one).
+//                        Sheets start on 32-tracer boundaries so every thread's
+//                        tracers are 16-byte aligned.
+//   V[2][n_alloc] float  velocity in cells per step (v dt / dx).
+//   Qh[n_alloc]   int32  half charge of each tracer in fixed-point units (only
+//                        when weights differ inside a sheet; otherwise every
+//                        work item carries its sheet's value).
+//   mesh[nx]      u64    int64 charge accumulator the deposit adds into.
+//   mesh_last     int64  charge of the latest completed deposit.
+//   Ek[nx]        float2 (Ek_j, Ek_{j+1} - Ek_j): the kick per step
+//                        qm E_j dt^2 / dx at node j, paired for one load.
+//   E64[nx]       double the node field E_j in physical units.
+//   rho64[nx]     double the neutralised density of the latest deposit.
 // Charge unit: a segment between tracers of weights w_i, w_{i+1} carries
 // Q_s = Qh_i + Qh_{i+1} = round(w_i sigma / 2) + round(w_{i+1} sigma / 2)
 // units, sigma chosen so that every Q_s < 2^29.
@@ -25,9 +27,8 @@
 #define SIC_ALIGN_TRACERS 32
 #define SIC_K1_BLOCK 256
 #define SIC_K1_R 8
-#define SIC_K1_TILE (SIC_K1_BLOCK * SIC_K1_R)
-#define SIC_K2_BLOCK 1024
-#define SIC_FIX_ONE 4294967296.0  // 2^32
+#define SIC_K1_WARPS (SIC_K1_BLOCK / 32)
+#define SIC_K1_WARP_TRACERS (32 * SIC_K1_R)
 
 // error bits raised on the device
 #define SIC_ERR_RANGE 1u
@@ -42,25 +43,28 @@ struct NxDiv {
     int32_t offset;    // multiple of nx >= 2^30, added before the division
 };
 
-// One work item: consecutive tracers of one sheet.
+// One work item, the task of one warp: up to 256 consecutive tracers of one sheet.
 struct WorkItem {
     int32_t sim;        // slot in the launch's simulation table
     int32_t local;      // index of the item inside its simulation
     int64_t t0;         // first tracer (aligned to SIC_ALIGN_TRACERS)
-    int32_t count;      // tracers, 1..SIC_K1_TILE * k
+    int32_t count;      // tracers, 1..SIC_K1_WARP_TRACERS
     int32_t qh;         // sheet half charge when the simulation has no Qh array
-    int32_t seam_next;  // local item whose first tracer ends this item's last
-                        // segment, -1 for the open end of a chain
-    int32_t pad;
-    int64_t seam_shift; // added to that first tracer (winding * nx * 2^32)
+    int64_t halo;       // tracer after the item's last one: the next item's
+                        // first, or the sheet's first for a closed sheet; -1
+                        // at the open end of a chain
+    int64_t halo_shift; // added to the halo position (winding * nx * 2^32)
 };
 
-// Per-step diagnostics that K1 leaves per item, reduced by K2 in fixed order.
-struct ItemDiag {
-    double ke;          // sum Qh (v_old^2 + v_new^2)   (cells/step)^2 units
-    double p;           // sum Qh (v_old + v_new)
-    int64_t maxseg;     // longest segment deposited, 2^-32 cells
-    int64_t pad;
+// Per-step sums every block adds into and the epilogue reads: the kinetic
+// energy and momentum terms as 128-bit fixed-point integers (2^-32 units,
+// each item's FP32 partial converted exactly), so the totals do not depend
+// on the order of the additions; the longest segment by atomicMax.
+struct SimAccum {
+    unsigned long long ke[2];   // sum Qh (v_old^2 + v_new^2)  ((cells/step)^2), lo/hi
+    unsigned long long p[2];    // sum Qh (v_old + v_new)                      , lo/hi
+    unsigned long long maxseg;  // longest segment crossing a cell edge, 2^-32 cells
+    unsigned long long pad[3];
 };
 
 struct SimScalars {
@@ -69,22 +73,19 @@ struct SimScalars {
     double we;          // W_E of the current field
     int64_t maxseg;     // longest segment of the latest deposit
     uint32_t err;       // SIC_ERR_* bits
-    uint32_t pad;
+    uint32_t buf;       // which state buffer is current
 };
 
 struct SimDev {
-    int64_t *U;
-    float *V;
+    int64_t *U[2];
+    float *V[2];
     const int32_t *Qh;          // may be null
     unsigned long long *mesh;
     long long *mesh_last;
     float2 *Ek;
     double *E64;
-    double *rho64;              // neutralised density n_j - mean(n) of the latest deposit
-    const WorkItem *items;      // this simulation's own items
-    int64_t *edge_first;        // [n_items]
-    int64_t *edge_last;         // [n_items]
-    ItemDiag *item_diag;        // [n_items]
+    double *rho64;
+    SimAccum *acc;
     double *hist;               // [hist_len][4]
     SimScalars *sc;
     int32_t n_items;
@@ -97,29 +98,32 @@ struct SimDev {
     double ke_scale;            // KE = ke_scale * sum ke
     double p_scale;             // P  = p_scale * sum p
     int32_t strict;
-    int32_t pad;
+    int32_t pow2;               // nx is a power of two
 };
 
-// One simulation of a field launch (K2): table slot.
-struct FieldJob {
-    int32_t slot;
-    int32_t pad;
+// Everything one launch of the step kernel needs.
+struct LaunchArgs {
+    const SimDev *sims;         // table, one entry per slot
+    const WorkItem *items;      // grouped by slot
+    const int32_t *slot_end;    // [slots] one past the slot's last item
+    const int32_t *cta_begin;   // [grid + 1]
+    unsigned *tickets;          // [slots], zero between launches
+    const int32_t *expected;    // [slots] blocks that touch each slot
+    int32_t nx_max;
+    int32_t drift;
+    int32_t record;
+    float kick_scale;
 };
 
-// Host-side launch helpers implemented in sic_kernels.cu.
 #include <cuda_runtime.h>
 namespace sic {
-cudaError_t launch_push_deposit(const SimDev *sims, const WorkItem *items, const int32_t *cta_begin,
-                                int grid, int nx_max, bool push, bool deposit, bool per_q,
-                                float kick_scale, int drift, cudaStream_t s);
-cudaError_t launch_field(const SimDev *sims, const FieldJob *jobs, int n_jobs, int nx_max,
-                         int record, cudaStream_t s);
-cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template,
-                                     int32_t n_template, const float *v_sheet,
-                                     const int64_t *sheet_offset, int32_t n_sheets,
+enum Mode { MODE_STEP = 0, MODE_DEPOSIT = 1, MODE_PUSH = 2 };
+cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s);
+cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,
+                                     const float *v_sheet, const int64_t *sheet_offset, int32_t n_sheets,
                                      cudaStream_t s);
-int k1_blocks_per_sm(int nx_max, bool push, bool deposit, bool per_q);
-size_t k1_smem_bytes(int nx_max);
+int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2);
+size_t step_smem_bytes(int nx_max);
 void count_launches(int64_t n);
 int64_t launches();
 }  // namespace sic

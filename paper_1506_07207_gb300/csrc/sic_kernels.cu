@@ -1,20 +1,28 @@
-// sic_kernels.cu -- sm_103a kernels of the SIC step.
+// sic_kernels.cu -- sm_103a kernel of the SIC step.
 //
-//  K1 k_push_deposit  fused gather -> kick -> drift -> deposit over work items
-//                     (consecutive tracers of one sheet); the whole mesh of the
-//                     current simulation is staged in shared memory as an int64
-//                     histogram and flushed to HBM with int64 atomics.
-//  K2 k_field         per simulation: deposit the item seams, exact integer
-//                     prefix sum of the mesh, neutralising mean and zero-mean
-//                     field with one final rounding, field energy, history row.
+// k_step runs one whole step (or one of its halves) in a single launch:
+//   1. every warp takes work items of up to 256 consecutive tracers of one
+//      sheet (8 per lane) from its block's run of items, gathers E at each
+//      tracer (linear weighting between the two nodes), kicks, drifts, and
+//      writes the tracer to the other state buffer;
+//   2. it deposits the segment from each of its tracers to the next one
+//      (Sec. 2.3, Eq. overlap and Eq. rho_sum) into the block's shared-memory
+//      copy of the simulation's int64 charge mesh.  The tracer after the
+//      warp's last one is read from the input buffer and pushed again by the
+//      warp itself, so warps and blocks never wait for one another;
+//   3. when a block leaves a simulation it adds its mesh into the global mesh
+//      with int64 atomics and takes a ticket; the block that takes the last
+//      ticket of that simulation runs its epilogue: the exact integer field
+//      solve, the field energy, the diagnostic row, and the buffer swap.
 //
-// Deposit (Sec. 2.3, Eq. overlap and Eq. rho_sum): the particle between two
-// tracers spreads its charge Q_s uniformly over [a, b]; cell j receives
-// Q_s |[a, b] ∩ cell j| / (b - a).  In fixed point the cumulative charge at
-// each interior cell edge e_k is C_k = round(Q_s (e_k - a) / (b - a)) and
-// cell k receives C_k - C_{k-1} (C_0 = 0, C_last = Q_s), so the pieces of a
-// segment always sum to Q_s exactly and the mesh is independent of the order
-// in which the integer atomics land.
+// Deposit arithmetic: a segment [a, b] of q units in 32.32 fixed-point cell
+// coordinates gives its first cell F = round(q (e_1 - a) / (b - a)) (FP32),
+// every whole cell inside P = floor(q 2^32 / (b - a)) (exact integer), and the
+// last cell the rest, q - F - (cells inside) P.  The pieces always sum to q
+// exactly and never go negative; the integer mesh does not depend on the
+// order of the atomic adds, so results are bit-identical however the work is
+// split.  Whole cells inside a long segment are added through a difference
+// array, so a segment costs O(1) shared-memory atomics at any length.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,16 +32,73 @@ namespace sic {
 
 namespace {
 
+constexpr int B = SIC_K1_BLOCK;
+constexpr int R = SIC_K1_R;
+constexpr int NW = SIC_K1_WARPS;
+constexpr int WT = SIC_K1_WARP_TRACERS;
+
 __device__ __forceinline__ int cell_of(long long u) { return (int)(u >> 32); }
 __device__ __forceinline__ unsigned frac_of(long long u) { return (unsigned)(unsigned long long)u; }
 
 // floor-mod of a cell number into [0, nx) for |c| < 2^30
+template <bool POW2>
 __device__ __forceinline__ int wrap_cell(int c, const NxDiv &d)
 {
-    unsigned n = (unsigned)c + (unsigned)d.offset;
-    unsigned t = __umulhi(d.magic, n);
-    unsigned q = (t + ((n - t) >> 1)) >> d.shift;
+    if (POW2)
+        return c & (d.nx - 1);
+    const unsigned n = (unsigned)c + (unsigned)d.offset;
+    const unsigned t = __umulhi(d.magic, n);
+    const unsigned q = (t + ((n - t) >> 1)) >> d.shift;
     return (int)(n - q * (unsigned)d.nx);
+}
+
+// fraction of a cell in [0, 1) from the low word (its top 23 bits)
+__device__ __forceinline__ float frac_float(long long u)
+{
+    return __fsub_rn(__uint_as_float(0x3f800000u | (frac_of(u) >> 9)), 1.0f);
+}
+
+// v cells -> 32.32 fixed point, v * 2^32 rounded to an integer; 32-bit
+// conversions only (|v| < 2^31)
+__device__ __forceinline__ long long to_fixed(float v)
+{
+    const float h = floorf(v);
+    const int hi = __float2int_rz(h);
+    const unsigned lo = __float2uint_rn(__fmul_rn(__fsub_rn(v, h), 4294967296.0f));
+    return (long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned long long)lo);
+}
+
+// gather (linear weighting between nodes j and j+1), kick, drift; j is the
+// cell of the new position on return
+template <bool POW2>
+__device__ __forceinline__ void push_one(long long &u, float &v, int &j, const float2 *ek, const NxDiv &d,
+                                         float ks, int drift, unsigned &rerr)
+{
+    const int c = cell_of(u);
+    j = wrap_cell<POW2>(c, d);
+    const float2 e = ek[j];
+    const float a = __fmaf_rn(frac_float(u), e.y, e.x);
+    const float vn = __fmaf_rn(ks, a, v);
+    v = vn;
+    if (drift) {
+        const long long nu = u + to_fixed(vn);
+        const int cn = cell_of(nu);
+        if (POW2) {
+            j = cn & (d.nx - 1);
+        } else {
+            const int dc = cn - c;
+            if (dc >= -d.nx && dc < d.nx) {
+                int t = j + dc;
+                t += (t < 0) ? d.nx : 0;
+                t -= (t >= d.nx) ? d.nx : 0;
+                j = t;
+            } else {
+                j = wrap_cell<false>(cn, d);
+            }
+        }
+        rerr |= (unsigned)(cn + (1 << 30));  // bit 31 set: |cell| >= 2^30
+        u = nu;
+    }
 }
 
 // Per-thread run of consecutive contributions to one cell; a cell change
@@ -63,15 +128,45 @@ struct RunAcc {
     }
 };
 
-// Deposit one segment between fixed-point positions ua (cell ja mod nx) and
-// ub (cell jb mod nx) carrying q units; returns its length in 2^-32 cells.
-// Up to two box lengths the cumulative cut points are walked edge by edge;
-// a longer segment (it wraps the box, or its tracers left the valid range)
-// takes a bounded O(nx) path: the overlap of each cell summed over all its
-// images, one rounding per cell, the remainder on the first interior cell.
-__device__ __forceinline__ long long emit_segment(long long ua, int ja, long long ub, int jb, int q,
-                                                  int nx, RunAcc &acc)
+__device__ __forceinline__ float span_to_float(long long span)
 {
+    if ((unsigned long long)span < (1ull << 32))
+        return __uint2float_rn((unsigned)span);
+    return __fmaf_rn(__int2float_rn((int)(span >> 32)), 4294967296.0f, __uint2float_rn(frac_of(span)));
+}
+
+// n whole cells starting at cell js (mod nx) each receive p units
+__device__ __noinline__ void range_add(int js, long long n, long long p, int nx, unsigned long long *diff,
+                                       int *diff_used)
+{
+    const long long full = n / nx;
+    const int rem = (int)(n - full * nx);
+    if (full)
+        atomicAdd(diff, (unsigned long long)(full * p));
+    if (rem) {
+        const int e = js + rem;
+        atomicAdd(diff + js, (unsigned long long)p);
+        if (e <= nx) {
+            atomicAdd(diff + e, (unsigned long long)(-p));
+        } else {
+            atomicAdd(diff, (unsigned long long)p);
+            atomicAdd(diff + (e - nx), (unsigned long long)(-p));
+        }
+    }
+    *diff_used = 1;
+}
+
+// Deposit one segment between fixed-point positions ua (cell ja mod nx) and
+// ub (cell jb mod nx) carrying q units.  maxseg tracks the longest segment
+// that crosses a cell edge (2^-32 cells).
+__device__ __forceinline__ void emit_segment(long long ua, int ja, long long ub, int jb, int q, int nx,
+                                             RunAcc &acc, unsigned long long *diff, int *diff_used,
+                                             long long &maxseg)
+{
+    if (cell_of(ua) == cell_of(ub)) {  // also the zero-length segment: all charge in its cell
+        acc.add(ja, q);
+        return;
+    }
     if (ub < ua) {
         const long long t = ua;
         ua = ub;
@@ -80,345 +175,87 @@ __device__ __forceinline__ long long emit_segment(long long ua, int ja, long lon
         ja = jb;
         jb = tj;
     }
-    const int ca = cell_of(ua), cb = cell_of(ub);
     const long long span = ub - ua;
-    if (ca == cb) {  // also the zero-length segment: all charge in the cell holding it
-        acc.add(ja, q);
-        return span;
+    maxseg = max(maxseg, span);
+    const unsigned la = frac_of(ua);
+    const float df = la ? __uint2float_rn(0u - la) : 4294967296.0f;  // a to the first edge
+    const float inv = __frcp_rn(span_to_float(span));
+    int F = __float2int_rn(__fmul_rn(__fmul_rn(df, inv), __int2float_rn(q)));
+    F = min(max(F, 0), q);
+    const long long ncut = (long long)cell_of(ub) - (long long)cell_of(ua);
+    if (ncut == 1) {
+        acc.add(ja, F);
+        acc.add(jb, q - F);
+        return;
     }
-    const float inv = __frcp_rn(__ll2float_rn(span));
-    const float qf = __int2float_rn(q);
-    const long long ncut = (long long)cb - (long long)ca;
-    if (ncut <= 2LL * nx) {
-        long long d = (1LL << 32) - (long long)frac_of(ua);  // a to the first interior edge
-        int prev = 0;
-        int j = ja;
-        for (int k = 0; k < (int)ncut; ++k) {
-            const float t = __fmul_rn(__ll2float_rn(d), inv);
-            int c = __float2int_rn(__fmul_rn(t, qf));
-            c = min(max(c, prev), q);
-            acc.add(j, (long long)(c - prev));
-            prev = c;
+    const long long nint = ncut - 1;
+    const long long P = span > 0 ? (long long)(((unsigned long long)q << 32) / (unsigned long long)span) : 0;
+    const long long inner = nint * P;
+    if ((long long)F > (long long)q - inner)
+        F = (int)((long long)q - inner);
+    acc.add(ja, F);
+    int j = (ja + 1 == nx) ? 0 : ja + 1;
+    if (nint <= 2) {
+        acc.add(j, P);
+        if (nint == 2) {
             j = (j + 1 == nx) ? 0 : j + 1;
-            d += (1LL << 32);
+            acc.add(j, P);
         }
-        acc.add(j, (long long)(q - prev));
-        return span;
+    } else {
+        range_add(j, nint, P, nx, diff, diff_used);
     }
-    const long long nint = ncut - 1;  // whole cells strictly inside (a, b)
-    const int jfix = (ja + 1 == nx) ? 0 : ja + 1;
-    long long given = 0;
-    for (int j = 0; j < nx; ++j) {
-        int o = j - jfix;
-        o += (o < 0) ? nx : 0;
-        const long long cnt = (nint > o) ? (nint - o - 1) / nx + 1 : 0;
-        long long ov = cnt << 32;
-        if (j == ja)
-            ov += (1LL << 32) - (long long)frac_of(ua);
-        if (j == jb)
-            ov += (long long)frac_of(ub);
-        int pc = __float2int_rn(__fmul_rn(__fmul_rn(__ll2float_rn(ov), inv), qf));
-        pc = min(max(pc, 0), q);
-        if (j != jfix) {
-            given += pc;
-            acc.add(j, (long long)pc);
-        }
-    }
-    // jfix holds at least one whole image: give it the rest so the pieces sum to q
-    acc.add(jfix, (long long)q - given);
-    return span;
+    acc.add(jb, (long long)q - F - inner);
 }
 
-struct K1Shared {
-    long long fu[2][SIC_K1_BLOCK];  // first tracer of each thread (new position)
-    int fj[2][SIC_K1_BLOCK];        // its cell mod nx
-    int fq[2][SIC_K1_BLOCK];        // its half charge
-    long long pu[2];                // last tracer of the previous tile of the item
-    int pj[2];
-    int pq[2];
-    double ra[SIC_K1_BLOCK / 32];
-    double rb[SIC_K1_BLOCK / 32];
-    long long rm[SIC_K1_BLOCK / 32];
+// FP32 value -> 128-bit fixed point with 32 fractional bits: exact for
+// |x| >= 2^-32 up to 2^94 (larger values, inf and nan saturate)
+__device__ __forceinline__ __int128 f32_to_fix(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0)
+        return 0;
+    const unsigned m = (b & 0x7fffffu) | 0x800000u;
+    const int sh = e - 118;  // x * 2^32 = m * 2^(e - 150 + 32)
+    __int128 r;
+    if (sh >= 0)
+        r = sh > 100 ? ((__int128)1 << 124) : ((__int128)m << sh);
+    else
+        r = sh <= -24 ? 0 : (__int128)(m >> (-sh));
+    return (b >> 31) ? -r : r;
+}
+
+// 128-bit add into a (lo, hi) pair of 64-bit words with two atomics
+__device__ __forceinline__ void atomic_add_i128(unsigned long long *lohi, __int128 v)
+{
+    if (v == 0)
+        return;
+    const unsigned long long lo = (unsigned long long)v;
+    const unsigned long long hi = (unsigned long long)(v >> 64);
+    const unsigned long long old = atomicAdd(lohi, lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry)
+        atomicAdd(lohi + 1, hi + carry);
+}
+
+__device__ __forceinline__ double i128_words_to_double(unsigned long long lo, unsigned long long hi)
+{
+    return __fma_rn((double)(long long)hi, 18446744073709551616.0, __ull2double_rn(lo));
+}
+
+struct Shared {
+    int diff_used;
+    int last;
+    unsigned long long ke[2], p[2], maxseg;
+    long long w64[NW];
+    long long hi[NW], lo[NW];
+    double da[NW], db[NW], dc[NW];
+    long long dm[NW];
 };
 
-#define K1_FIXED_BYTES ((sizeof(K1Shared) + 15) / 16 * 16)
+constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
 
-template <bool PUSH, bool DEPOSIT, bool PER_Q>
-__global__ void __launch_bounds__(SIC_K1_BLOCK, 2)
-    k_push_deposit(const SimDev *__restrict__ sims, const WorkItem *__restrict__ items,
-                   const int32_t *__restrict__ cta_begin, int nx_max, float kick_scale, int drift)
-{
-    constexpr int B = SIC_K1_BLOCK, R = SIC_K1_R, TILE = SIC_K1_TILE;
-    extern __shared__ __align__(16) unsigned char smem[];
-    K1Shared &sh = *reinterpret_cast<K1Shared *>(smem);
-    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smem + K1_FIXED_BYTES);
-    float2 *ek = reinterpret_cast<float2 *>(hist + nx_max);
-
-    const int tid = threadIdx.x;
-    const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
-    int cur = -1, nx = 0, parity = 0;
-    long long *U = nullptr;
-    float *V = nullptr;
-    const int32_t *Qh = nullptr;
-    unsigned long long *mesh = nullptr;
-    int64_t *edge_first = nullptr, *edge_last = nullptr;
-    ItemDiag *idiag = nullptr;
-    SimScalars *sc = nullptr;
-    NxDiv dv{};
-    bool range_err = false;
-
-    for (int it = ib; it < ie; ++it) {
-        const WorkItem W = items[it];
-        if (W.sim != cur) {
-            if (DEPOSIT && cur >= 0) {
-                __syncthreads();
-                for (int j = tid; j < nx; j += B) {
-                    const unsigned long long h = hist[j];
-                    if (h)
-                        atomicAdd(mesh + j, h);
-                }
-            }
-            if (range_err && sc) {
-                atomicOr(&sc->err, SIC_ERR_RANGE);
-                range_err = false;
-            }
-            __syncthreads();
-            cur = W.sim;
-            const SimDev &S = sims[cur];
-            U = reinterpret_cast<long long *>(S.U);
-            V = S.V;
-            Qh = S.Qh;
-            mesh = S.mesh;
-            edge_first = S.edge_first;
-            edge_last = S.edge_last;
-            idiag = S.item_diag;
-            sc = S.sc;
-            dv = S.div;
-            nx = dv.nx;
-            if (DEPOSIT)
-                for (int j = tid; j < nx; j += B)
-                    hist[j] = 0ull;
-            if (PUSH)
-                for (int j = tid; j < nx; j += B)
-                    ek[j] = S.Ek[j];
-            __syncthreads();
-        }
-
-        const int qs_uniform = 2 * W.qh;
-        const float qh_uniform = (float)W.qh;
-        float acc_a = 0.f, acc_b = 0.f;
-        long long maxseg = 0;
-        const int ntile = (W.count + TILE - 1) / TILE;
-        for (int tl = 0; tl < ntile; ++tl, parity ^= 1) {
-            const long long base = W.t0 + (long long)tl * TILE;
-            const int m = min(TILE, W.count - tl * TILE);
-            const int l0 = tid * R;
-            const int rn = max(0, min(R, m - l0));
-            long long u[R];
-            float v[R];
-            int q[R];
-            int jn[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                u[r] = 0;
-                v[r] = 0.f;
-                q[r] = 0;
-                jn[r] = 0;
-            }
-            if (rn == R) {
-                const longlong2 *pu = reinterpret_cast<const longlong2 *>(U + base + l0);
-#pragma unroll
-                for (int k = 0; k < R / 2; ++k) {
-                    const longlong2 t = pu[k];
-                    u[2 * k] = t.x;
-                    u[2 * k + 1] = t.y;
-                }
-                if (PUSH) {
-                    const float4 *pv = reinterpret_cast<const float4 *>(V + base + l0);
-#pragma unroll
-                    for (int k = 0; k < R / 4; ++k) {
-                        const float4 t = pv[k];
-                        v[4 * k] = t.x;
-                        v[4 * k + 1] = t.y;
-                        v[4 * k + 2] = t.z;
-                        v[4 * k + 3] = t.w;
-                    }
-                }
-                if (PER_Q) {
-                    const int4 *pq = reinterpret_cast<const int4 *>(Qh + base + l0);
-#pragma unroll
-                    for (int k = 0; k < R / 4; ++k) {
-                        const int4 t = pq[k];
-                        q[4 * k] = t.x;
-                        q[4 * k + 1] = t.y;
-                        q[4 * k + 2] = t.z;
-                        q[4 * k + 3] = t.w;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r < rn) {
-                        u[r] = U[base + l0 + r];
-                        if (PUSH)
-                            v[r] = V[base + l0 + r];
-                        if (PER_Q)
-                            q[r] = Qh[base + l0 + r];
-                    }
-                }
-            }
-
-            // gather (linear weighting), kick, drift
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (r < rn) {
-                    const int c = cell_of(u[r]);
-                    int j = wrap_cell(c, dv);
-                    if (PUSH) {
-                        const float f = __uint2float_rn(frac_of(u[r])) * 2.3283064365386963e-10f;
-                        const float2 e = ek[j];
-                        const float a = fmaf(f, e.y, e.x);
-                        const float vo = v[r];
-                        const float vn = fmaf(kick_scale, a, vo);
-                        const float qq = PER_Q ? (float)q[r] : qh_uniform;
-                        acc_a = fmaf(qq, fmaf(vo, vo, vn * vn), acc_a);
-                        acc_b = fmaf(qq, vo + vn, acc_b);
-                        v[r] = vn;
-                        if (drift) {
-                            const long long nu = u[r] + __float2ll_rn(vn * 4294967296.0f);
-                            const int cn = cell_of(nu);
-                            const int dc = cn - c;
-                            if (dc >= -nx && dc < nx) {
-                                int t = j + dc;
-                                t += (t < 0) ? nx : 0;
-                                t -= (t >= nx) ? nx : 0;
-                                j = t;
-                            } else {
-                                j = wrap_cell(cn, dv);
-                            }
-                            if ((unsigned)(cn + (1 << 30)) >= (1u << 31))
-                                range_err = true;
-                            u[r] = nu;
-                        }
-                    }
-                    jn[r] = j;
-                }
-            }
-
-            if (PUSH) {
-                if (rn == R) {
-                    if (drift) {
-                        longlong2 *pu = reinterpret_cast<longlong2 *>(U + base + l0);
-#pragma unroll
-                        for (int k = 0; k < R / 2; ++k)
-                            pu[k] = make_longlong2(u[2 * k], u[2 * k + 1]);
-                    }
-                    float4 *pv = reinterpret_cast<float4 *>(V + base + l0);
-#pragma unroll
-                    for (int k = 0; k < R / 4; ++k)
-                        pv[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (r < rn) {
-                            if (drift)
-                                U[base + l0 + r] = u[r];
-                            V[base + l0 + r] = v[r];
-                        }
-                    }
-                }
-            }
-
-            if (DEPOSIT) {
-                if (rn > 0) {
-                    sh.fu[parity][tid] = u[0];
-                    sh.fj[parity][tid] = jn[0];
-                    sh.fq[parity][tid] = q[0];
-                }
-                if (tl == 0 && tid == 0)
-                    edge_first[W.local] = u[0];
-                __syncthreads();
-                RunAcc acc(hist);
-                if (tid == 0 && tl > 0) {
-                    const int qs = PER_Q ? sh.pq[parity ^ 1] + q[0] : qs_uniform;
-                    const long long sp =
-                        emit_segment(sh.pu[parity ^ 1], sh.pj[parity ^ 1], u[0], jn[0], qs, nx, acc);
-                    maxseg = max(maxseg, sp);
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r < rn) {
-                        const int l = l0 + r;
-                        if (l + 1 < m) {
-                            long long ub;
-                            int jb, qb;
-                            if (r + 1 < R) {
-                                ub = u[r + 1];
-                                jb = jn[r + 1];
-                                qb = q[r + 1];
-                            } else {
-                                ub = sh.fu[parity][tid + 1];
-                                jb = sh.fj[parity][tid + 1];
-                                qb = sh.fq[parity][tid + 1];
-                            }
-                            const int qs = PER_Q ? q[r] + qb : qs_uniform;
-                            const long long sp = emit_segment(u[r], jn[r], ub, jb, qs, nx, acc);
-                            maxseg = max(maxseg, sp);
-                        } else if (tl + 1 < ntile) {
-                            sh.pu[parity] = u[r];
-                            sh.pj[parity] = jn[r];
-                            sh.pq[parity] = q[r];
-                        } else {
-                            edge_last[W.local] = u[r];
-                        }
-                    }
-                }
-                acc.flush();
-            }
-        }
-
-        // per-item diagnostics, reduced in a fixed order
-        double da = acc_a, db = acc_b;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            da += __shfl_down_sync(0xffffffffu, da, o);
-            db += __shfl_down_sync(0xffffffffu, db, o);
-            maxseg = max(maxseg, __shfl_down_sync(0xffffffffu, maxseg, o));
-        }
-        if ((tid & 31) == 0) {
-            sh.ra[tid >> 5] = da;
-            sh.rb[tid >> 5] = db;
-            sh.rm[tid >> 5] = maxseg;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            ItemDiag d;
-            d.ke = 0.0;
-            d.p = 0.0;
-            d.maxseg = 0;
-            d.pad = 0;
-            for (int w = 0; w < B / 32; ++w) {
-                d.ke += sh.ra[w];
-                d.p += sh.rb[w];
-                d.maxseg = max((long long)d.maxseg, sh.rm[w]);
-            }
-            idiag[W.local] = d;
-        }
-        __syncthreads();
-    }
-    if (DEPOSIT && cur >= 0) {
-        __syncthreads();
-        for (int j = tid; j < nx; j += B) {
-            const unsigned long long h = hist[j];
-            if (h)
-                atomicAdd(mesh + j, h);
-        }
-    }
-    if (range_err && sc)
-        atomicOr(&sc->err, SIC_ERR_RANGE);
-}
-
-// ---------------------------------------------------------------- K2 ----
+// ------------------------------------------------------------ epilogue ----
 
 __device__ __forceinline__ double i128_to_double(__int128 v)
 {
@@ -436,69 +273,30 @@ __device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int o)
     return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned long long)lo);
 }
 
-constexpr int K2_PER_MAX = (SIC_NX_MAX + SIC_K2_BLOCK - 1) / SIC_K2_BLOCK;
-
-__global__ void __launch_bounds__(SIC_K2_BLOCK)
-    k_field(const SimDev *__restrict__ sims, const FieldJob *__restrict__ jobs, int nx_max, int record)
+__device__ __forceinline__ __int128 make_i128(long long hi, long long lo)
 {
-    constexpr int B = SIC_K2_BLOCK, NW = B / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *sm = reinterpret_cast<unsigned long long *>(smem);
-    float *sE = reinterpret_cast<float *>(sm + nx_max);
-    __shared__ long long s_w[NW];
-    __shared__ long long s_hi[NW], s_lo[NW];
-    __shared__ double s_a[NW], s_b[NW], s_c[NW];
-    __shared__ long long s_m[NW];
-    __shared__ long long s_sumD_hi, s_sumD_lo;
-    __shared__ double s_we, s_ke, s_p;
-    __shared__ long long s_maxseg;
+    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned long long)lo);
+}
 
-    const SimDev &S = sims[jobs[blockIdx.x].slot];
-    const int nx = S.div.nx;
+// Field solve of one simulation (Sec. 2.1 with C = 1) by the block holding
+// its last ticket: sm (nx u64) and sE (nx floats) are this block's scratch.
+//   P_j = sum_{i<j} mesh_i, D_j = nx P_j - j Q (= nx sigma E'_j exactly),
+//   K_j = nx D_j - sum_j D_j (= nx^2 sigma E_j, zero mean), all integers;
+//   E_j = K_j E_scale, kick table Ek_j = K_j e_scale (one rounding each).
+__device__ void field_epilogue(const SimDev &S, int record, unsigned long long *sm, float *sE, Shared &sh)
+{
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
+    const int nx = S.div.nx;
     for (int j = tid; j < nx; j += B) {
-        sm[j] = S.mesh[j];
+        sm[j] = __ldcg(S.mesh + j);
         S.mesh[j] = 0ull;
     }
     __syncthreads();
-
-    // seams: the last segment of every item, whose far tracer another item moved
-    long long maxseg = 0;
-    {
-        RunAcc acc(sm);
-        for (int k = tid; k < S.n_items; k += B) {
-            const WorkItem W = S.items[k];
-            if (W.seam_next < 0)
-                continue;
-            const WorkItem Wn = S.items[W.seam_next];
-            const long long ua = S.edge_last[k];
-            const long long ub = S.edge_first[W.seam_next] + W.seam_shift;
-            const int qs = S.Qh ? S.Qh[W.t0 + W.count - 1] + S.Qh[Wn.t0] : W.qh + Wn.qh;
-            const int ja = wrap_cell(cell_of(ua), S.div);
-            const int jb = wrap_cell(cell_of(ub), S.div);
-            const long long sp = emit_segment(ua, ja, ub, jb, qs, nx, acc);
-            maxseg = max(maxseg, sp);
-        }
-        acc.flush();
-    }
-    // longest segment over the items as well
-    for (int k = tid; k < S.n_items; k += B)
-        maxseg = max(maxseg, (long long)S.item_diag[k].maxseg);
-    __syncthreads();
-
-    // exact prefix sums P_j = sum_{i<j} mesh_i over each thread's run of cells
     const int per = (nx + B - 1) / B;
-    const int j0 = tid * per;
-    long long loc[K2_PER_MAX];
+    const int j0 = min(tid * per, nx), j1 = min(j0 + per, nx);
     long long lsum = 0;
-#pragma unroll
-    for (int k = 0; k < K2_PER_MAX; ++k) {
-        const int j = j0 + k;
-        const long long mv = (k < per && j < nx) ? (long long)sm[j] : 0;
-        loc[k] = mv;
-        lsum += mv;
-    }
+    for (int j = j0; j < j1; ++j)
+        lsum += (long long)sm[j];
     long long incl = lsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -507,135 +305,471 @@ __global__ void __launch_bounds__(SIC_K2_BLOCK)
             incl += t;
     }
     if (lane == 31)
-        s_w[warp] = incl;
+        sh.w64[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        long long wv = lane < NW ? s_w[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, wv, o);
-            if (lane >= o)
-                wv += t;
-        }
-        if (lane < NW)
-            s_w[lane] = wv;
+    long long before = 0, qtot = 0;
+    for (int w = 0; w < NW; ++w) {
+        if (w < warp)
+            before += sh.w64[w];
+        qtot += sh.w64[w];
     }
-    __syncthreads();
-    const long long qtot = s_w[NW - 1];
-    const long long run0 = incl - lsum + (warp > 0 ? s_w[warp - 1] : 0);
+    const long long run0 = incl - lsum + before;
 
-    // D_j = nx P_j - j Q  (= nx sigma E'_j, exact) and its sum over the mesh
     __int128 dsum = 0;
     {
         long long run = run0;
-#pragma unroll
-        for (int k = 0; k < K2_PER_MAX; ++k) {
-            const int j = j0 + k;
-            if (k < per && j < nx) {
-                dsum += (__int128)nx * run - (__int128)j * qtot;
-                run += loc[k];
-            }
+        for (int j = j0; j < j1; ++j) {
+            dsum += (__int128)nx * run - (__int128)j * qtot;
+            run += (long long)sm[j];
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         dsum += shfl_down_i128(dsum, o);
     if (lane == 0) {
-        s_hi[warp] = (long long)(dsum >> 64);
-        s_lo[warp] = (long long)(unsigned long long)dsum;
+        sh.hi[warp] = (long long)(dsum >> 64);
+        sh.lo[warp] = (long long)(unsigned long long)dsum;
     }
     __syncthreads();
-    if (tid == 0) {
-        __int128 t = 0;
-        for (int w = 0; w < NW; ++w)
-            t += (__int128)(((unsigned __int128)(unsigned long long)s_hi[w] << 64) |
-                            (unsigned long long)s_lo[w]);
-        s_sumD_hi = (long long)(t >> 64);
-        s_sumD_lo = (long long)(unsigned long long)t;
-    }
-    __syncthreads();
-    const __int128 sumD = (__int128)(((unsigned __int128)(unsigned long long)s_sumD_hi << 64) |
-                                     (unsigned long long)s_sumD_lo);
+    __int128 sumD = 0;
+    for (int w = 0; w < NW; ++w)
+        sumD += make_i128(sh.hi[w], sh.lo[w]);
 
-    // K_j = nx D_j - sum D = nx^2 sigma E_j: one rounding to double, one to float
     double wloc = 0.0;
     {
         long long run = run0;
-#pragma unroll
-        for (int k = 0; k < K2_PER_MAX; ++k) {
-            const int j = j0 + k;
-            if (k < per && j < nx) {
-                const __int128 d = (__int128)nx * run - (__int128)j * qtot;
-                const double kd = i128_to_double((__int128)nx * d - sumD);
-                const double e = kd * S.E_scale;
-                S.E64[j] = e;
-                S.mesh_last[j] = loc[k];
-                S.rho64[j] = i128_to_double((__int128)nx * loc[k] - qtot) * S.rho_scale;
-                sE[j] = (float)(kd * S.e_scale);
-                wloc += e * e;
-                run += loc[k];
-            }
-        }
-    }
-    double ka = 0.0, pb = 0.0;
-    if (record) {
-        for (int k = tid; k < S.n_items; k += B) {
-            ka += S.item_diag[k].ke;
-            pb += S.item_diag[k].p;
+        for (int j = j0; j < j1; ++j) {
+            const long long mj = (long long)sm[j];
+            const __int128 d = (__int128)nx * run - (__int128)j * qtot;
+            const double kd = i128_to_double((__int128)nx * d - sumD);
+            const double e = kd * S.E_scale;
+            S.E64[j] = e;
+            S.mesh_last[j] = mj;
+            S.rho64[j] = i128_to_double((__int128)nx * mj - qtot) * S.rho_scale;
+            sE[j] = (float)(kd * S.e_scale);
+            wloc += e * e;
+            run += mj;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1)
         wloc += __shfl_down_sync(0xffffffffu, wloc, o);
-        ka += __shfl_down_sync(0xffffffffu, ka, o);
-        pb += __shfl_down_sync(0xffffffffu, pb, o);
-        maxseg = max(maxseg, __shfl_down_sync(0xffffffffu, maxseg, o));
-    }
-    if (lane == 0) {
-        s_a[warp] = wloc;
-        s_b[warp] = ka;
-        s_m[warp] = maxseg;
-        s_hi[warp] = 0;
-    }
-    if (lane == 0)
-        s_c[warp] = pb;
     __syncthreads();
-    if (tid == 0) {
-        double w = 0.0, kk = 0.0, pp = 0.0;
-        long long mm = 0;
-        for (int i = 0; i < NW; ++i) {
-            w += s_a[i];
-            kk += s_b[i];
-            pp += s_c[i];
-            mm = max(mm, s_m[i]);
-        }
-        s_we = w * S.half_dx;
-        s_ke = kk;
-        s_p = pp;
-        s_maxseg = mm;
-    }
+    if (lane == 0)
+        sh.da[warp] = wloc;
     __syncthreads();
     for (int j = tid; j < nx; j += B) {
-        const int j1 = (j + 1 == nx) ? 0 : j + 1;
-        S.Ek[j] = make_float2(sE[j], sE[j1] - sE[j]);
+        const int j1n = (j + 1 == nx) ? 0 : j + 1;
+        S.Ek[j] = make_float2(sE[j], sE[j1n] - sE[j]);
     }
     if (tid == 0) {
+        double w = 0.0;
+        for (int i = 0; i < NW; ++i)
+            w += sh.da[i];
+        SimAccum *ac = S.acc;
+        const double kk = i128_words_to_double(__ldcg(&ac->ke[0]), __ldcg(&ac->ke[1])) * 2.3283064365386963e-10;
+        const double pp = i128_words_to_double(__ldcg(&ac->p[0]), __ldcg(&ac->p[1])) * 2.3283064365386963e-10;
+        const long long mm = (long long)__ldcg(&ac->maxseg);
+        ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
         SimScalars *sc = S.sc;
         if (record) {
             const long long step = sc->step;
             double *row = S.hist + 4 * (step % S.hist_len);
             row[0] = sc->we;
-            row[1] = S.ke_scale * s_ke;
-            row[2] = S.p_scale * s_p;
+            row[1] = S.ke_scale * kk;
+            row[2] = S.p_scale * pp;
             row[3] = (double)sc->q_total;
             sc->step = step + 1;
         }
-        sc->we = s_we;
+        sc->we = w * S.half_dx;
         sc->q_total = qtot;
-        sc->maxseg = s_maxseg;
-        if (S.strict && s_maxseg > ((long long)nx << 32))
+        sc->maxseg = mm;
+        if (S.strict && mm > ((long long)nx << 32))
             sc->err |= SIC_ERR_SEGLONG;
     }
+}
+
+// inclusive prefix sum of diff[0..nx) added into hist (block-wide)
+__device__ void add_diff_prefix(unsigned long long *hist, unsigned long long *diff, int nx, Shared &sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (nx + B - 1) / B;
+    const int j0 = min(tid * per, nx), j1 = min(j0 + per, nx);
+    long long lsum = 0;
+    for (int j = j0; j < j1; ++j)
+        lsum += (long long)diff[j];
+    long long incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += t;
+    }
+    if (lane == 31)
+        sh.w64[warp] = incl;
+    __syncthreads();
+    long long run = incl - lsum;
+    for (int w = 0; w < warp; ++w)
+        run += sh.w64[w];
+    for (int j = j0; j < j1; ++j) {
+        run += (long long)diff[j];
+        hist[j] += (unsigned long long)run;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernel ----
+
+// One work item (up to 256 tracers, 8 per lane) of the current simulation.
+// FULL: the item has all 256 tracers, so no lane needs a bounds test.
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL>
+__device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
+                                        const float *__restrict__ Vin, long long *__restrict__ Uout,
+                                        float *__restrict__ Vout, const int32_t *__restrict__ Qh,
+                                        const float2 *ek, unsigned long long *hist, unsigned long long *diff,
+                                        Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = dv.nx;
+    const int m = FULL ? WT : W.count;
+    const long long base = W.t0;
+    const int l0 = lane * R;
+    const int rn = FULL ? R : max(0, min(R, m - l0));
+    const int lane_last = FULL ? 31 : (m - 1) / R;
+
+    long long u[R];
+    float v[R];
+    int q[R];
+    int jn[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        u[r] = 0;
+        v[r] = 0.f;
+        q[r] = W.qh;
+        jn[r] = 0;
+    }
+    // the tracer after the item's last one (next item, or the sheet's first)
+    long long hu = 0;
+    float hv = 0.f;
+    int hq = W.qh, hj = 0;
+    bool has_halo = false;
+    if (DEPOSIT && lane == lane_last && W.halo >= 0) {
+        has_halo = true;
+        hu = Uin[W.halo];
+        if (PUSH)
+            hv = Vin[W.halo];
+        if (PER_Q)
+            hq = Qh[W.halo];
+    }
+    if (FULL || rn == R) {
+        const longlong2 *pu = reinterpret_cast<const longlong2 *>(Uin + base + l0);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const longlong2 t = pu[k];
+            u[2 * k] = t.x;
+            u[2 * k + 1] = t.y;
+        }
+        if (PUSH) {
+            const float4 *pv = reinterpret_cast<const float4 *>(Vin + base + l0);
+#pragma unroll
+            for (int k = 0; k < R / 4; ++k) {
+                const float4 t = pv[k];
+                v[4 * k] = t.x;
+                v[4 * k + 1] = t.y;
+                v[4 * k + 2] = t.z;
+                v[4 * k + 3] = t.w;
+            }
+        }
+        if (PER_Q) {
+            const int4 *pq = reinterpret_cast<const int4 *>(Qh + base + l0);
+#pragma unroll
+            for (int k = 0; k < R / 4; ++k) {
+                const int4 t = pq[k];
+                q[4 * k] = t.x;
+                q[4 * k + 1] = t.y;
+                q[4 * k + 2] = t.z;
+                q[4 * k + 3] = t.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r < rn) {
+                u[r] = Uin[base + l0 + r];
+                if (PUSH)
+                    v[r] = Vin[base + l0 + r];
+                if (PER_Q)
+                    q[r] = Qh[base + l0 + r];
+            }
+        }
+    }
+
+    float acc_a = 0.f, acc_b = 0.f;
+    if (PUSH) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (FULL || r < rn) {
+                const float vo = v[r];
+                push_one<POW2>(u[r], v[r], jn[r], ek, dv, ks, drift, rerr);
+                const float vn = v[r];
+                if (PER_Q) {
+                    const float qq = __int2float_rn(q[r]);
+                    acc_a = __fmaf_rn(qq, __fmaf_rn(vo, vo, __fmul_rn(vn, vn)), acc_a);
+                    acc_b = __fmaf_rn(qq, __fadd_rn(vo, vn), acc_b);
+                } else {
+                    acc_a = __fmaf_rn(vo, vo, __fmaf_rn(vn, vn, acc_a));
+                    acc_b = __fadd_rn(acc_b, __fadd_rn(vo, vn));
+                }
+            }
+        }
+        if (has_halo) {
+            unsigned ignore = 0;
+            push_one<POW2>(hu, hv, hj, ek, dv, ks, drift, ignore);
+        }
+        if (FULL || rn == R) {
+            longlong2 *pu = reinterpret_cast<longlong2 *>(Uout + base + l0);
+#pragma unroll
+            for (int k = 0; k < R / 2; ++k)
+                pu[k] = make_longlong2(u[2 * k], u[2 * k + 1]);
+            float4 *pv = reinterpret_cast<float4 *>(Vout + base + l0);
+#pragma unroll
+            for (int k = 0; k < R / 4; ++k)
+                pv[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < rn) {
+                    Uout[base + l0 + r] = u[r];
+                    Vout[base + l0 + r] = v[r];
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (FULL || r < rn)
+                jn[r] = wrap_cell<POW2>(cell_of(u[r]), dv);
+        if (has_halo)
+            hj = wrap_cell<POW2>(cell_of(hu), dv);
+    }
+
+    long long maxseg = 0;
+    if (DEPOSIT) {
+        hu += W.halo_shift;  // closing segment: the sheet's first tracer one winding on
+        // the next tracer of each lane's last one comes from the lane above
+        const long long nu = __shfl_down_sync(0xffffffffu, u[0], 1);
+        const int nj = __shfl_down_sync(0xffffffffu, jn[0], 1);
+        const int nq = __shfl_down_sync(0xffffffffu, q[0], 1);
+        RunAcc acc(hist);
+        const int qs_sheet = 2 * W.qh;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (FULL || r < rn) {
+                long long ub;
+                int jb, qb;
+                bool seg = true;
+                if (r + 1 < R && (FULL || r + 1 < rn)) {
+                    ub = u[r + 1 < R ? r + 1 : r];
+                    jb = jn[r + 1 < R ? r + 1 : r];
+                    qb = q[r + 1 < R ? r + 1 : r];
+                } else if (lane < lane_last) {
+                    ub = nu;
+                    jb = nj;
+                    qb = nq;
+                } else {
+                    ub = hu;
+                    jb = hj;
+                    qb = hq;
+                    seg = has_halo;
+                }
+                if (seg)
+                    emit_segment(u[r], jn[r], ub, jb, PER_Q ? q[r] + qb : qs_sheet, nx, acc, diff,
+                                 &sh.diff_used, maxseg);
+            }
+        }
+        acc.flush();
+    }
+
+    // this item's kinetic-energy and momentum sums, in a fixed lane order,
+    // then exactly into the block's 128-bit accumulators
+    if (PUSH) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_a += __shfl_down_sync(0xffffffffu, acc_a, o);
+            acc_b += __shfl_down_sync(0xffffffffu, acc_b, o);
+        }
+        if (lane == 0) {
+            if (!PER_Q) {
+                const float qq = __int2float_rn(W.qh);
+                acc_a = __fmul_rn(acc_a, qq);
+                acc_b = __fmul_rn(acc_b, qq);
+            }
+            atomic_add_i128(sh.ke, f32_to_fix(acc_a));
+            atomic_add_i128(sh.p, f32_to_fix(acc_b));
+        }
+    }
+    if (DEPOSIT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            maxseg = max(maxseg, __shfl_down_sync(0xffffffffu, maxseg, o));
+        if (lane == 0 && maxseg)
+            atomicMax(&sh.maxseg, (unsigned long long)maxseg);
+    }
+}
+
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2>
+__global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Shared &sh = *reinterpret_cast<Shared *>(smem);
+    const int nx_max = A.nx_max;
+    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smem + kSharedHead);
+    unsigned long long *diff = hist + nx_max;  // nx_max + 2 entries
+    float2 *ek = reinterpret_cast<float2 *>(diff + nx_max + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int ib = A.cta_begin[blockIdx.x], ie = A.cta_begin[blockIdx.x + 1];
+    const float ks = A.kick_scale;
+    const int drift = A.drift;
+
+    for (int it0 = ib; it0 < ie;) {
+        // enter the next simulation of this block's run of items
+        const int cur = A.items[it0].sim;
+        const SimDev &S = A.sims[cur];
+        const NxDiv dv = S.div;
+        const int nx = dv.nx;
+        const int src = (int)S.sc->buf;
+        const long long *Uin = reinterpret_cast<const long long *>(S.U[src]);
+        const float *Vin = S.V[src];
+        long long *Uout = reinterpret_cast<long long *>(S.U[src ^ 1]);
+        float *Vout = S.V[src ^ 1];
+        const int32_t *Qh = S.Qh;
+        if (DEPOSIT) {
+            for (int j = tid; j < nx; j += B)
+                hist[j] = 0ull;
+            for (int j = tid; j < nx + 2; j += B)
+                diff[j] = 0ull;
+        }
+        if (tid == 0) {
+            sh.diff_used = 0;
+            sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
+        }
+        if (PUSH)
+            for (int j = tid; j < nx; j += B)
+                ek[j] = S.Ek[j];
+        __syncthreads();
+
+        const int run_end = min(A.slot_end[cur], ie);
+        unsigned rerr = 0;
+        for (int it = it0 + warp; it < run_end; it += NW) {
+            const WorkItem W = A.items[it];
+            if (W.count == WT)
+                do_item<PUSH, DEPOSIT, PER_Q, POW2, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh, dv, ks,
+                                                          drift, rerr);
+            else
+                do_item<PUSH, DEPOSIT, PER_Q, POW2, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh, dv, ks,
+                                                           drift, rerr);
+        }
+
+        // leave the simulation: fold the block's mesh and sums into the
+        // global ones, take a ticket, run the epilogue if it is the last one
+        __syncthreads();
+        if (DEPOSIT) {
+            if (sh.diff_used)
+                add_diff_prefix(hist, diff, nx, sh);
+            for (int j = tid; j < nx; j += B) {
+                const unsigned long long h = hist[j];
+                if (h)
+                    atomicAdd(S.mesh + j, h);
+            }
+        }
+        if (rerr >> 31)
+            atomicOr(&S.sc->err, SIC_ERR_RANGE);
+        if (tid == 0) {
+            SimAccum *ac = S.acc;
+            atomic_add_i128(ac->ke, (__int128)(((unsigned __int128)sh.ke[1] << 64) | sh.ke[0]));
+            atomic_add_i128(ac->p, (__int128)(((unsigned __int128)sh.p[1] << 64) | sh.p[0]));
+            if (sh.maxseg)
+                atomicMax(&ac->maxseg, sh.maxseg);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned t = atomicAdd(A.tickets + cur, 1u);
+            sh.last = (t + 1 == (unsigned)A.expected[cur]) ? 1 : 0;
+        }
+        __syncthreads();
+        if (sh.last) {
+            __threadfence();
+            if (DEPOSIT)
+                field_epilogue(S, A.record, hist, reinterpret_cast<float *>(ek), sh);
+            if (tid == 0) {
+                if (PUSH)
+                    S.sc->buf = (unsigned)(src ^ 1);
+                if (!DEPOSIT) {  // the epilogue did not consume the sums: drop them
+                    SimAccum *ac = S.acc;
+                    ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
+                }
+                A.tickets[cur] = 0u;
+            }
+        }
+        __syncthreads();
+        it0 = run_end;
+    }
+}
+
+template <bool P, bool D, bool Q, bool T>
+cudaError_t prep(size_t smem)
+{
+    static size_t done = 0;
+    if (smem > done) {
+        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        done = smem;
+    }
+    return cudaSuccess;
+}
+
+template <bool P, bool D, bool Q, bool T>
+cudaError_t run(const LaunchArgs &a, int grid, cudaStream_t s)
+{
+    const size_t smem = step_smem_bytes(a.nx_max);
+    cudaError_t e = prep<P, D, Q, T>(smem);
+    if (e != cudaSuccess)
+        return e;
+    k_step<P, D, Q, T><<<grid, B, smem, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <bool P, bool D, bool Q, bool T>
+int occ(int nx_max)
+{
+    const size_t smem = step_smem_bytes(nx_max);
+    if (prep<P, D, Q, T>(smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, T>, B, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <bool P, bool D>
+cudaError_t run_pd(const LaunchArgs &a, int grid, bool per_q, bool pow2, cudaStream_t s)
+{
+    if (per_q)
+        return pow2 ? run<P, D, true, true>(a, grid, s) : run<P, D, true, false>(a, grid, s);
+    return pow2 ? run<P, D, false, true>(a, grid, s) : run<P, D, false, false>(a, grid, s);
+}
+
+template <bool P, bool D>
+int occ_pd(int nx_max, bool per_q, bool pow2)
+{
+    if (per_q)
+        return pow2 ? occ<P, D, true, true>(nx_max) : occ<P, D, true, false>(nx_max);
+    return pow2 ? occ<P, D, false, true>(nx_max) : occ<P, D, false, false>(nx_max);
 }
 
 __global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int32_t n, const float *vs,
@@ -651,92 +785,40 @@ __global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int
     }
 }
 
-template <bool P, bool D, bool Q>
-cudaError_t prep_k1(size_t smem)
-{
-    static size_t done = 0;
-    if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(k_push_deposit<P, D, Q>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        done = smem;
-    }
-    return cudaSuccess;
-}
-
-template <bool P, bool D, bool Q>
-cudaError_t run_k1(const SimDev *sims, const WorkItem *items, const int32_t *cta, int grid, int nx_max,
-                   float ks, int drift, cudaStream_t s)
-{
-    const size_t smem = k1_smem_bytes(nx_max);
-    cudaError_t e = prep_k1<P, D, Q>(smem);
-    if (e != cudaSuccess)
-        return e;
-    k_push_deposit<P, D, Q><<<grid, SIC_K1_BLOCK, smem, s>>>(sims, items, cta, nx_max, ks, drift);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template <bool P, bool D, bool Q>
-int occ_k1(int nx_max)
-{
-    const size_t smem = k1_smem_bytes(nx_max);
-    if (prep_k1<P, D, Q>(smem) != cudaSuccess)
-        return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push_deposit<P, D, Q>, SIC_K1_BLOCK, smem) !=
-        cudaSuccess)
-        return 0;
-    return n;
-}
-
 }  // namespace
 
-size_t k1_smem_bytes(int nx_max) { return K1_FIXED_BYTES + (size_t)16 * nx_max; }
+size_t step_smem_bytes(int nx_max)
+{
+    // shared head, hist[nx], diff[nx + 2], ek[nx] (the epilogue reuses hist and ek)
+    return kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
+}
 
 static long long g_launches = 0;
 void count_launches(int64_t n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
 int64_t launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
-cudaError_t launch_push_deposit(const SimDev *sims, const WorkItem *items, const int32_t *cta_begin, int grid,
-                                int nx_max, bool push, bool deposit, bool per_q, float kick_scale, int drift,
-                                cudaStream_t s)
+cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s)
 {
-    if (push && deposit)
-        return per_q ? run_k1<true, true, true>(sims, items, cta_begin, grid, nx_max, kick_scale, drift, s)
-                     : run_k1<true, true, false>(sims, items, cta_begin, grid, nx_max, kick_scale, drift, s);
-    if (deposit)
-        return per_q ? run_k1<false, true, true>(sims, items, cta_begin, grid, nx_max, kick_scale, drift, s)
-                     : run_k1<false, true, false>(sims, items, cta_begin, grid, nx_max, kick_scale, drift, s);
-    return per_q ? run_k1<true, false, true>(sims, items, cta_begin, grid, nx_max, kick_scale, drift, s)
-                 : run_k1<true, false, false>(sims, items, cta_begin, grid, nx_max, kick_scale, drift, s);
-}
-
-int k1_blocks_per_sm(int nx_max, bool push, bool deposit, bool per_q)
-{
-    if (push && deposit)
-        return per_q ? occ_k1<true, true, true>(nx_max) : occ_k1<true, true, false>(nx_max);
-    if (deposit)
-        return per_q ? occ_k1<false, true, true>(nx_max) : occ_k1<false, true, false>(nx_max);
-    return per_q ? occ_k1<true, false, true>(nx_max) : occ_k1<true, false, false>(nx_max);
-}
-
-cudaError_t launch_field(const SimDev *sims, const FieldJob *jobs, int n_jobs, int nx_max, int record,
-                         cudaStream_t s)
-{
-    const size_t smem = (size_t)12 * nx_max;
-    static size_t done = 0;
-    if (smem > done) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        done = smem;
+    switch (mode) {
+    case MODE_STEP:
+        return run_pd<true, true>(a, grid, per_q, pow2, s);
+    case MODE_DEPOSIT:
+        return run_pd<false, true>(a, grid, per_q, pow2, s);
+    default:
+        return run_pd<true, false>(a, grid, per_q, pow2, s);
     }
-    k_field<<<n_jobs, SIC_K2_BLOCK, smem, s>>>(sims, jobs, nx_max, record);
-    count_launches(1);
-    return cudaGetLastError();
+}
+
+int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2)
+{
+    switch (mode) {
+    case MODE_STEP:
+        return occ_pd<true, true>(nx_max, per_q, pow2);
+    case MODE_DEPOSIT:
+        return occ_pd<false, true>(nx_max, per_q, pow2);
+    default:
+        return occ_pd<true, false>(nx_max, per_q, pow2);
+    }
 }
 
 cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,

@@ -27,7 +27,7 @@ SIC_NX_MAX = 8192
 # every symbol include/sic.h declares
 EXPORTS = [
     "sic_create", "sic_create_horizontal", "sic_deposit", "sic_field", "sic_push", "sic_step",
-    "sic_step_phase", "sic_step_batch", "sic_diagnostics", "sic_history", "sic_get_state", "sic_device_state",
+    "sic_step_batch", "sic_diagnostics", "sic_history", "sic_get_state", "sic_device_state",
     "sic_sync", "sic_destroy", "sic_strerror", "sic_launch_count",
 ]
 
@@ -76,7 +76,6 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_field": ([simp, dp], ctypes.c_int),
         "sic_push": ([simp], ctypes.c_int),
         "sic_step": ([simp, ctypes.c_int32], ctypes.c_int),
-        "sic_step_phase": ([simp, ctypes.c_int32], ctypes.c_int),
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
         "sic_history": ([simp, dp, ip], ctypes.c_int),
@@ -224,9 +223,6 @@ class Sim:
 
     def sic_step(self, n_steps: int):
         _check(_lib.sic_step(self.handle, int(n_steps)), "sic_step")
-
-    def sic_step_phase(self, phase: int):
-        _check(_lib.sic_step_phase(self.handle, int(phase)), "sic_step_phase")
 
     def sic_diagnostics(self) -> dict:
         d = sic_diag()

@@ -87,7 +87,11 @@ def test_deposit_irregular_sheets(sic, seed):
 
 
 def test_single_segments_exact(sic):
-    """Dyadic segments: the fixed-point pieces equal the exact overlaps."""
+    """Dyadic segments: the fixed-point pieces equal the exact overlaps.
+
+    Whole cells inside a segment get floor(q 2^32 / span) units each, so the
+    last cell carries the remainder: at most one unit per inside cell, plus
+    the FP32 rounding of the first cut (~2e-7 q)."""
     nx, L = 8, 8.0
     cases = [([1.25, 1.75], [0, 1, 0, 0, 0, 0, 0, 0]),
              ([4.0, 1.0], [0, 1 / 3, 1 / 3, 1 / 3, 0, 0, 0, 0]),
@@ -102,7 +106,8 @@ def test_single_segments_exact(sic):
             mesh, _ = sim.sic_deposit()
             unit = sim.sic_diagnostics()["charge_unit"]
             got = mesh * unit
-            np.testing.assert_allclose(got, want, rtol=0, atol=4e-7 * max(want))
+            inside = abs(x[1] - x[0]) / (L / nx)
+            np.testing.assert_allclose(got, want, rtol=0, atol=(inside + 2) * unit + 2.5e-7)
             assert int(mesh.sum()) * unit == 1.0
         finally:
             sim.sic_destroy()
@@ -259,13 +264,12 @@ def test_strict_mode_reports_long_segment(sic):
         sim.sic_destroy()
 
 
-def test_item_size_and_grid_do_not_change_results(sic, monkeypatch):
-    """Multi-tile work items (the carried segment between tiles) and other grid
-    shapes give bit-identical states, meshes and field energies."""
+def test_grid_shape_does_not_change_results(sic, monkeypatch):
+    """Other block counts (down to one block doing everything) give
+    bit-identical states, meshes and diagnostic histories."""
     p = inputs.tiny_problem(21, n_sheets=4, max_tracers=9000, nx=300, L=2.0)
     runs = []
-    for tiles, grid in [("1", ""), ("3", ""), ("2", "7"), ("1", "1")]:
-        monkeypatch.setenv("SIC_ITEM_TILES", tiles)
+    for grid in ["", "7", "1", "33"]:
         monkeypatch.setenv("SIC_GRID", grid)
         sim = sic.Sim.from_problem(p, history_len=8)
         sim.sic_step(6)
@@ -276,5 +280,4 @@ def test_item_size_and_grid_do_not_change_results(sic, monkeypatch):
         np.testing.assert_array_equal(x, x0)
         np.testing.assert_array_equal(v, v0)
         np.testing.assert_array_equal(m, m0)
-        np.testing.assert_array_equal(h[:, 0], h0[:, 0])
-        np.testing.assert_allclose(h[:, 1:3], h0[:, 1:3], rtol=1e-6)
+        np.testing.assert_array_equal(h, h0)
