@@ -318,6 +318,8 @@ int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
         return SIC_ERANGE;
     if (sc.err & SIC_ERR_SEGLONG)
         return SIC_ESEGMENT_LONG;
+    if (sc.err & SIC_ERR_TIMEOUT)
+        return SIC_ETIMEOUT;
     return SIC_OK;
 }
 

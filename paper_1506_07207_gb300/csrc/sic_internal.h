@@ -33,6 +33,14 @@
 // error bits raised on the device
 #define SIC_ERR_RANGE 1u
 #define SIC_ERR_SEGLONG 2u
+#define SIC_ERR_TIMEOUT 4u
+
+// Per-warp double-buffered staging of the next work item in shared memory
+// (filled by bulk copies): positions, velocities and, per-tracer charge mode,
+// half charges, each with room for the item's 256 tracers plus its halo.
+#define SIC_STAGE_U_BYTES 2064
+#define SIC_STAGE_V_BYTES 1040
+#define SIC_STAGE_Q_BYTES 1040
 
 // periodic cell reduction by a precomputed multiplier (unsigned division by
 // an invariant integer: q = (t + ((n - t) >> 1)) >> (l - 1), t = umulhi(m, n))
@@ -123,7 +131,8 @@ cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_temp
                                      const float *v_sheet, const int64_t *sheet_offset, int32_t n_sheets,
                                      cudaStream_t s);
 int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2);
-size_t step_smem_bytes(int nx_max);
+size_t step_smem_bytes(int nx_max, bool staged, bool per_q);
+bool step_staged(int nx_max, bool per_q);
 void count_launches(int64_t n);
 int64_t launches();
 }  // namespace sic

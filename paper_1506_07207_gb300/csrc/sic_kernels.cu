@@ -101,13 +101,39 @@ __device__ __forceinline__ void push_one(long long &u, float &v, int &j, const f
     }
 }
 
+// The block's copy of the charge mesh: cell j holds hi[j] * 2^32 + lo[j].
+// Adds use 32-bit shared-memory atomics (a carry out of the low word goes to
+// the high word), which the hardware executes natively.
+struct Hist {
+    unsigned *lo;
+    unsigned *hi;
+    __device__ __forceinline__ void add(int j, long long v) const
+    {
+        const unsigned l = (unsigned)(unsigned long long)v;
+        const unsigned h = (unsigned)((unsigned long long)v >> 32);
+        const unsigned old = atomicAdd(lo + j, l);
+        const unsigned c = h + ((old + l < old) ? 1u : 0u);
+        if (c)
+            atomicAdd(hi + j, c);
+    }
+    __device__ __forceinline__ unsigned long long get(int j) const
+    {
+        return ((unsigned long long)hi[j] << 32) | lo[j];
+    }
+    __device__ __forceinline__ void set(int j, unsigned long long v) const
+    {
+        lo[j] = (unsigned)v;
+        hi[j] = (unsigned)(v >> 32);
+    }
+};
+
 // Per-thread run of consecutive contributions to one cell; a cell change
-// commits the run with one shared-memory int64 atomic.
+// commits the run to the block's mesh.
 struct RunAcc {
-    unsigned long long *h;
+    Hist h;
     int cell;
     long long sum;
-    __device__ __forceinline__ explicit RunAcc(unsigned long long *hist) : h(hist), cell(-1), sum(0) {}
+    __device__ __forceinline__ explicit RunAcc(const Hist &hist) : h(hist), cell(-1), sum(0) {}
     __device__ __forceinline__ void add(int j, long long v)
     {
         if (j == cell) {
@@ -115,14 +141,14 @@ struct RunAcc {
             return;
         }
         if (sum)
-            atomicAdd(h + cell, (unsigned long long)sum);
+            h.add(cell, sum);
         cell = j;
         sum = v;
     }
     __device__ __forceinline__ void flush()
     {
         if (sum)
-            atomicAdd(h + cell, (unsigned long long)sum);
+            h.add(cell, sum);
         sum = 0;
         cell = -1;
     }
@@ -243,7 +269,84 @@ __device__ __forceinline__ double i128_words_to_double(unsigned long long lo, un
     return __fma_rn((double)(long long)hi, 18446744073709551616.0, __ull2double_rn(lo));
 }
 
+// ---- bulk-copy staging (cp.async.bulk into shared memory, mbarrier completion)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// A bounded wait on a stage barrier: true once the phase of this parity has
+// completed; false after about a second of polling (the caller raises an
+// error instead of hanging).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+{
+    for (int i = 0; i < (1 << 24); ++i)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+constexpr int kStageBytesU = SIC_STAGE_U_BYTES;
+constexpr int kStageBytesV = SIC_STAGE_V_BYTES;
+constexpr int kStageBytesQ = SIC_STAGE_Q_BYTES;
+
+template <bool PER_Q>
+struct StageBytes {
+    static constexpr int value = kStageBytesU + kStageBytesV + (PER_Q ? kStageBytesQ : 0);
+};
+
+// Lane 0 of a warp: start the bulk copies of item W (and its halo when the
+// halo is the next tracer in memory) into one stage.
+template <bool PER_Q>
+__device__ __forceinline__ void stage_issue(const WorkItem &W, const long long *Uin, const float *Vin,
+                                            const int32_t *Qh, char *st, unsigned long long *bar)
+{
+    const bool contiguous_halo = (W.halo == W.t0 + W.count);
+    const int n = W.count + (contiguous_halo ? 1 : 0);
+    const unsigned bu = (unsigned)(n * 8 + 15) & ~15u;
+    const unsigned bv = (unsigned)(n * 4 + 15) & ~15u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, bu + bv + (PER_Q ? bv : 0u));
+    bulk_g2s(st, Uin + W.t0, bu, bar);
+    bulk_g2s(st + kStageBytesU, Vin + W.t0, bv, bar);
+    if (PER_Q)
+        bulk_g2s(st + kStageBytesU + kStageBytesV, Qh + W.t0, bv, bar);
+}
+
 struct Shared {
+    unsigned long long mbar[NW][2];
     int diff_used;
     int last;
     unsigned long long ke[2], p[2], maxseg;
@@ -254,6 +357,14 @@ struct Shared {
 };
 
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
+
+// shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx]; staging starts on a
+// 128-byte boundary (bulk copies need 16)
+__host__ __device__ __forceinline__ size_t stage_offset(int nx_max)
+{
+    const size_t end = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
+    return (end + 127) / 128 * 128;
+}
 
 // ------------------------------------------------------------ epilogue ----
 
@@ -390,7 +501,7 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
 }
 
 // inclusive prefix sum of diff[0..nx) added into hist (block-wide)
-__device__ void add_diff_prefix(unsigned long long *hist, unsigned long long *diff, int nx, Shared &sh)
+__device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int nx, Shared &sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (nx + B - 1) / B;
@@ -413,7 +524,7 @@ __device__ void add_diff_prefix(unsigned long long *hist, unsigned long long *di
         run += sh.w64[w];
     for (int j = j0; j < j1; ++j) {
         run += (long long)diff[j];
-        hist[j] += (unsigned long long)run;
+        hist.set(j, hist.get(j) + (unsigned long long)run);
     }
     __syncthreads();
 }
@@ -422,13 +533,17 @@ __device__ void add_diff_prefix(unsigned long long *hist, unsigned long long *di
 
 // One work item (up to 256 tracers, 8 per lane) of the current simulation.
 // FULL: the item has all 256 tracers, so no lane needs a bounds test.
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED>
 __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
                                         const float *__restrict__ Vin, long long *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
-                                        const float2 *ek, unsigned long long *hist, unsigned long long *diff,
-                                        Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr)
+                                        const float2 *ek, const Hist &hist, unsigned long long *diff,
+                                        Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
+                                        const char *st)
 {
+    const long long *stU = reinterpret_cast<const long long *>(st);
+    const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
+    const int *stQ = reinterpret_cast<const int *>(st + kStageBytesU + kStageBytesV);
     const int lane = threadIdx.x & 31;
     const int nx = dv.nx;
     const int m = FULL ? WT : W.count;
@@ -455,13 +570,52 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
     bool has_halo = false;
     if (DEPOSIT && lane == lane_last && W.halo >= 0) {
         has_halo = true;
-        hu = Uin[W.halo];
-        if (PUSH)
-            hv = Vin[W.halo];
-        if (PER_Q)
-            hq = Qh[W.halo];
+        if (STAGED && W.halo == base + m) {
+            hu = stU[m];
+            if (PUSH)
+                hv = stV[m];
+            if (PER_Q)
+                hq = stQ[m];
+        } else {
+            hu = Uin[W.halo];
+            if (PUSH)
+                hv = Vin[W.halo];
+            if (PER_Q)
+                hq = Qh[W.halo];
+        }
     }
-    if (FULL || rn == R) {
+    if (STAGED) {
+        // the stage holds the whole item (and garbage past its end)
+        const longlong2 *pu = reinterpret_cast<const longlong2 *>(stU + l0);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const longlong2 t = pu[k];
+            u[2 * k] = t.x;
+            u[2 * k + 1] = t.y;
+        }
+        if (PUSH) {
+            const float4 *pv = reinterpret_cast<const float4 *>(stV + l0);
+#pragma unroll
+            for (int k = 0; k < R / 4; ++k) {
+                const float4 t = pv[k];
+                v[4 * k] = t.x;
+                v[4 * k + 1] = t.y;
+                v[4 * k + 2] = t.z;
+                v[4 * k + 3] = t.w;
+            }
+        }
+        if (PER_Q) {
+            const int4 *pq = reinterpret_cast<const int4 *>(stQ + l0);
+#pragma unroll
+            for (int k = 0; k < R / 4; ++k) {
+                const int4 t = pq[k];
+                q[4 * k] = t.x;
+                q[4 * k + 1] = t.y;
+                q[4 * k + 2] = t.z;
+                q[4 * k + 3] = t.w;
+            }
+        }
+    } else if (FULL || rn == R) {
         const longlong2 *pu = reinterpret_cast<const longlong2 *>(Uin + base + l0);
 #pragma unroll
         for (int k = 0; k < R / 2; ++k) {
@@ -617,20 +771,33 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
     }
 }
 
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED>
 __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Shared &sh = *reinterpret_cast<Shared *>(smem);
     const int nx_max = A.nx_max;
-    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smem + kSharedHead);
-    unsigned long long *diff = hist + nx_max;  // nx_max + 2 entries
+    unsigned long long *mesh_region = reinterpret_cast<unsigned long long *>(smem + kSharedHead);
+    Hist hist;
+    hist.lo = reinterpret_cast<unsigned *>(mesh_region);
+    hist.hi = hist.lo + nx_max;
+    unsigned long long *diff = mesh_region + nx_max;  // nx_max + 2 entries
     float2 *ek = reinterpret_cast<float2 *>(diff + nx_max + 2);
+    char *stage_base = reinterpret_cast<char *>(smem) + stage_offset(nx_max);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ib = A.cta_begin[blockIdx.x], ie = A.cta_begin[blockIdx.x + 1];
     const float ks = A.kick_scale;
     const int drift = A.drift;
+    char *my_stage = stage_base + (size_t)warp * 2 * StageBytes<PER_Q>::value;
+    unsigned phase = 0;      // bit s: parity of stage s's next completion
+    bool timed_out = false;
+    if (STAGED) {
+        if (tid < 2 * NW)
+            mbar_init(&sh.mbar[tid >> 1][tid & 1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        __syncthreads();
+    }
 
     for (int it0 = ib; it0 < ie;) {
         // enter the next simulation of this block's run of items
@@ -645,8 +812,10 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
         float *Vout = S.V[src ^ 1];
         const int32_t *Qh = S.Qh;
         if (DEPOSIT) {
-            for (int j = tid; j < nx; j += B)
-                hist[j] = 0ull;
+            for (int j = tid; j < nx; j += B) {
+                hist.lo[j] = 0u;
+                hist.hi[j] = 0u;
+            }
             for (int j = tid; j < nx + 2; j += B)
                 diff[j] = 0ull;
         }
@@ -661,14 +830,48 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
 
         const int run_end = min(A.slot_end[cur], ie);
         unsigned rerr = 0;
-        for (int it = it0 + warp; it < run_end; it += NW) {
-            const WorkItem W = A.items[it];
-            if (W.count == WT)
-                do_item<PUSH, DEPOSIT, PER_Q, POW2, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh, dv, ks,
-                                                          drift, rerr);
-            else
-                do_item<PUSH, DEPOSIT, PER_Q, POW2, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh, dv, ks,
-                                                           drift, rerr);
+        if (STAGED) {
+            // each warp streams its items through two stages: the copy of the
+            // next item runs while this one is pushed and deposited
+            int it = it0 + warp, s = 0;
+            if (it < run_end && lane == 0 && !timed_out)
+                stage_issue<PER_Q>(A.items[it], Uin, Vin, Qh, my_stage, &sh.mbar[warp][0]);
+            while (it < run_end && !timed_out) {
+                const int nxt = it + NW;
+                if (nxt < run_end && lane == 0)
+                    stage_issue<PER_Q>(A.items[nxt], Uin, Vin, Qh, my_stage + (s ^ 1) * StageBytes<PER_Q>::value,
+                                       &sh.mbar[warp][s ^ 1]);
+                const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
+                phase ^= 1u << s;
+                if (!__all_sync(0xffffffffu, ok)) {
+                    // give up on this run; let the copy in flight land first
+                    timed_out = true;
+                    if (nxt < run_end)
+                        mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
+                    break;
+                }
+                const WorkItem W = A.items[it];
+                const char *st = my_stage + s * StageBytes<PER_Q>::value;
+                if (W.count == WT)
+                    do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                    sh, dv, ks, drift, rerr, st);
+                else
+                    do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                     sh, dv, ks, drift, rerr, st);
+                __syncwarp();
+                it = nxt;
+                s ^= 1;
+            }
+        } else {
+            for (int it = it0 + warp; it < run_end; it += NW) {
+                const WorkItem W = A.items[it];
+                if (W.count == WT)
+                    do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                     sh, dv, ks, drift, rerr, nullptr);
+                else
+                    do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                      sh, dv, ks, drift, rerr, nullptr);
+            }
         }
 
         // leave the simulation: fold the block's mesh and sums into the
@@ -678,13 +881,15 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
             if (sh.diff_used)
                 add_diff_prefix(hist, diff, nx, sh);
             for (int j = tid; j < nx; j += B) {
-                const unsigned long long h = hist[j];
+                const unsigned long long h = hist.get(j);
                 if (h)
                     atomicAdd(S.mesh + j, h);
             }
         }
         if (rerr >> 31)
             atomicOr(&S.sc->err, SIC_ERR_RANGE);
+        if (STAGED && timed_out && lane == 0)
+            atomicOr(&S.sc->err, SIC_ERR_TIMEOUT);
         if (tid == 0) {
             SimAccum *ac = S.acc;
             atomic_add_i128(ac->ke, (__int128)(((unsigned __int128)sh.ke[1] << 64) | sh.ke[0]));
@@ -702,7 +907,7 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
         if (sh.last) {
             __threadfence();
             if (DEPOSIT)
-                field_epilogue(S, A.record, hist, reinterpret_cast<float *>(ek), sh);
+                field_epilogue(S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
             if (tid == 0) {
                 if (PUSH)
                     S.sc->buf = (unsigned)(src ^ 1);
@@ -718,12 +923,12 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
     }
 }
 
-template <bool P, bool D, bool Q, bool T>
+template <bool P, bool D, bool Q, bool T, bool G>
 cudaError_t prep(size_t smem)
 {
     static size_t done = 0;
     if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess)
             return e;
@@ -732,44 +937,44 @@ cudaError_t prep(size_t smem)
     return cudaSuccess;
 }
 
-template <bool P, bool D, bool Q, bool T>
+template <bool P, bool D, bool Q, bool T, bool G>
 cudaError_t run(const LaunchArgs &a, int grid, cudaStream_t s)
 {
-    const size_t smem = step_smem_bytes(a.nx_max);
-    cudaError_t e = prep<P, D, Q, T>(smem);
+    const size_t smem = step_smem_bytes(a.nx_max, G, Q);
+    cudaError_t e = prep<P, D, Q, T, G>(smem);
     if (e != cudaSuccess)
         return e;
-    k_step<P, D, Q, T><<<grid, B, smem, s>>>(a);
+    k_step<P, D, Q, T, G><<<grid, B, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <bool P, bool D, bool Q, bool T>
+template <bool P, bool D, bool Q, bool T, bool G>
 int occ(int nx_max)
 {
-    const size_t smem = step_smem_bytes(nx_max);
-    if (prep<P, D, Q, T>(smem) != cudaSuccess)
+    const size_t smem = step_smem_bytes(nx_max, G, Q);
+    if (prep<P, D, Q, T, G>(smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, T>, B, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, T, G>, B, smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-template <bool P, bool D>
+template <bool P, bool D, bool G>
 cudaError_t run_pd(const LaunchArgs &a, int grid, bool per_q, bool pow2, cudaStream_t s)
 {
     if (per_q)
-        return pow2 ? run<P, D, true, true>(a, grid, s) : run<P, D, true, false>(a, grid, s);
-    return pow2 ? run<P, D, false, true>(a, grid, s) : run<P, D, false, false>(a, grid, s);
+        return pow2 ? run<P, D, true, true, G>(a, grid, s) : run<P, D, true, false, G>(a, grid, s);
+    return pow2 ? run<P, D, false, true, G>(a, grid, s) : run<P, D, false, false, G>(a, grid, s);
 }
 
-template <bool P, bool D>
+template <bool P, bool D, bool G>
 int occ_pd(int nx_max, bool per_q, bool pow2)
 {
     if (per_q)
-        return pow2 ? occ<P, D, true, true>(nx_max) : occ<P, D, true, false>(nx_max);
-    return pow2 ? occ<P, D, false, true>(nx_max) : occ<P, D, false, false>(nx_max);
+        return pow2 ? occ<P, D, true, true, G>(nx_max) : occ<P, D, true, false, G>(nx_max);
+    return pow2 ? occ<P, D, false, true, G>(nx_max) : occ<P, D, false, false, G>(nx_max);
 }
 
 __global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int32_t n, const float *vs,
@@ -787,11 +992,18 @@ __global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int
 
 }  // namespace
 
-size_t step_smem_bytes(int nx_max)
+size_t step_smem_bytes(int nx_max, bool staged, bool per_q)
 {
-    // shared head, hist[nx], diff[nx + 2], ek[nx] (the epilogue reuses hist and ek)
-    return kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
+    // shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx] (the epilogue
+    // reuses mesh and ek), then the warps' staging buffers
+    size_t bytes = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
+    if (staged)
+        bytes = stage_offset(nx_max) + (size_t)NW * 2 * (kStageBytesU + kStageBytesV + (per_q ? kStageBytesQ : 0));
+    return bytes;
 }
+
+// Stage items through shared memory when two blocks still fit on an SM.
+bool step_staged(int nx_max, bool per_q) { return step_smem_bytes(nx_max, true, per_q) <= 112 * 1024; }
 
 static long long g_launches = 0;
 void count_launches(int64_t n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
@@ -801,11 +1013,13 @@ cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool pe
 {
     switch (mode) {
     case MODE_STEP:
-        return run_pd<true, true>(a, grid, per_q, pow2, s);
+        if (step_staged(a.nx_max, per_q))
+            return run_pd<true, true, true>(a, grid, per_q, pow2, s);
+        return run_pd<true, true, false>(a, grid, per_q, pow2, s);
     case MODE_DEPOSIT:
-        return run_pd<false, true>(a, grid, per_q, pow2, s);
+        return run_pd<false, true, false>(a, grid, per_q, pow2, s);
     default:
-        return run_pd<true, false>(a, grid, per_q, pow2, s);
+        return run_pd<true, false, false>(a, grid, per_q, pow2, s);
     }
 }
 
@@ -813,11 +1027,13 @@ int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2)
 {
     switch (mode) {
     case MODE_STEP:
-        return occ_pd<true, true>(nx_max, per_q, pow2);
+        if (step_staged(nx_max, per_q))
+            return occ_pd<true, true, true>(nx_max, per_q, pow2);
+        return occ_pd<true, true, false>(nx_max, per_q, pow2);
     case MODE_DEPOSIT:
-        return occ_pd<false, true>(nx_max, per_q, pow2);
+        return occ_pd<false, true, false>(nx_max, per_q, pow2);
     default:
-        return occ_pd<true, false>(nx_max, per_q, pow2);
+        return occ_pd<true, false, false>(nx_max, per_q, pow2);
     }
 }
 
