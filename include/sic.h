@@ -97,7 +97,8 @@ typedef struct {
     double momentum;       /* sum m (v- + v+)/2 of the last kick; m = w / qm */
     int64_t charge_fixed;  /* total mesh charge in fixed-point units (constant) */
     double charge_unit;    /* charge of one fixed-point unit */
-    double max_segment;    /* longest segment of the last deposit, in box lengths */
+    double max_segment;    /* longest segment of the last deposit that crosses a cell
+                              edge, in box lengths (0 when none does) */
 } sic_diag;
 
 /*

@@ -323,11 +323,12 @@ int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
     return SIC_OK;
 }
 
-// Fixed-point charge scale: every segment charge below 2^29 units, a power of two.
+// Fixed-point charge scale: every segment charge at most 2^28 units (so the
+// sum of a lane's 8 segments fits 32 bits), a power of two.
 double choose_sigma(double max_w)
 {
-    double sigma = std::ldexp(1.0, (int)std::floor(std::log2(std::ldexp(1.0, 29) / max_w)));
-    while (std::llround(max_w * sigma * 0.5) * 2 > (1LL << 29))
+    double sigma = std::ldexp(1.0, (int)std::floor(std::log2(std::ldexp(1.0, 28) / max_w)));
+    while (std::llround(max_w * sigma * 0.5) * 2 > (1LL << 28))
         sigma *= 0.5;
     return sigma;
 }
@@ -401,7 +402,14 @@ int setup(sic_sim *sim, const sic_config *cfg)
     h.E_scale = 1.0 / (nx2 * sim->sigma);
     h.e_scale = sim->qm * sim->dt * sim->dt / sim->dx * h.E_scale;
     h.rho_scale = 1.0 / ((double)nx * sim->sigma * sim->dx);
-    h.half_dx = 0.5 * sim->dx;
+    // W_E = dx/2 sum E_j^2 = dx/2 E_scale^2 2^120 sum (K_j 2^-60)^2
+    h.we_scale = 0.5 * sim->dx * h.E_scale * h.E_scale * std::ldexp(1.0, 120);
+    {
+        int ex = 0;
+        const double mant = std::frexp(h.e_scale, &ex);  // e_scale = mant 2^ex, mant in [0.5, 1)
+        h.ek_mant = (float)(mant * 2.0);
+        h.ek_exp = ex - 1;
+    }
     const double vu = sim->dx / sim->dt;  // physical velocity of one cell per step
     h.ke_scale = vu * vu / (2.0 * sim->sigma * sim->qm);
     h.p_scale = vu / (sim->sigma * sim->qm);
@@ -620,6 +628,7 @@ int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host)
     if (!sim)
         return SIC_EINVAL;
     CK(launch(sim->plan, MODE_DEPOSIT, 0.0f, 0, 0, sim->stream));
+    CK(launch_field_out(sim->h, sim->stream));
     if (mesh_fixed_host)
         CK(cudaMemcpyAsync(mesh_fixed_host, sim->h.mesh_last, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost,
                            sim->stream));
@@ -632,6 +641,7 @@ int sic_field(sic_sim *sim, double *E_host)
 {
     if (!sim || !E_host)
         return SIC_EINVAL;
+    CK(launch_field_out(sim->h, sim->stream));
     CK(cudaMemcpyAsync(E_host, sim->h.E64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
     return check_device_errors(sim);
 }
@@ -756,7 +766,7 @@ int sic_diagnostics(sic_sim *sim, sic_diag *out)
     }
     out->charge_fixed = sc.q_total;
     out->charge_unit = 1.0 / sim->sigma;
-    out->max_segment = (double)sc.maxseg / kTwo32 / (double)sim->nx;
+    out->max_segment = (double)sc.maxseg / 65536.0 / (double)sim->nx;
     return SIC_OK;
 }
 

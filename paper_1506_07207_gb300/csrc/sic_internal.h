@@ -18,7 +18,7 @@
 //   rho64[nx]     double the neutralised density of the latest deposit.
 // Charge unit: a segment between tracers of weights w_i, w_{i+1} carries
 // Q_s = Qh_i + Qh_{i+1} = round(w_i sigma / 2) + round(w_{i+1} sigma / 2)
-// units, sigma chosen so that every Q_s < 2^29.
+// units, sigma a power of two chosen so that every Q_s <= 2^28.
 #pragma once
 #include <stdint.h>
 
@@ -26,7 +26,12 @@
 
 #define SIC_ALIGN_TRACERS 32
 #define SIC_K1_BLOCK 256
+#ifndef SIC_K1_R
 #define SIC_K1_R 8
+#endif
+#ifndef SIC_K1_MIN_BLOCKS
+#define SIC_K1_MIN_BLOCKS 2
+#endif
 #define SIC_K1_WARPS (SIC_K1_BLOCK / 32)
 #define SIC_K1_WARP_TRACERS (32 * SIC_K1_R)
 
@@ -38,9 +43,9 @@
 // Per-warp double-buffered staging of the next work item in shared memory
 // (filled by bulk copies): positions, velocities and, per-tracer charge mode,
 // half charges, each with room for the item's 256 tracers plus its halo.
-#define SIC_STAGE_U_BYTES 2064
-#define SIC_STAGE_V_BYTES 1040
-#define SIC_STAGE_Q_BYTES 1040
+#define SIC_STAGE_U_BYTES (((SIC_K1_WARP_TRACERS + 1) * 8 + 15) / 16 * 16)
+#define SIC_STAGE_V_BYTES (((SIC_K1_WARP_TRACERS + 1) * 4 + 15) / 16 * 16)
+#define SIC_STAGE_Q_BYTES SIC_STAGE_V_BYTES
 
 // periodic cell reduction by a precomputed multiplier (unsigned division by
 // an invariant integer: q = (t + ((n - t) >> 1)) >> (l - 1), t = umulhi(m, n))
@@ -71,7 +76,7 @@ struct WorkItem {
 struct SimAccum {
     unsigned long long ke[2];   // sum Qh (v_old^2 + v_new^2)  ((cells/step)^2), lo/hi
     unsigned long long p[2];    // sum Qh (v_old + v_new)                      , lo/hi
-    unsigned long long maxseg;  // longest segment crossing a cell edge, 2^-32 cells
+    unsigned long long maxseg;  // longest segment crossing a cell edge, 2^-16 cells
     unsigned long long pad[3];
 };
 
@@ -79,7 +84,7 @@ struct SimScalars {
     int64_t step;
     int64_t q_total;    // total charge of the mesh E was solved from
     double we;          // W_E of the current field
-    int64_t maxseg;     // longest segment of the latest deposit
+    int64_t maxseg;     // longest segment of the latest deposit crossing a cell edge, 2^-16 cells
     uint32_t err;       // SIC_ERR_* bits
     uint32_t buf;       // which state buffer is current
 };
@@ -102,7 +107,9 @@ struct SimDev {
     double e_scale;             // Ek_j = K_j * e_scale
     double E_scale;             // E_j  = K_j * E_scale
     double rho_scale;           // rho_j = (nx mesh_j - Q) * rho_scale
-    double half_dx;             // dx / 2 (field energy)
+    double we_scale;            // W_E = we_scale * sum (K_j 2^-60)^2
+    float ek_mant;              // e_scale = ek_mant * 2^ek_exp
+    int32_t ek_exp;
     double ke_scale;            // KE = ke_scale * sum ke
     double p_scale;             // P  = p_scale * sum p
     int32_t strict;
@@ -127,6 +134,7 @@ struct LaunchArgs {
 namespace sic {
 enum Mode { MODE_STEP = 0, MODE_DEPOSIT = 1, MODE_PUSH = 2 };
 cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s);
+cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s);
 cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,
                                      const float *v_sheet, const int64_t *sheet_offset, int32_t n_sheets,
                                      cudaStream_t s);

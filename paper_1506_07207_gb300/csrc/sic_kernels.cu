@@ -182,17 +182,24 @@ __device__ __noinline__ void range_add(int js, long long n, long long p, int nx,
     *diff_used = 1;
 }
 
-// Deposit one segment between fixed-point positions ua (cell ja mod nx) and
-// ub (cell jb mod nx) carrying q units.  maxseg tracks the longest segment
-// that crosses a cell edge (2^-32 cells).
-__device__ __forceinline__ void emit_segment(long long ua, int ja, long long ub, int jb, int q, int nx,
-                                             RunAcc &acc, unsigned long long *diff, int *diff_used,
-                                             long long &maxseg)
-{
-    if (cell_of(ua) == cell_of(ub)) {  // also the zero-length segment: all charge in its cell
-        acc.add(ja, q);
-        return;
+// Deposit one segment that crosses at least one cell edge, between
+// fixed-point positions ua (cell ja mod nx) and ub (cell jb mod nx), carrying
+// q units.  maxseg tracks the longest such segment, in 2^-16 cells
+// (saturating).
+// Adds each piece straight into the block's mesh.
+struct DirectAdd {
+    Hist h;
+    __device__ __forceinline__ void add(int j, long long v) const
+    {
+        if (v)
+            h.add(j, v);
     }
+};
+
+template <class ACC>
+__device__ __forceinline__ void emit_cross(long long ua, int ja, long long ub, int jb, int q, int nx, ACC &acc,
+                                           unsigned long long *diff, int *diff_used, unsigned &maxseg)
+{
     if (ub < ua) {
         const long long t = ua;
         ua = ub;
@@ -202,7 +209,7 @@ __device__ __forceinline__ void emit_segment(long long ua, int ja, long long ub,
         jb = tj;
     }
     const long long span = ub - ua;
-    maxseg = max(maxseg, span);
+    maxseg = max(maxseg, (unsigned)min((unsigned long long)span >> 16, 0xffffffffull));
     const unsigned la = frac_of(ua);
     const float df = la ? __uint2float_rn(0u - la) : 4294967296.0f;  // a to the first edge
     const float inv = __frcp_rn(span_to_float(span));
@@ -233,22 +240,71 @@ __device__ __forceinline__ void emit_segment(long long ua, int ja, long long ub,
     acc.add(jb, (long long)q - F - inner);
 }
 
-// FP32 value -> 128-bit fixed point with 32 fractional bits: exact for
-// |x| >= 2^-32 up to 2^94 (larger values, inf and nan saturate)
-__device__ __forceinline__ __int128 f32_to_fix(float x)
+// A 128-bit fixed-point sum (2^-32 units) held in registers; adding the
+// same FP32 values in any order gives the same bits.
+struct Acc128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __noinline__ void acc_add_f32_wide(Acc128 &a, float x)
 {
     const unsigned b = __float_as_uint(x);
     const int e = (int)((b >> 23) & 0xffu);
-    if (e == 0)
-        return 0;
-    const unsigned m = (b & 0x7fffffu) | 0x800000u;
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+    const int sh = e - 118;
+    const __int128 t = sh > 100 ? ((__int128)1 << 124) : ((__int128)m << sh);
+    const unsigned long long lo = (unsigned long long)t;
+    const long long hi = (long long)(t >> 64);
+    if (b >> 31) {
+        const unsigned long long nlo = a.lo - lo;
+        a.hi = a.hi - hi - (a.lo < lo ? 1 : 0);
+        a.lo = nlo;
+    } else {
+        const unsigned long long nlo = a.lo + lo;
+        a.hi = a.hi + hi + (nlo < lo ? 1 : 0);
+        a.lo = nlo;
+    }
+}
+
+// Add x * 2^32, truncated to an integer, to the 128-bit sum: branch-free
+// for |x| < 2^31 (the common case), a call for larger values.
+__device__ __forceinline__ void acc_add_f32(Acc128 &a, float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
     const int sh = e - 118;  // x * 2^32 = m * 2^(e - 150 + 32)
-    __int128 r;
-    if (sh >= 0)
-        r = sh > 100 ? ((__int128)1 << 124) : ((__int128)m << sh);
-    else
-        r = sh <= -24 ? 0 : (__int128)(m >> (-sh));
-    return (b >> 31) ? -r : r;
+    if (__builtin_expect(sh <= 39, 1)) {
+        const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+        unsigned long long v = sh >= 0 ? (m << sh) : (m >> min(-sh, 63));
+        v = e ? v : 0ull;
+        const unsigned long long neg = (unsigned long long)((long long)(int)b >> 31);  // all ones if x < 0
+        const unsigned long long sv = (v ^ neg) - neg;                                 // +-v mod 2^64
+        const unsigned long long nlo = a.lo + sv;
+        a.hi += (long long)((v != 0ull) ? neg : 0ull) + (nlo < sv ? 1 : 0);
+        a.lo = nlo;
+    } else {
+        acc_add_f32_wide(a, x);
+    }
+}
+
+__device__ __forceinline__ void acc_add(Acc128 &a, const Acc128 &b)
+{
+    const unsigned long long nlo = a.lo + b.lo;
+    a.hi = a.hi + b.hi + (nlo < b.lo ? 1 : 0);
+    a.lo = nlo;
+}
+
+__device__ __forceinline__ Acc128 acc_warp_sum(Acc128 a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Acc128 t;
+        t.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+        t.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+        acc_add(a, t);
+    }
+    return a;
 }
 
 // 128-bit add into a (lo, hi) pair of 64-bit words with two atomics
@@ -322,9 +378,13 @@ constexpr int kStageBytesU = SIC_STAGE_U_BYTES;
 constexpr int kStageBytesV = SIC_STAGE_V_BYTES;
 constexpr int kStageBytesQ = SIC_STAGE_Q_BYTES;
 
-template <bool PER_Q>
-struct StageBytes {
-    static constexpr int value = kStageBytesU + kStageBytesV + (PER_Q ? kStageBytesQ : 0);
+// Per-warp buffer: two stages when staging (U | V | Q each), otherwise one
+// scratch of new positions (U | Q) for the cross-cell pass.
+template <bool PER_Q, bool STAGED>
+struct WarpBuf {
+    static constexpr int q_offset = STAGED ? kStageBytesU + kStageBytesV : kStageBytesU;
+    static constexpr int stage = q_offset + (PER_Q ? kStageBytesQ : 0);
+    static constexpr int bytes = (STAGED ? 2 : 1) * stage;
 };
 
 // Lane 0 of a warp: start the bulk copies of item W (and its halo when the
@@ -389,18 +449,46 @@ __device__ __forceinline__ __int128 make_i128(long long hi, long long lo)
     return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned long long)lo);
 }
 
+// v * 2^e2 as a float, without FP64: normalise |v|, keep its top 32 bits,
+// round them to 24 (relative error < 2^-24 + 2^-31), then scale by 2^(...)
+__device__ __forceinline__ float pow2f(int e)
+{
+    e = max(-126, min(127, e));
+    return __uint_as_float((unsigned)(e + 127) << 23);
+}
+
+__device__ __forceinline__ float i128_to_float(__int128 v, int e2)
+{
+    if (v == 0)
+        return 0.f;
+    const bool neg = v < 0;
+    const unsigned __int128 m = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+    const unsigned t = (unsigned)((m << lz) >> 96);
+    const int e = 96 - lz + e2;  // |v| * 2^e2 = t * 2^e
+    const int e_a = e / 2, e_b = e - e / 2;
+    const float f = __fmul_rn(__fmul_rn(__uint2float_rn(t), pow2f(e_a)), pow2f(e_b));
+    return neg ? -f : f;
+}
+
 // Field solve of one simulation (Sec. 2.1 with C = 1) by the block holding
 // its last ticket: sm (nx u64) and sE (nx floats) are this block's scratch.
 //   P_j = sum_{i<j} mesh_i, D_j = nx P_j - j Q (= nx sigma E'_j exactly),
 //   K_j = nx D_j - sum_j D_j (= nx^2 sigma E_j, zero mean), all integers;
-//   E_j = K_j E_scale, kick table Ek_j = K_j e_scale (one rounding each).
+//   kick table Ek_j = K_j e_scale rounded once to FP32, field energy from
+//   the squares of K_j 2^-60 summed in FP32 per thread and FP64 across.
+// The double-precision field and density for the host are recomputed from
+// mesh_last on request (k_field_out), so this path has no FP64 per cell.
 __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *sm, float *sE, Shared &sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = S.div.nx;
     for (int j = tid; j < nx; j += B) {
-        sm[j] = __ldcg(S.mesh + j);
+        const unsigned long long mv = __ldcg(S.mesh + j);
+        sm[j] = mv;
         S.mesh[j] = 0ull;
+        S.mesh_last[j] = (long long)mv;
     }
     __syncthreads();
     const int per = (nx + B - 1) / B;
@@ -446,28 +534,24 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
     for (int w = 0; w < NW; ++w)
         sumD += make_i128(sh.hi[w], sh.lo[w]);
 
-    double wloc = 0.0;
+    float wloc = 0.f;
     {
         long long run = run0;
         for (int j = j0; j < j1; ++j) {
-            const long long mj = (long long)sm[j];
             const __int128 d = (__int128)nx * run - (__int128)j * qtot;
-            const double kd = i128_to_double((__int128)nx * d - sumD);
-            const double e = kd * S.E_scale;
-            S.E64[j] = e;
-            S.mesh_last[j] = mj;
-            S.rho64[j] = i128_to_double((__int128)nx * mj - qtot) * S.rho_scale;
-            sE[j] = (float)(kd * S.e_scale);
-            wloc += e * e;
-            run += mj;
+            const __int128 K = (__int128)nx * d - sumD;
+            sE[j] = __fmul_rn(i128_to_float(K, S.ek_exp), S.ek_mant);
+            const float kn = i128_to_float(K, -60);
+            wloc = __fmaf_rn(kn, kn, wloc);
+            run += (long long)sm[j];
         }
     }
+    double wd = (double)wloc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-        wloc += __shfl_down_sync(0xffffffffu, wloc, o);
-    __syncthreads();
+        wd += __shfl_down_sync(0xffffffffu, wd, o);
     if (lane == 0)
-        sh.da[warp] = wloc;
+        sh.da[warp] = wd;
     __syncthreads();
     for (int j = tid; j < nx; j += B) {
         const int j1n = (j + 1 == nx) ? 0 : j + 1;
@@ -492,10 +576,10 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
             row[3] = (double)sc->q_total;
             sc->step = step + 1;
         }
-        sc->we = w * S.half_dx;
+        sc->we = w * S.we_scale;
         sc->q_total = qtot;
         sc->maxseg = mm;
-        if (S.strict && mm > ((long long)nx << 32))
+        if (S.strict && mm > ((long long)nx << 16))
             sc->err |= SIC_ERR_SEGLONG;
     }
 }
@@ -539,7 +623,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
                                         const float2 *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
-                                        const char *st)
+                                        char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg)
 {
     const long long *stU = reinterpret_cast<const long long *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
@@ -707,72 +791,162 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             hj = wrap_cell<POW2>(cell_of(hu), dv);
     }
 
-    long long maxseg = 0;
     if (DEPOSIT) {
         hu += W.halo_shift;  // closing segment: the sheet's first tracer one winding on
+        // publish the new positions (and charges) of the item in shared
+        // memory, so the cross-cell segments can be shared out over the warp
+        long long *pts = reinterpret_cast<long long *>(st);
+        int *qpts = reinterpret_cast<int *>(st + WarpBuf<PER_Q, STAGED>::q_offset);
+        if (FULL || rn == R) {
+            longlong2 *pp = reinterpret_cast<longlong2 *>(pts + l0);
+#pragma unroll
+            for (int k = 0; k < R / 2; ++k)
+                pp[k] = make_longlong2(u[2 * k], u[2 * k + 1]);
+            if (PER_Q) {
+                int4 *pq = reinterpret_cast<int4 *>(qpts + l0);
+#pragma unroll
+                for (int k = 0; k < R / 4; ++k)
+                    pq[k] = make_int4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (r < rn) {
+                    pts[l0 + r] = u[r];
+                    if (PER_Q)
+                        qpts[l0 + r] = q[r];
+                }
+        }
+        if (lane == lane_last && has_halo) {
+            pts[m] = hu;
+            if (PER_Q)
+                qpts[m] = hq;
+        }
         // the next tracer of each lane's last one comes from the lane above
         const long long nu = __shfl_down_sync(0xffffffffu, u[0], 1);
-        const int nj = __shfl_down_sync(0xffffffffu, jn[0], 1);
         const int nq = __shfl_down_sync(0xffffffffu, q[0], 1);
-        RunAcc acc(hist);
         const int qs_sheet = 2 * W.qh;
+        __syncwarp();
+
+        // segments inside one cell: whole charges summed per lane into three
+        // buckets for the cells c0, c0 + 1, c0 + 2 of its first tracer (a lane
+        // that reaches other cells falls back to run merging); the segments
+        // that cross a cell edge are marked for the second pass
+        unsigned cross = 0;
+        {
+            const int c0 = cell_of(u[0]);
+            unsigned b0 = 0, b1 = 0, b2 = 0;
+            bool wide = false;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (FULL || r < rn) {
-                long long ub;
-                int jb, qb;
-                bool seg = true;
-                if (r + 1 < R && (FULL || r + 1 < rn)) {
-                    ub = u[r + 1 < R ? r + 1 : r];
-                    jb = jn[r + 1 < R ? r + 1 : r];
-                    qb = q[r + 1 < R ? r + 1 : r];
-                } else if (lane < lane_last) {
-                    ub = nu;
-                    jb = nj;
-                    qb = nq;
-                } else {
-                    ub = hu;
-                    jb = hj;
-                    qb = hq;
-                    seg = has_halo;
+            for (int r = 0; r < R; ++r) {
+                if (FULL || r < rn) {
+                    long long ub;
+                    int qb;
+                    bool seg = true;
+                    if (r + 1 < R && (FULL || r + 1 < rn)) {
+                        ub = u[r + 1 < R ? r + 1 : r];
+                        qb = q[r + 1 < R ? r + 1 : r];
+                    } else if (lane < lane_last) {
+                        ub = nu;
+                        qb = nq;
+                    } else {
+                        ub = hu;
+                        qb = hq;
+                        seg = has_halo;
+                    }
+                    const int cr = cell_of(u[r]);
+                    const bool same = seg && cr == cell_of(ub);
+                    const unsigned qv = (unsigned)(PER_Q ? q[r] + qb : qs_sheet);
+                    const int d = cr - c0;
+                    b0 += (same && d == 0) ? qv : 0u;
+                    b1 += (same && d == 1) ? qv : 0u;
+                    b2 += (same && d == 2) ? qv : 0u;
+                    wide = wide || (same && (unsigned)d > 2u);
+                    cross |= (seg && !same) ? (1u << r) : 0u;
                 }
-                if (seg)
-                    emit_segment(u[r], jn[r], ub, jb, PER_Q ? q[r] + qb : qs_sheet, nx, acc, diff,
-                                 &sh.diff_used, maxseg);
+            }
+            if (__builtin_expect(!wide, 1)) {
+                const int j1 = (jn[0] + 1 == nx) ? 0 : jn[0] + 1;
+                const int j2 = (j1 + 1 == nx) ? 0 : j1 + 1;
+                if (b0)
+                    hist.add(jn[0], b0);
+                if (b1)
+                    hist.add(j1, b1);
+                if (b2)
+                    hist.add(j2, b2);
+            } else {
+                RunAcc acc(hist);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (FULL || r < rn) {
+                        long long ub;
+                        int qb;
+                        bool seg = true;
+                        if (r + 1 < R && (FULL || r + 1 < rn)) {
+                            ub = u[r + 1 < R ? r + 1 : r];
+                            qb = q[r + 1 < R ? r + 1 : r];
+                        } else if (lane < lane_last) {
+                            ub = nu;
+                            qb = nq;
+                        } else {
+                            ub = hu;
+                            qb = hq;
+                            seg = has_halo;
+                        }
+                        if (seg && cell_of(u[r]) == cell_of(ub))
+                            acc.add(jn[r], PER_Q ? q[r] + qb : qs_sheet);
+                    }
+                }
+                acc.flush();
             }
         }
-        acc.flush();
+
+        // cross-cell segments: compact them into a task list and let every
+        // lane take one in turn
+        const int cnt = __popc(cross);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            int pos = incl - cnt;
+            while (cross) {
+                const int r = __ffs(cross) - 1;
+                tasks[pos++] = (unsigned short)(l0 + r);
+                cross &= cross - 1u;
+            }
+            __syncwarp();
+            DirectAdd acc{hist};
+            for (int k = lane; k < total; k += 32) {
+                const int idx = tasks[k];
+                const long long ua = pts[idx], ub = pts[idx + 1];
+                const int qs = PER_Q ? qpts[idx] + qpts[idx + 1] : qs_sheet;
+                emit_cross(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs, nx, acc,
+                           diff, &sh.diff_used, mseg);
+            }
+        }
+        __syncwarp();  // pts and tasks are rewritten by the next item
     }
 
-    // this item's kinetic-energy and momentum sums, in a fixed lane order,
-    // then exactly into the block's 128-bit accumulators
+    // this lane's kinetic-energy and momentum terms, added exactly into its
+    // 128-bit registers (summed over the warp when the run ends)
     if (PUSH) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc_a += __shfl_down_sync(0xffffffffu, acc_a, o);
-            acc_b += __shfl_down_sync(0xffffffffu, acc_b, o);
+        if (!PER_Q) {
+            const float qq = __int2float_rn(W.qh);
+            acc_a = __fmul_rn(acc_a, qq);
+            acc_b = __fmul_rn(acc_b, qq);
         }
-        if (lane == 0) {
-            if (!PER_Q) {
-                const float qq = __int2float_rn(W.qh);
-                acc_a = __fmul_rn(acc_a, qq);
-                acc_b = __fmul_rn(acc_b, qq);
-            }
-            atomic_add_i128(sh.ke, f32_to_fix(acc_a));
-            atomic_add_i128(sh.p, f32_to_fix(acc_b));
-        }
-    }
-    if (DEPOSIT) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            maxseg = max(maxseg, __shfl_down_sync(0xffffffffu, maxseg, o));
-        if (lane == 0 && maxseg)
-            atomicMax(&sh.maxseg, (unsigned long long)maxseg);
+        acc_add_f32(ake, acc_a);
+        acc_add_f32(ap, acc_b);
     }
 }
 
 template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED>
-__global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
+__global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Shared &sh = *reinterpret_cast<Shared *>(smem);
@@ -789,7 +963,9 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
     const int ib = A.cta_begin[blockIdx.x], ie = A.cta_begin[blockIdx.x + 1];
     const float ks = A.kick_scale;
     const int drift = A.drift;
-    char *my_stage = stage_base + (size_t)warp * 2 * StageBytes<PER_Q>::value;
+    char *my_stage = stage_base + (size_t)warp * WarpBuf<PER_Q, STAGED>::bytes;
+    unsigned short *tasks =
+        reinterpret_cast<unsigned short *>(stage_base + (size_t)NW * WarpBuf<PER_Q, STAGED>::bytes) + warp * WT;
     unsigned phase = 0;      // bit s: parity of stage s's next completion
     bool timed_out = false;
     if (STAGED) {
@@ -829,18 +1005,27 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
         __syncthreads();
 
         const int run_end = min(A.slot_end[cur], ie);
-        unsigned rerr = 0;
+        unsigned rerr = 0, mseg = 0;
+        Acc128 ake{0ull, 0ll}, ap{0ull, 0ll};
         if (STAGED) {
             // each warp streams its items through two stages: the copy of the
             // next item runs while this one is pushed and deposited
             int it = it0 + warp, s = 0;
-            if (it < run_end && lane == 0 && !timed_out)
-                stage_issue<PER_Q>(A.items[it], Uin, Vin, Qh, my_stage, &sh.mbar[warp][0]);
+            WorkItem W = {};
+            if (it < run_end) {
+                W = A.items[it];
+                if (lane == 0 && !timed_out)
+                    stage_issue<PER_Q>(W, Uin, Vin, Qh, my_stage, &sh.mbar[warp][0]);
+            }
             while (it < run_end && !timed_out) {
                 const int nxt = it + NW;
-                if (nxt < run_end && lane == 0)
-                    stage_issue<PER_Q>(A.items[nxt], Uin, Vin, Qh, my_stage + (s ^ 1) * StageBytes<PER_Q>::value,
-                                       &sh.mbar[warp][s ^ 1]);
+                WorkItem Wn = W;
+                if (nxt < run_end) {
+                    Wn = A.items[nxt];
+                    if (lane == 0)
+                        stage_issue<PER_Q>(Wn, Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
+                                           &sh.mbar[warp][s ^ 1]);
+                }
                 const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
                 phase ^= 1u << s;
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -850,16 +1035,16 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
                         mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
                     break;
                 }
-                const WorkItem W = A.items[it];
-                const char *st = my_stage + s * StageBytes<PER_Q>::value;
+                char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
                 if (W.count == WT)
                     do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                    sh, dv, ks, drift, rerr, st);
+                                                                    sh, dv, ks, drift, rerr, st, tasks, ake, ap, mseg);
                 else
                     do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                     sh, dv, ks, drift, rerr, st);
+                                                                     sh, dv, ks, drift, rerr, st, tasks, ake, ap, mseg);
                 __syncwarp();
                 it = nxt;
+                W = Wn;
                 s ^= 1;
             }
         } else {
@@ -867,11 +1052,27 @@ __global__ void __launch_bounds__(B, 2) k_step(const LaunchArgs A)
                 const WorkItem W = A.items[it];
                 if (W.count == WT)
                     do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                     sh, dv, ks, drift, rerr, nullptr);
+                                                                     sh, dv, ks, drift, rerr, my_stage, tasks, ake, ap, mseg);
                 else
                     do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                      sh, dv, ks, drift, rerr, nullptr);
+                                                                      sh, dv, ks, drift, rerr, my_stage, tasks, ake, ap, mseg);
             }
+        }
+
+        // the warp's diagnostic sums into the block's
+        if (PUSH) {
+            const Acc128 k2 = acc_warp_sum(ake), p2 = acc_warp_sum(ap);
+            if (lane == 0) {
+                atomic_add_i128(sh.ke, (__int128)(((unsigned __int128)(unsigned long long)k2.hi << 64) | k2.lo));
+                atomic_add_i128(sh.p, (__int128)(((unsigned __int128)(unsigned long long)p2.hi << 64) | p2.lo));
+            }
+        }
+        if (DEPOSIT) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                mseg = max(mseg, __shfl_down_sync(0xffffffffu, mseg, o));
+            if (lane == 0 && mseg)
+                atomicMax(&sh.maxseg, (unsigned long long)mseg);
         }
 
         // leave the simulation: fold the block's mesh and sums into the
@@ -977,6 +1178,62 @@ int occ_pd(int nx_max, bool per_q, bool pow2)
     return pow2 ? occ<P, D, false, true, G>(nx_max) : occ<P, D, false, false, G>(nx_max);
 }
 
+// The double-precision node field E_j and density rho_j of the latest
+// deposit, recomputed from its exact charge mesh (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_field_out(const SimDev S)
+{
+    constexpr int BB = 1024, NWW = BB / 32;
+    __shared__ long long s_w[NWW];
+    __shared__ long long s_hi[NWW], s_lo[NWW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = S.div.nx;
+    const int per = (nx + BB - 1) / BB;
+    const int j0 = min(tid * per, nx), j1 = min(j0 + per, nx);
+    long long lsum = 0;
+    for (int j = j0; j < j1; ++j)
+        lsum += S.mesh_last[j];
+    long long incl = lsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += t;
+    }
+    if (lane == 31)
+        s_w[warp] = incl;
+    __syncthreads();
+    long long before = 0, qtot = 0;
+    for (int w = 0; w < NWW; ++w) {
+        if (w < warp)
+            before += s_w[w];
+        qtot += s_w[w];
+    }
+    const long long run0 = incl - lsum + before;
+    __int128 dsum = 0;
+    long long run = run0;
+    for (int j = j0; j < j1; ++j) {
+        dsum += (__int128)nx * run - (__int128)j * qtot;
+        run += S.mesh_last[j];
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        dsum += shfl_down_i128(dsum, o);
+    if (lane == 0) {
+        s_hi[warp] = (long long)(dsum >> 64);
+        s_lo[warp] = (long long)(unsigned long long)dsum;
+    }
+    __syncthreads();
+    __int128 sumD = 0;
+    for (int w = 0; w < NWW; ++w)
+        sumD += make_i128(s_hi[w], s_lo[w]);
+    run = run0;
+    for (int j = j0; j < j1; ++j) {
+        const long long mj = S.mesh_last[j];
+        const __int128 d = (__int128)nx * run - (__int128)j * qtot;
+        S.E64[j] = i128_to_double((__int128)nx * d - sumD) * S.E_scale;
+        S.rho64[j] = i128_to_double((__int128)nx * mj - qtot) * S.rho_scale;
+        run += mj;
+    }
+}
+
 __global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int32_t n, const float *vs,
                                     const int64_t *off, int32_t M)
 {
@@ -996,14 +1253,14 @@ size_t step_smem_bytes(int nx_max, bool staged, bool per_q)
 {
     // shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx] (the epilogue
     // reuses mesh and ek), then the warps' staging buffers
-    size_t bytes = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
-    if (staged)
-        bytes = stage_offset(nx_max) + (size_t)NW * 2 * (kStageBytesU + kStageBytesV + (per_q ? kStageBytesQ : 0));
-    return bytes;
+    // then per warp one staging buffer (two when staged) and a task list
+    const size_t buf = staged ? (per_q ? WarpBuf<true, true>::bytes : WarpBuf<false, true>::bytes)
+                              : (per_q ? WarpBuf<true, false>::bytes : WarpBuf<false, false>::bytes);
+    return stage_offset(nx_max) + (size_t)NW * buf + (size_t)NW * WT * sizeof(unsigned short);
 }
 
 // Stage items through shared memory when two blocks still fit on an SM.
-bool step_staged(int nx_max, bool per_q) { return step_smem_bytes(nx_max, true, per_q) <= 112 * 1024; }
+bool step_staged(int nx_max, bool per_q) { return step_smem_bytes(nx_max, true, per_q) <= 113 * 1024; }
 
 static long long g_launches = 0;
 void count_launches(int64_t n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
@@ -1035,6 +1292,13 @@ int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2)
     default:
         return occ_pd<true, false, false>(nx_max, per_q, pow2);
     }
+}
+
+cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s)
+{
+    k_field_out<<<1, 1024, 0, s>>>(sim);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,
