@@ -1,26 +1,33 @@
 #!/usr/bin/env python
-"""Benchmark of the SIC step on GB300: segment-updates/s.
+"""Benchmark of the SIC step on GB300: segment-updates/s and request latency.
 
-One step = one pass of the whole hot path over the workload: one launch of
-the step kernel (fused gather-kick-drift-deposit over every segment, then the
-field solve by the block that finishes last).  The default workload is the
-two-stream configuration (512 sheets x 16384 tracers = 8,388,608 segments,
-Nx = 1024), the largest single-simulation configuration of the paper-shaped
-set.  L2 (129 MB) is flushed before every timed step by reading a 256 MB
-buffer (a read leaves no dirty lines for the timed step to write back),
-because the tracer state (100 MB read + 100 MB written per step) would
-otherwise partly stay resident between steps.
+Workload (default ``serving``): a seeded sample of the serving request mix --
+Landau and two-stream runs with sheets M in [32, 1024], tracers per sheet N in
+[512, 65536], cells Nx in [64, 2048], 200-2000 steps, powers of two uniform
+in log2 (``inputs.serving_mix``, seed 0x5EC5).
+
+* ``value``: segment-updates/s of all sampled requests held resident on the
+  GPU as one persistent batch (one kernel launch per step for all of them);
+  the state (several GB) is far larger than L2, so no flush is needed.  The
+  dominant (only) kernel, the fused step, is timed per launch with CUDA
+  events on the batch's stream for the roofline.
+* ``serving``: the same requests replayed with Poisson arrivals (rate 0.7 x
+  the measured batched capacity) through the request server, batched
+  (continuous batching) and plain (one simulation per launch sequence,
+  first come first served): throughput and p50/p99 latency.
+* ``e2e``: the batched server fed from host arrays (compact horizontal-sheet
+  inputs), every request arriving at t = 0, end to end.
+* ``single_sim``: the two-stream configuration (512 x 16384 = 8,388,608
+  segments, Nx = 1024) stepped alone, L2 flushed by a 256 MB read before
+  every timed step.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-
-Prints one JSON line.  ``--impl reference`` times the FP64 oracle on the
-host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,24 +44,7 @@ UNIT = "segment-updates/s"
 ALGO_BYTES_PER_SEGMENT = 20          # read x, v, charge (4+4+4), write x, v (4+4)
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-
-
-def workload(name):
-    from paper_1506_07207_gb300 import inputs
-    makers = {
-        "two_stream": inputs.two_stream_config,
-        "landau_nonlinear": inputs.landau_nonlinear,
-        "landau_linear": inputs.landau_linear,
-        "langmuir": inputs.langmuir,
-    }
-    return makers[name]()
-
-
-def describe(p, name):
-    return {"workload": f"{name}: {p.n_sheets} sheets x {int(p.counts[0])} tracers "
-                        f"({p.n_segments} segments), Nx={p.nx}, L={p.L:.6g}, dt={p.dt}",
-            "segments": p.n_segments, "nx": p.nx, "sheets": p.n_sheets,
-            "l2": "flushed before every timed step (256 MB read)"}
+SEED = 0x5EC5
 
 
 def peaks():
@@ -68,22 +58,6 @@ def peaks():
         except Exception:
             pass
     return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
-
-
-def kernel_traffic(segments):
-    """ncu DRAM bytes of the fused kernel, if the committed capture matches the source."""
-    path = os.path.join(ROOT, "profiles", "traffic_push_deposit.json")
-    src = os.path.join(ROOT, "paper_1506_07207_gb300", "csrc", "sic_kernels.cu")
-    if not os.path.exists(path):
-        return None
-    try:
-        d = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get("source_sha256") != sha:
-            return None
-        return float(d["dram_bytes_per_segment"]) * segments
-    except Exception:
-        return None
 
 
 class Clocks:
@@ -140,39 +114,103 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(p, steps):
+def sample_requests(n, rate=None):
+    from paper_1506_07207_gb300 import inputs
+    return inputs.serving_mix(n_requests=n, seed=SEED, rate=rate)
+
+
+def describe(reqs, probs):
+    segs = [p.n_segments for p in probs]
+    return {"workload": f"serving mix sample: {len(reqs)} seeded requests (seed 0x5EC5), Landau and "
+                        f"two-stream, M 32-1024 sheets, N 512-65536 tracers, Nx 64-2048, 200-2000 steps",
+            "requests": len(reqs), "segments_resident": int(sum(segs)),
+            "segment_updates_total": int(sum(p.n_segments * p.n_steps for p in probs)),
+            "l2": "resident state several GB, far above the 129 MB L2: no flush"}
+
+
+def oracle_rate(probs, budget_s=12.0):
+    """FP64 oracle on a bounded sample: a few steps of the first requests."""
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.run_problem(p, n_steps=steps)
-    el = time.perf_counter() - t0
-    return {"value": p.n_segments * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} of {p.n_steps} steps of the same workload, FP64 C oracle, "
-                      f"single thread (includes one initial deposit)",
-            "seconds": el}
+    done_upd, el = 0, 0.0
+    for p in probs:
+        if p.n_segments > (1 << 24):     # bound host memory of the FP64 arrays
+            continue
+        steps = 4
+        p.x, p.v, p.w
+        t0 = time.perf_counter()
+        oracle.run_problem(p, n_steps=steps)
+        el += time.perf_counter() - t0
+        done_upd += p.n_segments * steps
+        if el > budget_s:
+            break
+    return done_upd / el, done_upd, el
 
 
 def run_reference(args, rank):
     if rank != 0:
         return 0
-    p = workload(args.workload)
+    reqs = sample_requests(args.requests)
+    probs = [r.problem() for r in reqs]
     import oracle
     oracle.build()
-    oracle.run_problem(p, n_steps=args.warmup)
-    t0 = time.perf_counter()
-    oracle.run_problem(p, n_steps=args.steps)
-    el = time.perf_counter() - t0
-    v = p.n_segments * args.steps / el
+    # warm-up: one step of a small request
+    small = min(probs, key=lambda p: p.n_segments)
+    for _ in range(args.warmup):
+        oracle.run_problem(small, n_steps=1)
+    upd, el = 0, 0.0
+    t_all = time.perf_counter()
+    config = describe(reqs, probs)
+    probs = [p for p in probs if p.n_segments <= (1 << 24)]
+    for k in range(args.steps):
+        p = probs[k % len(probs)]
+        p.x, p.v, p.w                    # expand the compact sheets before timing
+        t0 = time.perf_counter()
+        oracle.run_problem(p, n_steps=1)
+        el += time.perf_counter() - t0
+        upd += p.n_segments
+        if time.perf_counter() - t_all > 120:
+            break
+    v = upd / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": describe(p, args.workload),
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps (after {args.warmup} warm-up) of the "
-                                       f"workload, FP64 C oracle, single thread"},
+                             "sample": "one step (plus the initial deposit) of each of the first "
+                                       f"{args.steps} sampled requests of at most 2^24 segments, "
+                                       "FP64 C oracle, single thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def single_sim(torch, Sim, steps, warmup):
+    """Two-stream configuration alone, L2 flushed before each timed step."""
+    from paper_1506_07207_gb300 import inputs
+    p = inputs.two_stream_config()
+    stream = torch.cuda.Stream()
+    sim = Sim.from_problem(p, history_len=8, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush.fill_(1.0)
+    for _ in range(warmup):
+        sim.sic_step(1)
+    ev = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.sum()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.sic_step(1)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    sim.sic_destroy()
+    avg = statistics.mean(ms) / 1e3
+    return {"workload": "two-stream 512 x 16384 (8,388,608 segments), Nx 1024, L2 flushed per step",
+            "value": p.n_segments / avg, "unit": UNIT, "ms_per_step": avg * 1e3,
+            "achieved_gbs": ALGO_BYTES_PER_SEGMENT * p.n_segments / avg / 1e9}
 
 
 def main():
@@ -181,11 +219,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sic", choices=["sic", "reference"])
-    ap.add_argument("--workload", default="two_stream")
-    ap.add_argument("--cpu-steps", type=int, default=40)
-    ap.add_argument("--e2e-runs", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -196,7 +234,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -204,32 +241,25 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1506_07207_gb300 import build
-    if rank == 0 or world == 1:
+    if rank == 0:
         build.build()
     if world > 1:
         dist.barrier()
-    from paper_1506_07207_gb300.sic import Sim, sic_launch_count
+    from paper_1506_07207_gb300 import serving
+    from paper_1506_07207_gb300.sic import Batch, Sim, sic_launch_count
 
-    p = workload(args.workload)
-    S = p.n_segments
+    reqs = sample_requests(args.requests)
+    probs = [r.problem() for r in reqs]
+
+    # ---- value: the whole sample resident, one batch, one launch per step
     stream = torch.cuda.Stream()
-    sim = Sim.from_problem(p, history_len=64, stream=stream.cuda_stream)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    flush.fill_(1.0)
-
-    def one_step(ev=None):
-        with torch.cuda.stream(stream):
-            flush.sum()
-        if ev:
-            ev[0].record(stream)
-        sim.sic_step(1)
-        if ev:
-            ev[1].record(stream)
-
+    sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream) for p in probs]
+    batch = Batch(sims)
+    S = batch.sic_batch_segments()
     for _ in range(args.warmup):
-        one_step()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        batch.sic_batch_step(1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
@@ -242,70 +272,88 @@ def main():
     launches0 = sic_launch_count()
     with Clocks(uuid) as clk:
         t_wall = time.perf_counter()
-        for k in range(args.steps):
-            one_step(evs[k])
+        for a, b in evs:
+            a.record(stream)
+            batch.sic_batch_step(1)
+            b.record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
     launches = sic_launch_count() - launches0
-    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    k1_ms = step_ms  # one kernel per step
+    step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * S * args.steps / (total_ms / 1e3)
-    sim.sic_sync()
-
-    # end to end through the C ABI: host arrays in, a full run, state out
-    e2e = None
-    if rank == 0 and not args.no_e2e:
-        x, v, w = p.x, p.v, p.w
-        e2e_steps = args.e2e_steps
-        times = []
-        for _ in range(args.e2e_runs):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s2 = Sim.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, x, v, w,
-                                qm=p.qm, half_step_init=p.half_step_init, history_len=64,
-                                stream=stream.cuda_stream)
-            s2.sic_step(e2e_steps)
-            xs, vs = s2.sic_get_state()
-            times.append(time.perf_counter() - t0)
-            s2.sic_destroy()
-        n_alloc = sum(-(-int(c) // 32) * 32 for c in p.counts)
-        e2e = {"value": S * e2e_steps / min(times), "unit": UNIT,
-               "h2d_bytes_per_step": 12 * n_alloc / e2e_steps,
-               "d2h_bytes_per_step": 12 * n_alloc / e2e_steps,
-               "runs": args.e2e_runs, "steps_per_run": e2e_steps,
-               "note": "sic_create from float64 host arrays + sic_step(n) + sic_get_state; "
-                       "bytes are the int64 positions and float32 velocities crossing the bus"}
-
+    batch.sic_batch_destroy()
+    for s in sims:
+        s.sic_destroy()
+    del sims
     clocks = clk.summary()
-    peak, peak_src = peaks()
-    k1_avg_s = statistics.mean(k1_ms) / 1e3
-    achieved = ALGO_BYTES_PER_SEGMENT * S / k1_avg_s / 1e9
-    traffic = kernel_traffic(S)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 push/deposit, i64 charge, f64 field scale",
-        "data": "synthetic", "config": describe(p, args.workload),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_step (fused gather-kick-drift-deposit + field epilogue)",
-                     "algorithmic_bytes_per_launch": ALGO_BYTES_PER_SEGMENT * S,
-                     "avg_launch_ms": k1_avg_s * 1e3, "peak_source": peak_src,
-                     "kernels_per_step": 1},
-        "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
-        "wall_s_timed_region": t_wall,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 push/deposit, i64 fixed-point charge, exact integer field solve",
+        "data": "synthetic", "config": describe(reqs, probs),
     }
+    peak, peak_src = peaks()
+    avg_s = statistics.mean(step_ms) / 1e3
+    achieved = ALGO_BYTES_PER_SEGMENT * S / avg_s / 1e9
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "k_step (fused gather-kick-drift-deposit + field epilogue), one launch "
+                                  "per step over every resident request",
+                        "algorithmic_bytes_per_launch": ALGO_BYTES_PER_SEGMENT * S,
+                        "avg_launch_ms": avg_s * 1e3, "peak_source": peak_src}
+    line["clocks"] = clocks
+    line["gpu_launches"] = int(launches)
+    line["wall_s_timed_region"] = t_wall
+
+    if rank == 0 and not args.no_serving:
+        works = [p.n_segments * p.n_steps for p in probs]
+        rate = args.load * value / (sum(works) / len(works))
+        arrivals = []
+        t = 0.0
+        import numpy as np
+        rng = np.random.default_rng(SEED)
+        for _ in probs:
+            t += rng.exponential(1.0 / rate)
+            arrivals.append(t)
+        out = {}
+        for mode in ("batched", "plain"):
+            r = serving.run_trace(probs, arrivals, plain=(mode == "plain"), max_active=64, chunk_steps=32)
+            out[mode] = {"throughput": r["throughput"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                         "makespan_s": r["makespan_s"], "segment_updates": r["segment_updates"],
+                         "peak_device_bytes": r["bytes_peak"]}
+        out["arrival_rate_per_s"] = rate
+        out["load"] = args.load
+        line["serving"] = out
+    if rank == 0 and not args.no_e2e:
+        arrivals0 = [0.0] * len(probs)
+        r = serving.run_trace(probs, arrivals0, plain=False, max_active=64, chunk_steps=32)
+        steps_total = sum(p.n_steps for p in probs)
+        h2d = sum(8 * (p.x_template.size + 2 * p.n_sheets) for p in probs)
+        line["e2e"] = {"value": r["throughput"], "unit": UNIT,
+                       "h2d_bytes_per_step": h2d / steps_total,
+                       "d2h_bytes_per_step": 96 * len(probs) / steps_total,
+                       "note": "request server fed from host arrays (position template, per-sheet "
+                               "velocity and weight), all requests at t = 0, results read back; "
+                               "per-step bytes averaged over all requests' steps",
+                       "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "makespan_s": r["makespan_s"]}
+    if rank == 0 and not args.no_single:
+        line["single_sim"] = single_sim(torch, Sim, args.steps, args.warmup)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.cpu_steps)
-    sim.sic_destroy()
+        v, upd, el = oracle_rate(probs)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"4 steps each of the sampled requests of at most 2^24 segments, in order, until 12 s "
+                                          f"({upd} segment-updates in {el:.1f} s), FP64 C oracle, "
+                                          f"single thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -146,6 +146,19 @@ int sic_step(sic_sim *sim, int32_t n_steps);
  * calls bit for bit. */
 int sic_step_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps);
 
+/* A persistent batch: its launch plan is built once, so stepping it costs
+ * one kernel launch per step for all members (CUDA graphs of 8 steps when
+ * n_steps >= 8).  While the batch exists its members must be advanced only
+ * through it; it runs on the first member's stream, ordered after all
+ * members' streams at create and before them at destroy.  Every member
+ * advances by the same number of steps; results equal sic_step bit for bit. */
+typedef struct sic_batch sic_batch;
+int sic_batch_create(sic_sim *const *sims, int32_t n_sims, sic_batch **out);
+int sic_batch_step(sic_batch *batch, int32_t n_steps);
+/* Segments the batch advances per step (sum over its members). */
+int64_t sic_batch_segments(const sic_batch *batch);
+void sic_batch_destroy(sic_batch *batch);
+
 int sic_diagnostics(sic_sim *sim, sic_diag *out);
 
 /* Per-step history [rows][4] = {W_E, KE, P, charge_fixed} of the last
@@ -171,6 +184,84 @@ const char *sic_strerror(int code);
 
 /* Kernel launches issued by this process since load (for launch accounting). */
 int64_t sic_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of many simulations on one GPU.
+ *
+ * A request is a simulation (the arguments of sic_create or
+ * sic_create_horizontal) and a step count.  Requests wait in arrival order;
+ * each sic_server_tick admits waiting requests while an active slot is free
+ * and their device memory fits the budget, advances all active simulations
+ * together by up to chunk_steps steps (each step is one kernel launch over all
+ * of them), and retires the finished ones.  Results are bit-identical to
+ * running each request alone with sic_step.  In plain mode the server runs
+ * one request at a time to completion with sic_step, first come first served
+ * (the one-simulation-per-launch baseline).  Not thread-safe: one caller
+ * drives a server.
+ * ---------------------------------------------------------------------- */
+typedef struct sic_server sic_server;
+
+typedef struct {
+    int64_t hbm_budget;  /* bytes of device memory admitted simulations may hold, > 0 */
+    int32_t max_active;  /* simulations advanced together, >= 1 (forced to 1 in plain mode) */
+    int32_t chunk_steps; /* steps between two admission points, >= 1 */
+    int32_t plain;       /* 1: one request at a time, each run to completion */
+    void *stream;        /* cudaStream_t for all server work, NULL = its own */
+} sic_server_config;
+
+typedef struct {
+    int64_t id;              /* from submit */
+    int32_t status;          /* SIC_OK, SIC_EBUSY (larger than the budget) or the error that ended it */
+    int32_t pad;
+    int64_t steps;           /* steps taken */
+    int64_t segment_updates; /* segments x steps */
+    double field_energy;     /* final diagnostics, as in sic_diag */
+    double kinetic_energy;
+    double momentum;
+    int64_t charge_fixed;
+    double t_submit;         /* server clock (sic_server_clock), seconds */
+    double t_admit;
+    double t_done;
+    sic_sim *sim;            /* the simulation if submitted with keep != 0 (the caller
+                                owns it and destroys it), else NULL */
+} sic_result;
+
+typedef struct {
+    int64_t bytes_in_use;    /* device bytes held by admitted simulations */
+    int64_t bytes_peak;
+    int64_t hbm_budget;
+    int32_t active;
+    int32_t queued;
+    int64_t completed;
+    int64_t segment_updates; /* of completed requests */
+    int64_t ticks;
+} sic_server_info;
+
+int sic_server_create(const sic_server_config *cfg, sic_server **out);
+
+/* Queue a request; the inputs are copied (host arrays as for sic_create /
+ * sic_create_horizontal).  cfg->stream and cfg->history_len are ignored. */
+int sic_server_submit(sic_server *srv, const sic_config *cfg, const double *x_host, const double *v_host,
+                      const double *w_host, int32_t n_steps, int32_t keep, int64_t *id);
+int sic_server_submit_horizontal(sic_server *srv, const sic_config *cfg, int32_t n_template,
+                                 const double *x_template_host, const double *v_sheet_host,
+                                 const double *w_sheet_host, int32_t n_steps, int32_t keep, int64_t *id);
+
+/* One scheduling round (admit, advance one chunk, retire); blocks until the
+ * chunk has run.  *pending (nullable) gets the queued plus active requests. */
+int sic_server_tick(sic_server *srv, int32_t *pending);
+
+/* Move up to max finished requests into out[]; *n gets how many. */
+int sic_server_results(sic_server *srv, sic_result *out, int32_t max, int32_t *n);
+
+/* Seconds since sic_server_create on the server's steady clock. */
+double sic_server_clock(sic_server *srv);
+
+int sic_server_stats(sic_server *srv, sic_server_info *out);
+
+/* Destroys the server, its queued and active simulations, and kept
+ * simulations of results not yet taken. */
+void sic_server_destroy(sic_server *srv);
 
 #ifdef __cplusplus
 }

@@ -16,9 +16,11 @@
 #include <vector>
 
 #include "sic.h"
+#include "sic_host.h"
 #include "sic_internal.h"
 
 using namespace sic;
+using namespace sic_host;
 
 namespace {
 
@@ -82,22 +84,11 @@ int env_int(const char *name, int dflt)
     return x > 0 ? x : dflt;
 }
 
-// Device-side launch plan: table of simulations, items, block ranges, tickets.
-struct Plan {
-    void *mem = nullptr;
-    LaunchArgs args{};
-    int grid = 0;
-    bool per_q = false;
-    bool pow2 = false;
-};
-
-// Contiguous runs of items per block, balanced by tracer count.
-std::vector<int32_t> partition(const std::vector<WorkItem> &items, int grid)
+// Contiguous runs of items per block, balanced by tracer count: block b
+// takes the items whose start falls in [b T / grid, (b + 1) T / grid).
+std::vector<int32_t> partition(const std::vector<int64_t> &start, int grid)
 {
-    const int n = (int)items.size();
-    std::vector<int64_t> start(n + 1, 0);
-    for (int i = 0; i < n; ++i)
-        start[i + 1] = start[i] + items[i].count + kItemCost;
+    const int n = (int)start.size() - 1;
     const int64_t total = start[n];
     std::vector<int32_t> cta(grid + 1);
     int i = 0;
@@ -112,29 +103,6 @@ std::vector<int32_t> partition(const std::vector<WorkItem> &items, int grid)
 }
 
 }  // namespace
-
-struct sic_sim {
-    int nx = 0;
-    double L = 0, dt = 0, dx = 0, qm = 1;
-    int strict = 0, hist_len = 1, half_step_init = 0;
-    bool per_q = false;
-    int M = 0;
-    std::vector<int32_t> counts;
-    std::vector<uint8_t> closed;
-    std::vector<int32_t> winding;
-    std::vector<int64_t> sheet_off;
-    std::vector<int32_t> sheet_qh;
-    int64_t n_tracers = 0, n_alloc = 0;
-    double sigma = 1.0;
-    std::vector<WorkItem> items;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    void *dmem = nullptr;
-    SimDev h{};
-    Plan plan;
-    cudaGraphExec_t gexec = nullptr;
-    cudaError_t last = cudaSuccess;
-};
 
 namespace {
 
@@ -214,99 +182,6 @@ void plan_items(sic_sim *sim)
     }
 }
 
-void free_plan(Plan &p, cudaStream_t s)
-{
-    if (p.mem)
-        cudaFreeAsync(p.mem, s);
-    p.mem = nullptr;
-}
-
-// Build the device plan of one launch over several simulations (slot order).
-// Every member must share the charge mode; pow2 only if every nx is a power
-// of two.
-cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
-{
-    std::vector<SimDev> table;
-    std::vector<WorkItem> items;
-    int nx_max = 2;
-    bool pow2 = true;
-    for (int slot = 0; slot < n; ++slot) {
-        sic_sim *m = sims[slot];
-        table.push_back(m->h);
-        nx_max = std::max(nx_max, m->nx);
-        pow2 = pow2 && ((m->nx & (m->nx - 1)) == 0);
-        for (WorkItem w : m->items) {
-            w.sim = slot;
-            items.push_back(w);
-        }
-    }
-    const bool per_q = sims[0]->per_q;
-    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
-    if (per_sm < 1)
-        per_sm = 1;
-    const int by_items = ((int)items.size() + SIC_K1_WARPS - 1) / SIC_K1_WARPS;
-    const int grid = std::max(1, std::min(by_items, env_int("SIC_GRID", num_sms() * per_sm)));
-    std::vector<int32_t> cta = partition(items, grid);
-    std::vector<int32_t> slot_end(n, 0);
-    for (int i = 0; i < (int)items.size(); ++i)
-        slot_end[items[i].sim] = i + 1;
-    std::vector<int32_t> expected(n, 0);
-    for (int b = 0; b < grid; ++b) {
-        int last_slot = -1;
-        for (int i = cta[b]; i < cta[b + 1]; ++i)
-            if (items[i].sim != last_slot) {
-                last_slot = items[i].sim;
-                expected[last_slot] += 1;
-            }
-    }
-    Layout lay;
-    const size_t oT = lay.take(sizeof(SimDev) * table.size());
-    const size_t oI = lay.take(sizeof(WorkItem) * items.size());
-    const size_t oC = lay.take(4 * cta.size());
-    const size_t oS = lay.take(4 * slot_end.size());
-    const size_t oE = lay.take(4 * expected.size());
-    const size_t oK = lay.take(4 * (size_t)n);
-    cudaError_t e = cudaMallocAsync(&p.mem, lay.off, s);
-    if (e != cudaSuccess)
-        return e;
-    char *b = (char *)p.mem;
-    e = cudaMemcpyAsync(b + oT, table.data(), sizeof(SimDev) * table.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oI, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oC, cta.data(), 4 * cta.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oS, slot_end.data(), 4 * slot_end.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oE, expected.data(), 4 * expected.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)n, s);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
-    if (e != cudaSuccess)
-        return e;
-    p.args.sims = (const SimDev *)(b + oT);
-    p.args.items = (const WorkItem *)(b + oI);
-    p.args.cta_begin = (const int32_t *)(b + oC);
-    p.args.slot_end = (const int32_t *)(b + oS);
-    p.args.expected = (const int32_t *)(b + oE);
-    p.args.tickets = (unsigned *)(b + oK);
-    p.args.nx_max = nx_max;
-    p.grid = grid;
-    p.per_q = per_q;
-    p.pow2 = pow2;
-    return cudaSuccess;
-}
-
-cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int record, cudaStream_t s)
-{
-    LaunchArgs a = p.args;
-    a.kick_scale = kick_scale;
-    a.drift = drift;
-    a.record = record;
-    return launch_step_kernel(a, p.grid, mode, p.per_q, p.pow2, s);
-}
-
 int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
 {
     SimScalars sc;
@@ -362,24 +237,15 @@ int setup(sic_sim *sim, const sic_config *cfg)
     plan_items(sim);
     const int n_items = (int)sim->items.size();
 
-    Layout lay;
     const int nx = sim->nx;
-    const size_t oU0 = lay.take(8 * (size_t)sim->n_alloc);
-    const size_t oU1 = lay.take(8 * (size_t)sim->n_alloc);
-    const size_t oV0 = lay.take(4 * (size_t)sim->n_alloc);
-    const size_t oV1 = lay.take(4 * (size_t)sim->n_alloc);
-    const size_t oQ = sim->per_q ? lay.take(4 * (size_t)sim->n_alloc) : 0;
-    const size_t oMesh = lay.take(8 * (size_t)nx);
-    const size_t oLast = lay.take(8 * (size_t)nx);
-    const size_t oEk = lay.take(8 * (size_t)nx);
-    const size_t oE64 = lay.take(8 * (size_t)nx);
-    const size_t oRho = lay.take(8 * (size_t)nx);
-    const size_t oAcc = lay.take(sizeof(SimAccum));
-    const size_t oHist = lay.take(32 * (size_t)sim->hist_len);
-    const size_t oSc = lay.take(sizeof(SimScalars));
-    CK(cudaMallocAsync(&sim->dmem, lay.off, sim->stream));
+    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len);
+    const size_t oU0 = L.oU0, oU1 = L.oU1, oV0 = L.oV0, oV1 = L.oV1, oQ = L.oQ, oMesh = L.oMesh, oLast = L.oLast,
+                 oEk = L.oEk, oE64 = L.oE64, oRho = L.oRho, oAcc = L.oAcc, oItems = L.oItems, oHist = L.oHist,
+                 oSc = L.oSc;
+    sim->dbytes = L.total;
+    CK(cudaMallocAsync(&sim->dmem, L.total, sim->stream));
     char *b = (char *)sim->dmem;
-    CK(cudaMemsetAsync(b, 0, lay.off, sim->stream));
+    CK(cudaMemsetAsync(b, 0, L.total, sim->stream));
 
     SimDev &h = sim->h;
     h.U[0] = (int64_t *)(b + oU0);
@@ -393,6 +259,9 @@ int setup(sic_sim *sim, const sic_config *cfg)
     h.E64 = (double *)(b + oE64);
     h.rho64 = (double *)(b + oRho);
     h.acc = (SimAccum *)(b + oAcc);
+    h.items = (const WorkItem *)(b + oItems);
+    CK(cudaMemcpyAsync((void *)h.items, sim->items.data(), sizeof(WorkItem) * (size_t)n_items, cudaMemcpyHostToDevice,
+                       sim->stream));
     h.hist = (double *)(b + oHist);
     h.sc = (SimScalars *)(b + oSc);
     h.n_items = n_items;
@@ -430,6 +299,151 @@ int initialise(sic_sim *sim)
 }
 
 }  // namespace
+
+namespace sic_host {
+
+void free_plan(Plan &p, cudaStream_t s)
+{
+    if (p.mem)
+        cudaFreeAsync(p.mem, s);
+    p.mem = nullptr;
+}
+
+// Build the device plan of one launch over several simulations (slot order):
+// the table of their descriptors, where each one's items start in the
+// launch's list, each block's range of that list, and per simulation the
+// number of blocks that touch it (for the last-block epilogue).  Every member
+// must share the charge mode; pow2 only if every nx is a power of two.
+cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
+{
+    std::vector<SimDev> table(n);
+    std::vector<int32_t> slot_begin(n + 1, 0);
+    int nx_max = 2;
+    bool pow2 = true;
+    int64_t n_items = 0;
+    for (int slot = 0; slot < n; ++slot) {
+        sic_sim *m = sims[slot];
+        table[slot] = m->h;
+        nx_max = std::max(nx_max, m->nx);
+        pow2 = pow2 && ((m->nx & (m->nx - 1)) == 0);
+        slot_begin[slot] = (int32_t)n_items;
+        n_items += (int64_t)m->items.size();
+    }
+    slot_begin[n] = (int32_t)n_items;
+    std::vector<int64_t> start(n_items + 1, 0);
+    {
+        int64_t k = 0;
+        for (int slot = 0; slot < n; ++slot)
+            for (const WorkItem &w : sims[slot]->items) {
+                start[k + 1] = start[k] + w.count + kItemCost;
+                ++k;
+            }
+    }
+    const bool per_q = sims[0]->per_q;
+    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
+    if (per_sm < 1)
+        per_sm = 1;
+    const int by_items = (int)((n_items + SIC_K1_WARPS - 1) / SIC_K1_WARPS);
+    const int grid = std::max(1, std::min(by_items, env_int("SIC_GRID", num_sms() * per_sm)));
+    std::vector<int32_t> cta = partition(start, grid);
+    std::vector<int32_t> expected(n, 0);
+    {
+        int slot = 0;
+        for (int b = 0; b < grid; ++b) {
+            if (cta[b] == cta[b + 1])
+                continue;
+            while (slot_begin[slot + 1] <= cta[b])
+                ++slot;
+            for (int t = slot; t < n && slot_begin[t] < cta[b + 1]; ++t)
+                if (slot_begin[t + 1] > cta[b])
+                    expected[t] += 1;
+        }
+    }
+    Layout lay;
+    const size_t oT = lay.take(sizeof(SimDev) * table.size());
+    const size_t oS = lay.take(4 * slot_begin.size());
+    const size_t oC = lay.take(4 * cta.size());
+    const size_t oE = lay.take(4 * expected.size());
+    const size_t oK = lay.take(4 * (size_t)n);
+    cudaError_t e = cudaMallocAsync(&p.mem, lay.off, s);
+    if (e != cudaSuccess)
+        return e;
+    char *b = (char *)p.mem;
+    e = cudaMemcpyAsync(b + oT, table.data(), sizeof(SimDev) * table.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oS, slot_begin.data(), 4 * slot_begin.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oC, cta.data(), 4 * cta.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + oE, expected.data(), 4 * expected.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)n, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
+    if (e != cudaSuccess)
+        return e;
+    p.args.sims = (const SimDev *)(b + oT);
+    p.args.slot_begin = (const int32_t *)(b + oS);
+    p.args.cta_begin = (const int32_t *)(b + oC);
+    p.args.expected = (const int32_t *)(b + oE);
+    p.args.tickets = (unsigned *)(b + oK);
+    p.args.n_slots = n;
+    p.args.nx_max = nx_max;
+    p.grid = grid;
+    p.per_q = per_q;
+    p.pow2 = pow2;
+    return cudaSuccess;
+}
+
+cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int record, cudaStream_t s)
+{
+    LaunchArgs a = p.args;
+    a.kick_scale = kick_scale;
+    a.drift = drift;
+    a.record = record;
+    return launch_step_kernel(a, p.grid, mode, p.per_q, p.pow2, s);
+}
+
+
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len)
+{
+    Layout lay;
+    SimLayout L;
+    L.oU0 = lay.take(8 * (size_t)n_alloc);
+    L.oU1 = lay.take(8 * (size_t)n_alloc);
+    L.oV0 = lay.take(4 * (size_t)n_alloc);
+    L.oV1 = lay.take(4 * (size_t)n_alloc);
+    L.oQ = per_q ? lay.take(4 * (size_t)n_alloc) : 0;
+    L.oMesh = lay.take(8 * (size_t)nx);
+    L.oLast = lay.take(8 * (size_t)nx);
+    L.oEk = lay.take(8 * (size_t)nx);
+    L.oE64 = lay.take(8 * (size_t)nx);
+    L.oRho = lay.take(8 * (size_t)nx);
+    L.oAcc = lay.take(sizeof(SimAccum));
+    L.oItems = lay.take(sizeof(WorkItem) * (size_t)n_items);
+    L.oHist = lay.take(32 * (size_t)hist_len);
+    L.oSc = lay.take(sizeof(SimScalars));
+    L.total = lay.off;
+    return L;
+}
+
+int64_t padded_tracers(const int32_t *counts, int M)
+{
+    int64_t off = 0;
+    for (int s = 0; s < M; ++s)
+        off += (counts[s] + SIC_ALIGN_TRACERS - 1) / SIC_ALIGN_TRACERS * SIC_ALIGN_TRACERS;
+    return std::max<int64_t>(off, SIC_ALIGN_TRACERS);
+}
+
+int64_t work_items(const int32_t *counts, int M)
+{
+    int64_t n = 0;
+    for (int s = 0; s < M; ++s)
+        n += (counts[s] + SIC_K1_WARP_TRACERS - 1) / SIC_K1_WARP_TRACERS;
+    return n;
+}
+
+}  // namespace sic_host
 
 extern "C" {
 
@@ -742,6 +756,131 @@ int sic_step_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)
     for (cudaEvent_t e : ev)
         cudaEventDestroy(e);
     return SIC_OK;
+}
+
+}  // extern "C"
+
+struct sic_batch {
+    std::vector<sic_sim *> sims;
+    cudaStream_t stream = nullptr;
+    sic_host::Plan plan[2];
+    cudaGraphExec_t gexec = nullptr;
+    int64_t segments = 0;
+};
+
+namespace {
+
+cudaError_t batch_launch(sic_batch *b)
+{
+    for (int g = 0; g < 2; ++g)
+        if (b->plan[g].mem) {
+            const cudaError_t e = sic_host::launch(b->plan[g], MODE_STEP, 1.0f, 1, 1, b->stream);
+            if (e != cudaSuccess)
+                return e;
+        }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sic_batch_create(sic_sim *const *sims, int32_t n_sims, sic_batch **out)
+{
+    if (!sims || n_sims < 1 || !out)
+        return SIC_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n_sims; ++i) {
+        if (!sims[i])
+            return SIC_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (sims[k] == sims[i])
+                return SIC_EINVAL;
+    }
+    sic_batch *b = new (std::nothrow) sic_batch;
+    if (!b)
+        return SIC_ENOMEM;
+    b->sims.assign(sims, sims + n_sims);
+    b->stream = sims[0]->stream;
+    sic_sim *sim = sims[0];
+    for (int i = 1; i < n_sims; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaEventRecord(e, sims[i]->stream);
+        cudaStreamWaitEvent(b->stream, e, 0);
+        cudaEventDestroy(e);
+    }
+    std::vector<sic_sim *> grp[2];
+    for (sic_sim *m : b->sims) {
+        grp[m->per_q ? 1 : 0].push_back(m);
+        int64_t segs = 0;
+        for (int s = 0; s < m->M; ++s)
+            segs += m->counts[s] - (m->closed[s] ? 0 : 1);
+        b->segments += segs;
+    }
+    for (int g = 0; g < 2; ++g)
+        if (!grp[g].empty()) {
+            const cudaError_t e = sic_host::build_plan(b->plan[g], grp[g].data(), (int)grp[g].size(), b->stream);
+            if (e != cudaSuccess) {
+                sic_batch_destroy(b);
+                return e == cudaErrorMemoryAllocation ? SIC_ENOMEM : SIC_ECUDA;
+            }
+        }
+    *out = b;
+    return SIC_OK;
+}
+
+int sic_batch_step(sic_batch *b, int32_t n_steps)
+{
+    if (!b || n_steps < 0)
+        return SIC_EINVAL;
+    sic_sim *sim = b->sims[0];
+    const int launches_per_step = (b->plan[0].mem ? 1 : 0) + (b->plan[1].mem ? 1 : 0);
+    if (n_steps >= kGraphSteps && !b->gexec) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i)
+            e = batch_launch(b);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess)
+            return fail_cuda(sim, e);
+        CK(e2);
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        count_launches(-(int64_t)kGraphSteps * launches_per_step);
+    }
+    int32_t left = n_steps;
+    while (left >= kGraphSteps && b->gexec) {
+        CK(cudaGraphLaunch(b->gexec, b->stream));
+        count_launches((int64_t)kGraphSteps * launches_per_step);
+        left -= kGraphSteps;
+    }
+    for (; left > 0; --left)
+        CK(batch_launch(b));
+    return SIC_OK;
+}
+
+int64_t sic_batch_segments(const sic_batch *b) { return b ? b->segments : 0; }
+
+void sic_batch_destroy(sic_batch *b)
+{
+    if (!b)
+        return;
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    for (auto &p : b->plan)
+        sic_host::free_plan(p, b->stream);
+    cudaEvent_t done;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(done, b->stream);
+        for (sic_sim *m : b->sims)
+            if (m->stream != b->stream)
+                cudaStreamWaitEvent(m->stream, done, 0);
+        cudaEventDestroy(done);
+    }
+    delete b;
 }
 
 int sic_diagnostics(sic_sim *sim, sic_diag *out)

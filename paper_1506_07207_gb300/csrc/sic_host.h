@@ -1,0 +1,66 @@
+// sic_host.h -- host-side structures shared by the C ABI (sic_api.cu) and the
+// request server (sic_server.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "sic.h"
+#include "sic_internal.h"
+
+namespace sic_host {
+
+// Device-side launch plan: table of simulations, items, block ranges, tickets.
+struct Plan {
+    void *mem = nullptr;
+    LaunchArgs args{};
+    int grid = 0;
+    bool per_q = false;
+    bool pow2 = false;
+};
+
+// Device bytes of one simulation's allocation (state, meshes, items, ...).
+struct SimLayout {
+    size_t oU0, oU1, oV0, oV1, oQ, oMesh, oLast, oEk, oE64, oRho, oAcc, oItems, oHist, oSc, total;
+};
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len);
+
+// Tracer slots (sheets padded to SIC_ALIGN_TRACERS) and work items of M
+// sheets of n tracers each.
+int64_t padded_tracers(const int32_t *counts, int M);
+int64_t work_items(const int32_t *counts, int M);
+
+}  // namespace sic_host
+
+struct sic_sim {
+    int nx = 0;
+    double L = 0, dt = 0, dx = 0, qm = 1;
+    int strict = 0, hist_len = 1, half_step_init = 0;
+    bool per_q = false;
+    int M = 0;
+    std::vector<int32_t> counts;
+    std::vector<uint8_t> closed;
+    std::vector<int32_t> winding;
+    std::vector<int64_t> sheet_off;
+    std::vector<int32_t> sheet_qh;
+    int64_t n_tracers = 0, n_alloc = 0;
+    double sigma = 1.0;
+    std::vector<WorkItem> items;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    SimDev h{};
+    sic_host::Plan plan;
+    cudaGraphExec_t gexec = nullptr;
+    cudaError_t last = cudaSuccess;
+};
+
+
+namespace sic_host {
+cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s);
+void free_plan(Plan &p, cudaStream_t s);
+cudaError_t launch(const Plan &p, sic::Mode mode, float kick_scale, int drift, int record, cudaStream_t s);
+}  // namespace sic_host

@@ -101,6 +101,7 @@ struct SimDev {
     SimAccum *acc;
     double *hist;               // [hist_len][4]
     SimScalars *sc;
+    const WorkItem *items;      // [n_items] this simulation's work items
     int32_t n_items;
     int32_t hist_len;
     NxDiv div;
@@ -119,11 +120,12 @@ struct SimDev {
 // Everything one launch of the step kernel needs.
 struct LaunchArgs {
     const SimDev *sims;         // table, one entry per slot
-    const WorkItem *items;      // grouped by slot
-    const int32_t *slot_end;    // [slots] one past the slot's last item
-    const int32_t *cta_begin;   // [grid + 1]
+    const int32_t *slot_begin;  // [slots + 1] first item of each slot in the
+                                // launch's list (the slots' items back to back)
+    const int32_t *cta_begin;   // [grid + 1] each block's range of that list
     unsigned *tickets;          // [slots], zero between launches
     const int32_t *expected;    // [slots] blocks that touch each slot
+    int32_t n_slots;
     int32_t nx_max;
     int32_t drift;
     int32_t record;

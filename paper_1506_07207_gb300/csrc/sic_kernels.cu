@@ -977,8 +977,21 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
 
     for (int it0 = ib; it0 < ie;) {
         // enter the next simulation of this block's run of items
-        const int cur = A.items[it0].sim;
+        int cur = 0;
+        {
+            int lo = 0, hi = A.n_slots - 1;  // last slot with slot_begin <= it0
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.slot_begin[mid] <= it0)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            cur = lo;
+        }
         const SimDev &S = A.sims[cur];
+        const WorkItem *items = S.items;
+        const int ibase = A.slot_begin[cur];
         const NxDiv dv = S.div;
         const int nx = dv.nx;
         const int src = (int)S.sc->buf;
@@ -1004,7 +1017,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 ek[j] = S.Ek[j];
         __syncthreads();
 
-        const int run_end = min(A.slot_end[cur], ie);
+        const int run_end = min(A.slot_begin[cur + 1], ie);
         unsigned rerr = 0, mseg = 0;
         Acc128 ake{0ull, 0ll}, ap{0ull, 0ll};
         if (STAGED) {
@@ -1013,7 +1026,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             int it = it0 + warp, s = 0;
             WorkItem W = {};
             if (it < run_end) {
-                W = A.items[it];
+                W = items[it - ibase];
                 if (lane == 0 && !timed_out)
                     stage_issue<PER_Q>(W, Uin, Vin, Qh, my_stage, &sh.mbar[warp][0]);
             }
@@ -1021,7 +1034,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 const int nxt = it + NW;
                 WorkItem Wn = W;
                 if (nxt < run_end) {
-                    Wn = A.items[nxt];
+                    Wn = items[nxt - ibase];
                     if (lane == 0)
                         stage_issue<PER_Q>(Wn, Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
                                            &sh.mbar[warp][s ^ 1]);
@@ -1049,7 +1062,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             }
         } else {
             for (int it = it0 + warp; it < run_end; it += NW) {
-                const WorkItem W = A.items[it];
+                const WorkItem W = items[it - ibase];
                 if (W.count == WT)
                     do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                      sh, dv, ks, drift, rerr, my_stage, tasks, ake, ap, mseg);

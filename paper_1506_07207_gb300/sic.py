@@ -29,6 +29,9 @@ EXPORTS = [
     "sic_create", "sic_create_horizontal", "sic_deposit", "sic_field", "sic_push", "sic_step",
     "sic_step_batch", "sic_diagnostics", "sic_history", "sic_get_state", "sic_device_state",
     "sic_sync", "sic_destroy", "sic_strerror", "sic_launch_count",
+    "sic_batch_create", "sic_batch_step", "sic_batch_segments", "sic_batch_destroy",
+    "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
+    "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
 ]
 
 
@@ -62,6 +65,47 @@ class sic_diag(ctypes.Structure):
     ]
 
 
+class sic_server_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget", ctypes.c_int64),
+        ("max_active", ctypes.c_int32),
+        ("chunk_steps", ctypes.c_int32),
+        ("plain", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class sic_result(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("steps", ctypes.c_int64),
+        ("segment_updates", ctypes.c_int64),
+        ("field_energy", ctypes.c_double),
+        ("kinetic_energy", ctypes.c_double),
+        ("momentum", ctypes.c_double),
+        ("charge_fixed", ctypes.c_int64),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+        ("sim", ctypes.c_void_p),
+    ]
+
+
+class sic_server_info(ctypes.Structure):
+    _fields_ = [
+        ("bytes_in_use", ctypes.c_int64),
+        ("bytes_peak", ctypes.c_int64),
+        ("hbm_budget", ctypes.c_int64),
+        ("active", ctypes.c_int32),
+        ("queued", ctypes.c_int32),
+        ("completed", ctypes.c_int64),
+        ("segment_updates", ctypes.c_int64),
+        ("ticks", ctypes.c_int64),
+    ]
+
+
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"SIC CUDA library not built: {path} (run __graft_entry__.build())")
@@ -85,6 +129,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_destroy": ([simp], None),
         "sic_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sic_launch_count": ([], ctypes.c_int64),
+        "sic_batch_create": ([P(simp), ctypes.c_int32, P(vp)], ctypes.c_int),
+        "sic_batch_step": ([vp, ctypes.c_int32], ctypes.c_int),
+        "sic_batch_segments": ([vp], ctypes.c_int64),
+        "sic_batch_destroy": ([vp], None),
+        "sic_server_create": ([P(sic_server_config), P(vp)], ctypes.c_int),
+        "sic_server_submit": ([vp, P(sic_config), dp, dp, dp, ctypes.c_int32, ctypes.c_int32,
+                               P(ctypes.c_int64)], ctypes.c_int),
+        "sic_server_submit_horizontal": ([vp, P(sic_config), ctypes.c_int32, dp, dp, dp, ctypes.c_int32,
+                                          ctypes.c_int32, P(ctypes.c_int64)], ctypes.c_int),
+        "sic_server_tick": ([vp, ip], ctypes.c_int),
+        "sic_server_results": ([vp, P(sic_result), ctypes.c_int32, ip], ctypes.c_int),
+        "sic_server_clock": ([vp], ctypes.c_double),
+        "sic_server_stats": ([vp, P(sic_server_info)], ctypes.c_int),
+        "sic_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -278,3 +336,119 @@ def sic_step_batch(sims, n_steps):
         raise ValueError("one step count per simulation")
     _check(_lib.sic_step_batch(arr, len(sims), steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
            "sic_step_batch")
+
+
+class Batch:
+    """A persistent batch of simulations stepped together (``sic_batch*``)."""
+
+    def __init__(self, sims):
+        arr = (ctypes.c_void_p * len(sims))(*[s.handle for s in sims])
+        h = ctypes.c_void_p()
+        _check(_lib.sic_batch_create(arr, len(sims), ctypes.byref(h)), "sic_batch_create")
+        self._h = h
+        self.sims = list(sims)
+
+    def sic_batch_step(self, n_steps):
+        _check(_lib.sic_batch_step(self._h, int(n_steps)), "sic_batch_step")
+
+    def sic_batch_segments(self):
+        return int(_lib.sic_batch_segments(self._h))
+
+    def sic_batch_destroy(self):
+        if self._h is not None:
+            _lib.sic_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.sic_batch_destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """The request server (``sic_server*``): continuous batching of simulations."""
+
+    def __init__(self, hbm_budget=64 << 30, max_active=64, chunk_steps=32, plain=False, stream=None):
+        cfg = sic_server_config()
+        cfg.hbm_budget = int(hbm_budget)
+        cfg.max_active = int(max_active)
+        cfg.chunk_steps = int(chunk_steps)
+        cfg.plain = int(bool(plain))
+        cfg.stream = ctypes.c_void_p(int(stream) if stream else 0)
+        h = ctypes.c_void_p()
+        _check(_lib.sic_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sic_server_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server destroyed")
+        return self._h
+
+    def sic_server_submit_horizontal(self, p, n_steps=None, keep=False):
+        """Queue an ``inputs.Problem`` with horizontal sheets; returns the request id."""
+        xt = np.ascontiguousarray(p.x_template, dtype=np.float64)
+        vs = np.ascontiguousarray(p.v_sheet, dtype=np.float64)
+        ws = np.ascontiguousarray(p.w_sheet, dtype=np.float64)
+        cfg, keepalive = _config(p.nx, p.L, p.dt, vs.size, None, None, None, p.qm, p.half_step_init)
+        rid = ctypes.c_int64()
+        _check(_lib.sic_server_submit_horizontal(self.handle, ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs),
+                                                 _dptr(ws), int(p.n_steps if n_steps is None else n_steps),
+                                                 int(bool(keep)), ctypes.byref(rid)),
+               "sic_server_submit_horizontal")
+        return rid.value
+
+    def sic_server_submit(self, p, n_steps=None, keep=False):
+        """Queue an ``inputs.Problem`` from its full per-tracer arrays."""
+        x = np.ascontiguousarray(p.x, dtype=np.float64)
+        v = np.ascontiguousarray(p.v, dtype=np.float64)
+        w = np.ascontiguousarray(p.w, dtype=np.float64)
+        cfg, keepalive = _config(p.nx, p.L, p.dt, p.counts.size, p.counts, p.closed, p.winding, p.qm,
+                                 p.half_step_init)
+        rid = ctypes.c_int64()
+        _check(_lib.sic_server_submit(self.handle, ctypes.byref(cfg), _dptr(x), _dptr(v), _dptr(w),
+                                      int(p.n_steps if n_steps is None else n_steps), int(bool(keep)),
+                                      ctypes.byref(rid)), "sic_server_submit")
+        return rid.value
+
+    def sic_server_tick(self):
+        pending = ctypes.c_int32()
+        _check(_lib.sic_server_tick(self.handle, ctypes.byref(pending)), "sic_server_tick")
+        return pending.value
+
+    def sic_server_results(self, max_results=4096):
+        buf = (sic_result * max_results)()
+        n = ctypes.c_int32()
+        _check(_lib.sic_server_results(self.handle, buf, max_results, ctypes.byref(n)), "sic_server_results")
+        out = []
+        for i in range(n.value):
+            r = {name: getattr(buf[i], name) for name, _ in sic_result._fields_ if name not in ("pad", "sim")}
+            r["sim"] = buf[i].sim
+            out.append(r)
+        return out
+
+    def sic_server_clock(self):
+        return float(_lib.sic_server_clock(self.handle))
+
+    def sic_server_stats(self):
+        info = sic_server_info()
+        _check(_lib.sic_server_stats(self.handle, ctypes.byref(info)), "sic_server_stats")
+        return {name: getattr(info, name) for name, _ in sic_server_info._fields_}
+
+    def sic_server_destroy(self):
+        if self._h is not None:
+            _lib.sic_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.sic_server_destroy()
+        except Exception:
+            pass
+
+
+def adopt_sim(handle, nx, counts):
+    """Wrap a ``sic_sim*`` a server handed back (result of a keep request)."""
+    counts = np.asarray(counts, dtype=np.int64)
+    return Sim(ctypes.c_void_p(handle), nx, int(counts.sum()), counts)

@@ -89,3 +89,12 @@ def test_bad_config_fields(sic):
         sic.Sim.sic_create_horizontal(8, 1.0, 0.1, [0.0], [0.0], [1.0])   # one tracer
     with pytest.raises(sic.SicError):
         sic.Sim.sic_create_horizontal(8, 1.0, 0.1, [0.0, 0.5], [0.0], [-1.0])
+
+
+def test_server_rejects_bad_config(sic):
+    for kw in (dict(hbm_budget=0), dict(max_active=0), dict(chunk_steps=0)):
+        args = dict(hbm_budget=1 << 30, max_active=4, chunk_steps=8)
+        args.update(kw)
+        with pytest.raises(sic.SicError) as e:
+            sic.Server(**args)
+        assert e.value.code == sic.SIC_EINVAL

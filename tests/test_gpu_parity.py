@@ -281,3 +281,31 @@ def test_grid_shape_does_not_change_results(sic, monkeypatch):
         np.testing.assert_array_equal(v, v0)
         np.testing.assert_array_equal(m, m0)
         np.testing.assert_array_equal(h, h0)
+
+
+def test_persistent_batch_equals_alone(sic):
+    probs = [inputs.landau(0.1, 0.4, 128, 32, 3000, t_end=1.0),
+             inputs.two_stream(1.5, 0.2, 0.3, 512, 16, 5000, t_end=1.0),
+             inputs.langmuir(nx=100),
+             inputs.tiny_problem(12, n_sheets=4, max_tracers=2000, nx=64, L=1.0)]
+    steps = 19      # two graph replays of 8 and three single launches
+    alone = []
+    for p in probs:
+        sim = sic.Sim.from_problem(p, history_len=32)
+        sim.sic_step(steps)
+        alone.append((sim.sic_get_state(), sim.sic_history(32)))
+        sim.sic_destroy()
+    sims = [sic.Sim.from_problem(p, history_len=32) for p in probs]
+    b = sic.Batch(sims)
+    assert b.sic_batch_segments() == sum(p.n_segments for p in probs)
+    b.sic_batch_step(steps)
+    b.sic_batch_destroy()
+    try:
+        for s, (st, hist) in zip(sims, alone):
+            x, v = s.sic_get_state()
+            np.testing.assert_array_equal(x, st[0])
+            np.testing.assert_array_equal(v, st[1])
+            np.testing.assert_array_equal(s.sic_history(32), hist)
+    finally:
+        for s in sims:
+            s.sic_destroy()
