@@ -25,7 +25,6 @@ using namespace sic_host;
 namespace {
 
 constexpr int kGraphSteps = 8;  // steps captured in one graph
-constexpr int kItemCost = 16;   // fixed cost of a work item, in tracer units
 constexpr double kTwo32 = 4294967296.0;
 
 struct Layout {
@@ -84,22 +83,46 @@ int env_int(const char *name, int dflt)
     return x > 0 ? x : dflt;
 }
 
-// Contiguous runs of items per block, balanced by tracer count: block b
-// takes the items whose start falls in [b T / grid, (b + 1) T / grid).
-std::vector<int32_t> partition(const std::vector<int64_t> &start, int grid)
+// A percentage 0..100 from the environment, as a fraction (dflt if unset).
+double env_pct(const char *name, int dflt)
 {
-    const int n = (int)start.size() - 1;
-    const int64_t total = start[n];
-    std::vector<int32_t> cta(grid + 1);
-    int i = 0;
-    for (int b = 0; b <= grid; ++b) {
-        const int64_t target = (int64_t)((__int128)total * b / grid);
-        while (i < n && start[i] < target)
-            ++i;
-        cta[b] = i;
+    const char *v = std::getenv(name);
+    int x = (v && *v) ? std::atoi(v) : dflt;
+    x = std::min(100, std::max(0, x));
+    return x / 100.0;
+}
+
+// The chunks of a launch's item list.  Block b first takes chunk b of
+// n_static count-balanced slices of the first `static_frac` of the items (no
+// claim); the rest is cut for guided self-scheduling: each chunk a 1/(2 grid)
+// share of the items not yet cut (by default; rounded down to whole items per
+// warp, at least one each), so the first chunks are large and the last ones
+// small.  Blocks claim those in order, and the ones that finish early take the
+// small chunks at the end instead of waiting for a block that drew slower
+// items.  A block holds two chunks at most (the one it works on and the one it
+// claimed when that started), one fair share of what is left.
+std::vector<int32_t> plan_chunks(int64_t n_items, int grid, double static_frac, int *n_static)
+{
+    // SIC_CHUNK_DIV and SIC_CHUNK_MIN (items per warp) tune the guided sizes
+    const int64_t div = env_int("SIC_CHUNK_DIV", 2);
+    const int64_t least = (int64_t)SIC_K1_WARPS * env_int("SIC_CHUNK_MIN", 1);
+    std::vector<int32_t> b{0};
+    const int64_t head = (int64_t)(static_frac * (double)n_items);
+    *n_static = 0;
+    if (head > 0) {
+        for (int k = 1; k <= grid; ++k)
+            b.push_back((int32_t)(head * k / grid));
+        *n_static = grid;
     }
-    cta[grid] = n;
-    return cta;
+    int64_t at = b.back();
+    while (at < n_items) {
+        int64_t c = (n_items - at) / (div * (int64_t)grid) / SIC_K1_WARPS * SIC_K1_WARPS;
+        if (c < least)
+            c = least;
+        at = std::min(n_items, at + c);
+        b.push_back((int32_t)at);
+    }
+    return b;
 }
 
 }  // namespace
@@ -311,9 +334,9 @@ void free_plan(Plan &p, cudaStream_t s)
 
 // Build the device plan of one launch over several simulations (slot order):
 // the table of their descriptors, where each one's items start in the
-// launch's list, each block's range of that list, and per simulation the
-// number of blocks that touch it (for the last-block epilogue).  Every member
-// must share the charge mode; pow2 only if every nx is a power of two.
+// launch's list, the chunks of that list, and the zeroed claim counters and
+// item tickets.  Every member must share the charge mode; pow2 only if every
+// nx is a power of two.
 cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
 {
     std::vector<SimDev> table(n);
@@ -330,41 +353,23 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
         n_items += (int64_t)m->items.size();
     }
     slot_begin[n] = (int32_t)n_items;
-    std::vector<int64_t> start(n_items + 1, 0);
-    {
-        int64_t k = 0;
-        for (int slot = 0; slot < n; ++slot)
-            for (const WorkItem &w : sims[slot]->items) {
-                start[k + 1] = start[k] + w.count + kItemCost;
-                ++k;
-            }
-    }
     const bool per_q = sims[0]->per_q;
     int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
     if (per_sm < 1)
         per_sm = 1;
     const int by_items = (int)((n_items + SIC_K1_WARPS - 1) / SIC_K1_WARPS);
     const int grid = std::max(1, std::min(by_items, env_int("SIC_GRID", num_sms() * per_sm)));
-    std::vector<int32_t> cta = partition(start, grid);
-    std::vector<int32_t> expected(n, 0);
-    {
-        int slot = 0;
-        for (int b = 0; b < grid; ++b) {
-            if (cta[b] == cta[b + 1])
-                continue;
-            while (slot_begin[slot + 1] <= cta[b])
-                ++slot;
-            for (int t = slot; t < n && slot_begin[t] < cta[b + 1]; ++t)
-                if (slot_begin[t + 1] > cta[b])
-                    expected[t] += 1;
-        }
-    }
+    // one simulation: its items cost about alike, so 90% of them go in static
+    // slices; several: their costs per item differ (up to several times, with
+    // the tracers per cell), so all of them are claimed
+    const double frac = n == 1 ? env_pct("SIC_STATIC_PCT_ONE", 90) : env_pct("SIC_STATIC_PCT_MANY", 0);
+    int n_static = 0;
+    const std::vector<int32_t> chunks = plan_chunks(n_items, grid, frac, &n_static);
     Layout lay;
     const size_t oT = lay.take(sizeof(SimDev) * table.size());
     const size_t oS = lay.take(4 * slot_begin.size());
-    const size_t oC = lay.take(4 * cta.size());
-    const size_t oE = lay.take(4 * expected.size());
-    const size_t oK = lay.take(4 * (size_t)n);
+    const size_t oC = lay.take(4 * chunks.size());
+    const size_t oK = lay.take(4 * (size_t)(n + 2));  // claim[2], tickets[n]
     cudaError_t e = cudaMallocAsync(&p.mem, lay.off, s);
     if (e != cudaSuccess)
         return e;
@@ -373,20 +378,20 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + oS, slot_begin.data(), 4 * slot_begin.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oC, cta.data(), 4 * cta.size(), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(b + oC, chunks.data(), 4 * chunks.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oE, expected.data(), 4 * expected.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)n, s);
+        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)(n + 2), s);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
     if (e != cudaSuccess)
         return e;
     p.args.sims = (const SimDev *)(b + oT);
     p.args.slot_begin = (const int32_t *)(b + oS);
-    p.args.cta_begin = (const int32_t *)(b + oC);
-    p.args.expected = (const int32_t *)(b + oE);
-    p.args.tickets = (unsigned *)(b + oK);
+    p.args.chunk_begin = (const int32_t *)(b + oC);
+    p.args.claim = (unsigned *)(b + oK);
+    p.args.tickets = (unsigned *)(b + oK) + 2;
+    p.args.n_chunks = (int32_t)chunks.size() - 1;
+    p.args.n_static = n_static;
     p.args.n_slots = n;
     p.args.nx_max = nx_max;
     p.grid = grid;

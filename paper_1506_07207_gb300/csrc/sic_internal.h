@@ -119,12 +119,16 @@ struct SimDev {
 
 // Everything one launch of the step kernel needs.
 struct LaunchArgs {
-    const SimDev *sims;         // table, one entry per slot
-    const int32_t *slot_begin;  // [slots + 1] first item of each slot in the
-                                // launch's list (the slots' items back to back)
-    const int32_t *cta_begin;   // [grid + 1] each block's range of that list
-    unsigned *tickets;          // [slots], zero between launches
-    const int32_t *expected;    // [slots] blocks that touch each slot
+    const SimDev *sims;          // table, one entry per slot
+    const int32_t *slot_begin;   // [slots + 1] first item of each slot in the
+                                 // launch's list (the slots' items back to back)
+    const int32_t *chunk_begin;  // [chunks + 1] the list cut into chunks that
+                                 // blocks claim in order, largest first
+    unsigned *claim;             // [2] next chunk, blocks done; zero between launches
+    unsigned *tickets;           // [slots] items finished; zero between launches
+    int32_t n_chunks;
+    int32_t n_static;            // chunk b < n_static is block b's first chunk
+                                 // (not claimed); the rest are claimed
     int32_t n_slots;
     int32_t nx_max;
     int32_t drift;

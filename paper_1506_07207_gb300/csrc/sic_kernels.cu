@@ -409,6 +409,7 @@ struct Shared {
     unsigned long long mbar[NW][2];
     int diff_used;
     int last;
+    int ring[3];  // claimed chunks: this one, the next (kNoChunk until posted)
     unsigned long long ke[2], p[2], maxseg;
     long long w64[NW];
     long long hi[NW], lo[NW];
@@ -417,6 +418,7 @@ struct Shared {
 };
 
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
+constexpr int kNoChunk = -1;
 
 // shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx]; staging starts on a
 // 128-byte boundary (bulk copies need 16)
@@ -960,7 +962,6 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     char *stage_base = reinterpret_cast<char *>(smem) + stage_offset(nx_max);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ib = A.cta_begin[blockIdx.x], ie = A.cta_begin[blockIdx.x + 1];
     const float ks = A.kick_scale;
     const int drift = A.drift;
     char *my_stage = stage_base + (size_t)warp * WarpBuf<PER_Q, STAGED>::bytes;
@@ -968,117 +969,46 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         reinterpret_cast<unsigned short *>(stage_base + (size_t)NW * WarpBuf<PER_Q, STAGED>::bytes) + warp * WT;
     unsigned phase = 0;      // bit s: parity of stage s's next completion
     bool timed_out = false;
+    if (tid == 0) {
+        // the first chunk; each later one is claimed when its predecessor starts
+        sh.ring[0] = ((int)blockIdx.x < A.n_static) ? (int)blockIdx.x : A.n_static + (int)atomicAdd(A.claim, 1u);
+        sh.ring[1] = kNoChunk;
+    }
     if (STAGED) {
         if (tid < 2 * NW)
             mbar_init(&sh.mbar[tid >> 1][tid & 1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        __syncthreads();
     }
+    __syncthreads();
 
-    for (int it0 = ib; it0 < ie;) {
-        // enter the next simulation of this block's run of items
-        int cur = 0;
-        {
-            int lo = 0, hi = A.n_slots - 1;  // last slot with slot_begin <= it0
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (A.slot_begin[mid] <= it0)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            cur = lo;
-        }
-        const SimDev &S = A.sims[cur];
-        const WorkItem *items = S.items;
-        const int ibase = A.slot_begin[cur];
-        const NxDiv dv = S.div;
-        const int nx = dv.nx;
-        const int src = (int)S.sc->buf;
-        const long long *Uin = reinterpret_cast<const long long *>(S.U[src]);
-        const float *Vin = S.V[src];
-        long long *Uout = reinterpret_cast<long long *>(S.U[src ^ 1]);
-        float *Vout = S.V[src ^ 1];
-        const int32_t *Qh = S.Qh;
-        if (DEPOSIT) {
-            for (int j = tid; j < nx; j += B) {
-                hist.lo[j] = 0u;
-                hist.hi[j] = 0u;
-            }
-            for (int j = tid; j < nx + 2; j += B)
-                diff[j] = 0ull;
-        }
-        if (tid == 0) {
-            sh.diff_used = 0;
-            sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
-        }
-        if (PUSH)
-            for (int j = tid; j < nx; j += B)
-                ek[j] = S.Ek[j];
-        __syncthreads();
+    // the simulation whose mesh the block holds, and its views
+    int cur = -1, taken = 0;  // slot; items of it this block has taken
+    const SimDev *S = nullptr;
+    const WorkItem *items = nullptr;
+    int ibase = 0, iend = 0, src = 0;
+    NxDiv dv{};
+    const long long *Uin = nullptr;
+    const float *Vin = nullptr;
+    long long *Uout = nullptr;
+    float *Vout = nullptr;
+    const int32_t *Qh = nullptr;
+    unsigned rerr = 0, mseg = 0;
+    Acc128 ake{0ull, 0ll}, ap{0ull, 0ll};
+    // a warp's item whose copy was issued at the end of the previous chunk
+    int pend = -1, s = 0;
+    WorkItem Wp = {};
 
-        const int run_end = min(A.slot_begin[cur + 1], ie);
-        unsigned rerr = 0, mseg = 0;
-        Acc128 ake{0ull, 0ll}, ap{0ull, 0ll};
-        if (STAGED) {
-            // each warp streams its items through two stages: the copy of the
-            // next item runs while this one is pushed and deposited
-            int it = it0 + warp, s = 0;
-            WorkItem W = {};
-            if (it < run_end) {
-                W = items[it - ibase];
-                if (lane == 0 && !timed_out)
-                    stage_issue<PER_Q>(W, Uin, Vin, Qh, my_stage, &sh.mbar[warp][0]);
-            }
-            while (it < run_end && !timed_out) {
-                const int nxt = it + NW;
-                WorkItem Wn = W;
-                if (nxt < run_end) {
-                    Wn = items[nxt - ibase];
-                    if (lane == 0)
-                        stage_issue<PER_Q>(Wn, Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
-                                           &sh.mbar[warp][s ^ 1]);
-                }
-                const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
-                phase ^= 1u << s;
-                if (!__all_sync(0xffffffffu, ok)) {
-                    // give up on this run; let the copy in flight land first
-                    timed_out = true;
-                    if (nxt < run_end)
-                        mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
-                    break;
-                }
-                char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
-                if (W.count == WT)
-                    do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                    sh, dv, ks, drift, rerr, st, tasks, ake, ap, mseg);
-                else
-                    do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                     sh, dv, ks, drift, rerr, st, tasks, ake, ap, mseg);
-                __syncwarp();
-                it = nxt;
-                W = Wn;
-                s ^= 1;
-            }
-        } else {
-            for (int it = it0 + warp; it < run_end; it += NW) {
-                const WorkItem W = items[it - ibase];
-                if (W.count == WT)
-                    do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                     sh, dv, ks, drift, rerr, my_stage, tasks, ake, ap, mseg);
-                else
-                    do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                      sh, dv, ks, drift, rerr, my_stage, tasks, ake, ap, mseg);
-            }
-        }
-
-        // the warp's diagnostic sums into the block's
+    // fold the block's mesh and sums for slot cur into the simulation's,
+    // take an item ticket, run the field epilogue if it completes the slot
+    auto leave = [&]() {
         if (PUSH) {
             const Acc128 k2 = acc_warp_sum(ake), p2 = acc_warp_sum(ap);
             if (lane == 0) {
                 atomic_add_i128(sh.ke, (__int128)(((unsigned __int128)(unsigned long long)k2.hi << 64) | k2.lo));
                 atomic_add_i128(sh.p, (__int128)(((unsigned __int128)(unsigned long long)p2.hi << 64) | p2.lo));
             }
+            ake = Acc128{0ull, 0ll};
+            ap = Acc128{0ull, 0ll};
         }
         if (DEPOSIT) {
 #pragma unroll
@@ -1086,26 +1016,26 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 mseg = max(mseg, __shfl_down_sync(0xffffffffu, mseg, o));
             if (lane == 0 && mseg)
                 atomicMax(&sh.maxseg, (unsigned long long)mseg);
+            mseg = 0;
         }
-
-        // leave the simulation: fold the block's mesh and sums into the
-        // global ones, take a ticket, run the epilogue if it is the last one
         __syncthreads();
+        const int nx = dv.nx;
         if (DEPOSIT) {
             if (sh.diff_used)
                 add_diff_prefix(hist, diff, nx, sh);
             for (int j = tid; j < nx; j += B) {
                 const unsigned long long h = hist.get(j);
                 if (h)
-                    atomicAdd(S.mesh + j, h);
+                    atomicAdd(S->mesh + j, h);
             }
         }
         if (rerr >> 31)
-            atomicOr(&S.sc->err, SIC_ERR_RANGE);
+            atomicOr(&S->sc->err, SIC_ERR_RANGE);
+        rerr = 0;
         if (STAGED && timed_out && lane == 0)
-            atomicOr(&S.sc->err, SIC_ERR_TIMEOUT);
+            atomicOr(&S->sc->err, SIC_ERR_TIMEOUT);
         if (tid == 0) {
-            SimAccum *ac = S.acc;
+            SimAccum *ac = S->acc;
             atomic_add_i128(ac->ke, (__int128)(((unsigned __int128)sh.ke[1] << 64) | sh.ke[0]));
             atomic_add_i128(ac->p, (__int128)(((unsigned __int128)sh.p[1] << 64) | sh.p[0]));
             if (sh.maxseg)
@@ -1114,26 +1044,193 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            const unsigned t = atomicAdd(A.tickets + cur, 1u);
-            sh.last = (t + 1 == (unsigned)A.expected[cur]) ? 1 : 0;
+            const unsigned t = atomicAdd(A.tickets + cur, (unsigned)taken);
+            sh.last = (t + (unsigned)taken == (unsigned)(iend - ibase)) ? 1 : 0;
         }
         __syncthreads();
         if (sh.last) {
             __threadfence();
             if (DEPOSIT)
-                field_epilogue(S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
+                field_epilogue(*S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
             if (tid == 0) {
                 if (PUSH)
-                    S.sc->buf = (unsigned)(src ^ 1);
+                    S->sc->buf = (unsigned)(src ^ 1);
                 if (!DEPOSIT) {  // the epilogue did not consume the sums: drop them
-                    SimAccum *ac = S.acc;
+                    SimAccum *ac = S->acc;
                     ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
                 }
                 A.tickets[cur] = 0u;
             }
         }
         __syncthreads();
-        it0 = run_end;
+    };
+
+    for (int k = 0;; ++k) {
+        const int c = sh.ring[k % 3];
+        if (c >= A.n_chunks)
+            break;
+        // the next chunk: warp 0 posts it after its first item, by when the
+        // claim has returned; a warp that looks before then does not carry
+        volatile int *next_slot = sh.ring + (k + 1) % 3;
+        const int c_next = (tid == 0) ? A.n_static + (int)atomicAdd(A.claim, 1u) : 0;
+        bool posted = (warp != 0);
+        const int cb = A.chunk_begin[c], ce = A.chunk_begin[c + 1];
+        for (int r0 = cb; r0 < ce;) {
+            int slot;
+            {
+                int lo = 0, hi = A.n_slots - 1;  // last slot with slot_begin <= r0
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (A.slot_begin[mid] <= r0)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                slot = lo;
+            }
+            if (slot != cur) {
+                if (cur >= 0)
+                    leave();
+                cur = slot;
+                taken = 0;
+                S = A.sims + slot;
+                items = S->items;
+                ibase = A.slot_begin[slot];
+                iend = A.slot_begin[slot + 1];
+                dv = S->div;
+                src = (int)S->sc->buf;
+                Uin = reinterpret_cast<const long long *>(S->U[src]);
+                Vin = S->V[src];
+                Uout = reinterpret_cast<long long *>(S->U[src ^ 1]);
+                Vout = S->V[src ^ 1];
+                Qh = S->Qh;
+                const int nx = dv.nx;
+                if (DEPOSIT) {
+                    for (int j = tid; j < nx; j += B) {
+                        hist.lo[j] = 0u;
+                        hist.hi[j] = 0u;
+                    }
+                    for (int j = tid; j < nx + 2; j += B)
+                        diff[j] = 0ull;
+                }
+                if (tid == 0) {
+                    sh.diff_used = 0;
+                    sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
+                }
+                if (PUSH)
+                    for (int j = tid; j < nx; j += B)
+                        ek[j] = S->Ek[j];
+                __syncthreads();
+            }
+            const int r1 = min(iend, ce);
+            if (STAGED) {
+                // each warp streams its items through two stages: the copy of
+                // the next item (in this run, or the first of the next chunk
+                // when that continues the same simulation) runs while this one
+                // is pushed and deposited
+                int it = r0 + warp;
+                WorkItem W = {};
+                bool have = false;
+                if (it < r1 && !timed_out) {
+                    if (pend == it) {
+                        W = Wp;
+                    } else {
+                        W = items[it - ibase];
+                        if (lane == 0)
+                            stage_issue<PER_Q>(W, Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
+                                               &sh.mbar[warp][s]);
+                    }
+                    have = true;
+                }
+                pend = -1;
+                while (have) {
+                    int nxt = it + NW;
+                    bool more = nxt < r1, carry = false;
+                    if (!more && r1 == ce) {
+                        const int c1 = __shfl_sync(0xffffffffu, *next_slot, 0);
+                        if (c1 >= 0 && c1 < A.n_chunks) {
+                            const int cand = A.chunk_begin[c1] + warp;
+                            if (cand < A.chunk_begin[c1 + 1] && cand < iend) {
+                                nxt = cand;
+                                more = carry = true;
+                            }
+                        }
+                    }
+                    WorkItem Wn = W;
+                    if (more) {
+                        Wn = items[nxt - ibase];
+                        if (lane == 0)
+                            stage_issue<PER_Q>(Wn, Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
+                                               &sh.mbar[warp][s ^ 1]);
+                    }
+                    const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
+                    phase ^= 1u << s;
+                    if (!__all_sync(0xffffffffu, ok)) {
+                        // give up: let the copy in flight land, then only count items
+                        timed_out = true;
+                        if (more)
+                            mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
+                        break;
+                    }
+                    char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
+                    if (W.count == WT)
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                        sh, dv, ks, drift, rerr, st, tasks, ake, ap,
+                                                                        mseg);
+                    else
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                                                                         diff, sh, dv, ks, drift, rerr, st, tasks,
+                                                                         ake, ap, mseg);
+                    __syncwarp();
+                    if (!posted) {
+                        if (lane == 0)
+                            *next_slot = c_next;
+                        posted = true;
+                    }
+                    s ^= 1;
+                    if (!more)
+                        break;
+                    if (carry) {
+                        pend = nxt;
+                        Wp = Wn;
+                        break;
+                    }
+                    it = nxt;
+                    W = Wn;
+                }
+            } else {
+                for (int it = r0 + warp; it < r1; it += NW) {
+                    const WorkItem W = items[it - ibase];
+                    if (W.count == WT)
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                         sh, dv, ks, drift, rerr, my_stage, tasks,
+                                                                         ake, ap, mseg);
+                    else
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                                                                          diff, sh, dv, ks, drift, rerr, my_stage,
+                                                                          tasks, ake, ap, mseg);
+                }
+            }
+            taken += r1 - r0;
+            r0 = r1;
+        }
+        if (tid == 0) {
+            if (!posted)
+                *next_slot = c_next;
+            sh.ring[(k + 2) % 3] = kNoChunk;  // the slot of chunk k - 1, free now
+        }
+        __syncthreads();
+    }
+    if (cur >= 0)
+        leave();
+    if (tid == 0) {
+        // the last block out rewinds the chunk counter for the next launch
+        __threadfence();
+        const unsigned d = atomicAdd(A.claim + 1, 1u);
+        if (d + 1 == gridDim.x) {
+            A.claim[0] = 0u;
+            A.claim[1] = 0u;
+        }
     }
 }
 
