@@ -83,48 +83,6 @@ int env_int(const char *name, int dflt)
     return x > 0 ? x : dflt;
 }
 
-// A percentage 0..100 from the environment, as a fraction (dflt if unset).
-double env_pct(const char *name, int dflt)
-{
-    const char *v = std::getenv(name);
-    int x = (v && *v) ? std::atoi(v) : dflt;
-    x = std::min(100, std::max(0, x));
-    return x / 100.0;
-}
-
-// The chunks of a launch's item list.  Block b first takes chunk b of
-// n_static count-balanced slices of the first `static_frac` of the items (no
-// claim); the rest is cut for guided self-scheduling: each chunk a 1/(2 grid)
-// share of the items not yet cut (by default; rounded down to whole items per
-// warp, at least one each), so the first chunks are large and the last ones
-// small.  Blocks claim those in order, and the ones that finish early take the
-// small chunks at the end instead of waiting for a block that drew slower
-// items.  A block holds two chunks at most (the one it works on and the one it
-// claimed when that started), one fair share of what is left.
-std::vector<int32_t> plan_chunks(int64_t n_items, int grid, double static_frac, int *n_static)
-{
-    // SIC_CHUNK_DIV and SIC_CHUNK_MIN (items per warp) tune the guided sizes
-    const int64_t div = env_int("SIC_CHUNK_DIV", 2);
-    const int64_t least = (int64_t)SIC_K1_WARPS * env_int("SIC_CHUNK_MIN", 1);
-    std::vector<int32_t> b{0};
-    const int64_t head = (int64_t)(static_frac * (double)n_items);
-    *n_static = 0;
-    if (head > 0) {
-        for (int k = 1; k <= grid; ++k)
-            b.push_back((int32_t)(head * k / grid));
-        *n_static = grid;
-    }
-    int64_t at = b.back();
-    while (at < n_items) {
-        int64_t c = (n_items - at) / (div * (int64_t)grid) / SIC_K1_WARPS * SIC_K1_WARPS;
-        if (c < least)
-            c = least;
-        at = std::min(n_items, at + c);
-        b.push_back((int32_t)at);
-    }
-    return b;
-}
-
 }  // namespace
 
 namespace {
@@ -334,9 +292,17 @@ void free_plan(Plan &p, cudaStream_t s)
 
 // Build the device plan of one launch over several simulations (slot order):
 // the table of their descriptors, where each one's items start in the
-// launch's list, the chunks of that list, and the zeroed claim counters and
-// item tickets.  Every member must share the charge mode; pow2 only if every
-// nx is a power of two.
+// launch's list, and the zeroed claim cursors, item tickets and block count.
+// Every member must share the charge mode; pow2 only if every nx is a power
+// of two.
+//
+// Scheduling: block b starts on the simulation that holds its proportional
+// share of the items; its warps claim runs of consecutive items of that
+// simulation from the simulation's cursor (guided self-scheduling: each claim
+// a fraction of what is left, at least one item), so no warp waits for
+// another while the simulation has items; when none are left unclaimed, the
+// block folds its mesh into the simulation's and moves to the simulation with
+// the most unclaimed items.
 cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
 {
     std::vector<SimDev> table(n);
@@ -359,17 +325,14 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
         per_sm = 1;
     const int by_items = (int)((n_items + SIC_K1_WARPS - 1) / SIC_K1_WARPS);
     const int grid = std::max(1, std::min(by_items, env_int("SIC_GRID", num_sms() * per_sm)));
-    // one simulation: its items cost about alike, so 90% of them go in static
-    // slices; several: their costs per item differ (up to several times, with
-    // the tracers per cell), so all of them are claimed
-    const double frac = n == 1 ? env_pct("SIC_STATIC_PCT_ONE", 90) : env_pct("SIC_STATIC_PCT_MANY", 0);
-    int n_static = 0;
-    const std::vector<int32_t> chunks = plan_chunks(n_items, grid, frac, &n_static);
+    // a claim takes 1 / (D warps) of what is left: a warp's first claim on a
+    // simulation that all of them share is 1/D of its fair share, and a small
+    // simulation is spread over many warps (D = SIC_CLAIM_DIV, default 4)
+    const float claim_q = (float)(1.0 / ((double)env_int("SIC_CLAIM_DIV", 4) * grid * SIC_K1_WARPS));
     Layout lay;
     const size_t oT = lay.take(sizeof(SimDev) * table.size());
     const size_t oS = lay.take(4 * slot_begin.size());
-    const size_t oC = lay.take(4 * chunks.size());
-    const size_t oK = lay.take(4 * (size_t)(n + 2));  // claim[2], tickets[n]
+    const size_t oK = lay.take(4 * (size_t)(2 * n + 1));  // cursor[n], tickets[n], done
     cudaError_t e = cudaMallocAsync(&p.mem, lay.off, s);
     if (e != cudaSuccess)
         return e;
@@ -378,20 +341,18 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + oS, slot_begin.data(), 4 * slot_begin.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + oC, chunks.data(), 4 * chunks.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)(n + 2), s);
+        e = cudaMemsetAsync(b + oK, 0, 4 * (size_t)(2 * n + 1), s);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
     if (e != cudaSuccess)
         return e;
     p.args.sims = (const SimDev *)(b + oT);
     p.args.slot_begin = (const int32_t *)(b + oS);
-    p.args.chunk_begin = (const int32_t *)(b + oC);
-    p.args.claim = (unsigned *)(b + oK);
-    p.args.tickets = (unsigned *)(b + oK) + 2;
-    p.args.n_chunks = (int32_t)chunks.size() - 1;
-    p.args.n_static = n_static;
+    p.args.cursor = (unsigned *)(b + oK);
+    p.args.tickets = (unsigned *)(b + oK) + n;
+    p.args.done = (unsigned *)(b + oK) + 2 * n;
+    p.args.n_items = (int32_t)n_items;
+    p.args.claim_q = claim_q;
     p.args.n_slots = n;
     p.args.nx_max = nx_max;
     p.grid = grid;

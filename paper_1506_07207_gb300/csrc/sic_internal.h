@@ -122,13 +122,12 @@ struct LaunchArgs {
     const SimDev *sims;          // table, one entry per slot
     const int32_t *slot_begin;   // [slots + 1] first item of each slot in the
                                  // launch's list (the slots' items back to back)
-    const int32_t *chunk_begin;  // [chunks + 1] the list cut into chunks that
-                                 // blocks claim in order, largest first
-    unsigned *claim;             // [2] next chunk, blocks done; zero between launches
+    unsigned *cursor;            // [slots] items claimed; zero between launches
     unsigned *tickets;           // [slots] items finished; zero between launches
-    int32_t n_chunks;
-    int32_t n_static;            // chunk b < n_static is block b's first chunk
-                                 // (not claimed); the rest are claimed
+    unsigned *done;              // blocks finished; zero between launches
+    int32_t n_items;             // slot_begin[slots]
+    float claim_q;               // a claim takes this fraction of the items a
+                                 // simulation has left (guided scheduling)
     int32_t n_slots;
     int32_t nx_max;
     int32_t drift;

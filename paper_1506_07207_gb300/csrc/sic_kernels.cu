@@ -409,7 +409,8 @@ struct Shared {
     unsigned long long mbar[NW][2];
     int diff_used;
     int last;
-    int ring[3];  // claimed chunks: this one, the next (kNoChunk until posted)
+    int taken;               // items of the current simulation the block's warps took
+    int pick_n[NW], pick_s[NW];  // per warp: most unclaimed items, in which slot
     unsigned long long ke[2], p[2], maxseg;
     long long w64[NW];
     long long hi[NW], lo[NW];
@@ -418,7 +419,6 @@ struct Shared {
 };
 
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
-constexpr int kNoChunk = -1;
 
 // shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx]; staging starts on a
 // 128-byte boundary (bulk copies need 16)
@@ -968,39 +968,157 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     unsigned short *tasks =
         reinterpret_cast<unsigned short *>(stage_base + (size_t)NW * WarpBuf<PER_Q, STAGED>::bytes) + warp * WT;
     unsigned phase = 0;      // bit s: parity of stage s's next completion
+    int s = 0;               // the stage the warp's next item lands in
     bool timed_out = false;
-    if (tid == 0) {
-        // the first chunk; each later one is claimed when its predecessor starts
-        sh.ring[0] = ((int)blockIdx.x < A.n_static) ? (int)blockIdx.x : A.n_static + (int)atomicAdd(A.claim, 1u);
-        sh.ring[1] = kNoChunk;
-    }
     if (STAGED) {
         if (tid < 2 * NW)
             mbar_init(&sh.mbar[tid >> 1][tid & 1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
 
-    // the simulation whose mesh the block holds, and its views
-    int cur = -1, taken = 0;  // slot; items of it this block has taken
-    const SimDev *S = nullptr;
-    const WorkItem *items = nullptr;
-    int ibase = 0, iend = 0, src = 0;
-    NxDiv dv{};
-    const long long *Uin = nullptr;
-    const float *Vin = nullptr;
-    long long *Uout = nullptr;
-    float *Vout = nullptr;
-    const int32_t *Qh = nullptr;
+    // the first simulation: the one that holds this block's proportional
+    // share of the launch's items
+    int cur;
+    {
+        const long long target = ((2ll * blockIdx.x + 1) * (long long)A.n_items) / (2ll * gridDim.x);
+        int lo = 0, hi = A.n_slots - 1;  // last slot with slot_begin <= target
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.slot_begin[mid] <= target)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        cur = lo;
+    }
     unsigned rerr = 0, mseg = 0;
     Acc128 ake{0ull, 0ll}, ap{0ull, 0ll};
-    // a warp's item whose copy was issued at the end of the previous chunk
-    int pend = -1, s = 0;
-    WorkItem Wp = {};
 
-    // fold the block's mesh and sums for slot cur into the simulation's,
-    // take an item ticket, run the field epilogue if it completes the slot
-    auto leave = [&]() {
+    while (cur >= 0) {
+        // ---- enter simulation cur
+        const SimDev &S = A.sims[cur];
+        const WorkItem *items = S.items;
+        const int n_s = A.slot_begin[cur + 1] - A.slot_begin[cur];
+        const NxDiv dv = S.div;
+        const int nx = dv.nx;
+        const int src = (int)S.sc->buf;
+        const long long *Uin = reinterpret_cast<const long long *>(S.U[src]);
+        const float *Vin = S.V[src];
+        long long *Uout = reinterpret_cast<long long *>(S.U[src ^ 1]);
+        float *Vout = S.V[src ^ 1];
+        const int32_t *Qh = S.Qh;
+        unsigned *cursor = A.cursor + cur;
+        if (DEPOSIT) {
+            for (int j = tid; j < nx; j += B) {
+                hist.lo[j] = 0u;
+                hist.hi[j] = 0u;
+            }
+            for (int j = tid; j < nx + 2; j += B)
+                diff[j] = 0ull;
+        }
+        if (tid == 0) {
+            sh.diff_used = 0;
+            sh.taken = 0;
+            sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
+        }
+        if (PUSH)
+            for (int j = tid; j < nx; j += B)
+                ek[j] = S.Ek[j];
+        __syncthreads();
+
+        // ---- each warp claims runs of consecutive items (guided: a claim is
+        // the fraction claim_q of what it saw left, at least one item)
+        // and streams them through its two stages; the next run is claimed
+        // while the current one is processed, so its first copy can be issued
+        // before the current run's last item
+        const float q = A.claim_q;
+        unsigned seen = 0, c_old = 0, c_want = 0;  // lane 0: cursor as last seen; claim in flight
+        if (lane == 0)
+            seen = *(volatile unsigned *)cursor;
+        auto claim_issue = [&]() {
+            if (lane == 0) {
+                const int left = n_s - (int)min(seen, (unsigned)n_s);
+                c_want = left > 0 ? (unsigned)max(1, (int)((float)left * q)) : 0u;
+                c_old = c_want ? atomicAdd(cursor, c_want) : (unsigned)n_s;
+            }
+        };
+        auto claim_take = [&](int &a, int &n) {  // the first use of the claim's result
+            if (lane == 0)
+                seen = c_old + c_want;
+            const unsigned o = __shfl_sync(0xffffffffu, c_old, 0);
+            const unsigned w = __shfl_sync(0xffffffffu, c_want, 0);
+            a = (int)o;
+            n = (int)o < n_s ? min((int)w, n_s - (int)o) : 0;
+        };
+        int a, n;
+        claim_issue();
+        claim_take(a, n);
+        int count = 0;
+        if (STAGED) {
+            if (n > 0 && !timed_out && lane == 0)
+                stage_issue<PER_Q>(items[a], Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
+                                   &sh.mbar[warp][s]);
+        }
+        while (n > 0) {
+            claim_issue();  // the next run, taken at this run's last item
+            int na = 0, nn = 0;
+            bool took = false;
+            count += n;
+            for (int i = a; i < a + n && !timed_out; ++i) {
+                int nxt = i + 1;
+                if (nxt == a + n) {
+                    claim_take(na, nn);
+                    took = true;
+                    nxt = nn > 0 ? na : -1;
+                }
+                const WorkItem W = items[i];
+                if (STAGED) {
+                    if (nxt >= 0 && lane == 0)
+                        stage_issue<PER_Q>(items[nxt], Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
+                                           &sh.mbar[warp][s ^ 1]);
+                    const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
+                    phase ^= 1u << s;
+                    if (!__all_sync(0xffffffffu, ok)) {
+                        // give up: let the copy in flight land, then only count items
+                        timed_out = true;
+                        if (nxt >= 0) {
+                            mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
+                            phase ^= 1u << (s ^ 1);
+                        }
+                        break;
+                    }
+                    char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
+                    if (W.count == WT)
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                        sh, dv, ks, drift, rerr, st, tasks, ake, ap,
+                                                                        mseg);
+                    else
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                                                                         diff, sh, dv, ks, drift, rerr, st, tasks,
+                                                                         ake, ap, mseg);
+                    __syncwarp();
+                    s ^= 1;
+                } else {
+                    if (W.count == WT)
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                                                                         sh, dv, ks, drift, rerr, my_stage, tasks,
+                                                                         ake, ap, mseg);
+                    else
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                                                                          diff, sh, dv, ks, drift, rerr, my_stage,
+                                                                          tasks, ake, ap, mseg);
+                }
+            }
+            if (!took)
+                claim_take(na, nn);
+            a = na;
+            n = nn;
+        }
+        if (lane == 0)
+            atomicAdd(&sh.taken, count);
+
+        // ---- leave: fold the block's mesh and sums into the simulation's,
+        // take an item ticket, run the field epilogue if it completes it
         if (PUSH) {
             const Acc128 k2 = acc_warp_sum(ake), p2 = acc_warp_sum(ap);
             if (lane == 0) {
@@ -1019,23 +1137,22 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             mseg = 0;
         }
         __syncthreads();
-        const int nx = dv.nx;
         if (DEPOSIT) {
             if (sh.diff_used)
                 add_diff_prefix(hist, diff, nx, sh);
             for (int j = tid; j < nx; j += B) {
                 const unsigned long long h = hist.get(j);
                 if (h)
-                    atomicAdd(S->mesh + j, h);
+                    atomicAdd(S.mesh + j, h);
             }
         }
         if (rerr >> 31)
-            atomicOr(&S->sc->err, SIC_ERR_RANGE);
+            atomicOr(&S.sc->err, SIC_ERR_RANGE);
         rerr = 0;
         if (STAGED && timed_out && lane == 0)
-            atomicOr(&S->sc->err, SIC_ERR_TIMEOUT);
+            atomicOr(&S.sc->err, SIC_ERR_TIMEOUT);
         if (tid == 0) {
-            SimAccum *ac = S->acc;
+            SimAccum *ac = S.acc;
             atomic_add_i128(ac->ke, (__int128)(((unsigned __int128)sh.ke[1] << 64) | sh.ke[0]));
             atomic_add_i128(ac->p, (__int128)(((unsigned __int128)sh.p[1] << 64) | sh.p[0]));
             if (sh.maxseg)
@@ -1044,193 +1161,69 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            const unsigned t = atomicAdd(A.tickets + cur, (unsigned)taken);
-            sh.last = (t + (unsigned)taken == (unsigned)(iend - ibase)) ? 1 : 0;
+            const unsigned t = atomicAdd(A.tickets + cur, (unsigned)sh.taken);
+            sh.last = (t + (unsigned)sh.taken == (unsigned)n_s) ? 1 : 0;
         }
         __syncthreads();
         if (sh.last) {
             __threadfence();
             if (DEPOSIT)
-                field_epilogue(*S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
+                field_epilogue(S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
             if (tid == 0) {
                 if (PUSH)
-                    S->sc->buf = (unsigned)(src ^ 1);
+                    S.sc->buf = (unsigned)(src ^ 1);
                 if (!DEPOSIT) {  // the epilogue did not consume the sums: drop them
-                    SimAccum *ac = S->acc;
+                    SimAccum *ac = S.acc;
                     ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
                 }
                 A.tickets[cur] = 0u;
             }
         }
-        __syncthreads();
-    };
 
-    for (int k = 0;; ++k) {
-        const int c = sh.ring[k % 3];
-        if (c >= A.n_chunks)
-            break;
-        // the next chunk: warp 0 posts it after its first item, by when the
-        // claim has returned; a warp that looks before then does not carry
-        volatile int *next_slot = sh.ring + (k + 1) % 3;
-        const int c_next = (tid == 0) ? A.n_static + (int)atomicAdd(A.claim, 1u) : 0;
-        bool posted = (warp != 0);
-        const int cb = A.chunk_begin[c], ce = A.chunk_begin[c + 1];
-        for (int r0 = cb; r0 < ce;) {
-            int slot;
-            {
-                int lo = 0, hi = A.n_slots - 1;  // last slot with slot_begin <= r0
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (A.slot_begin[mid] <= r0)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
-                }
-                slot = lo;
+        // ---- next: the simulation with the most unclaimed items, if any
+        int best = -1, most = 0;
+        for (int j = tid; j < A.n_slots; j += B) {
+            const int left = (A.slot_begin[j + 1] - A.slot_begin[j]) - (int)*(volatile unsigned *)(A.cursor + j);
+            if (left > most) {
+                most = left;
+                best = j;
             }
-            if (slot != cur) {
-                if (cur >= 0)
-                    leave();
-                cur = slot;
-                taken = 0;
-                S = A.sims + slot;
-                items = S->items;
-                ibase = A.slot_begin[slot];
-                iend = A.slot_begin[slot + 1];
-                dv = S->div;
-                src = (int)S->sc->buf;
-                Uin = reinterpret_cast<const long long *>(S->U[src]);
-                Vin = S->V[src];
-                Uout = reinterpret_cast<long long *>(S->U[src ^ 1]);
-                Vout = S->V[src ^ 1];
-                Qh = S->Qh;
-                const int nx = dv.nx;
-                if (DEPOSIT) {
-                    for (int j = tid; j < nx; j += B) {
-                        hist.lo[j] = 0u;
-                        hist.hi[j] = 0u;
-                    }
-                    for (int j = tid; j < nx + 2; j += B)
-                        diff[j] = 0ull;
-                }
-                if (tid == 0) {
-                    sh.diff_used = 0;
-                    sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
-                }
-                if (PUSH)
-                    for (int j = tid; j < nx; j += B)
-                        ek[j] = S->Ek[j];
-                __syncthreads();
-            }
-            const int r1 = min(iend, ce);
-            if (STAGED) {
-                // each warp streams its items through two stages: the copy of
-                // the next item (in this run, or the first of the next chunk
-                // when that continues the same simulation) runs while this one
-                // is pushed and deposited
-                int it = r0 + warp;
-                WorkItem W = {};
-                bool have = false;
-                if (it < r1 && !timed_out) {
-                    if (pend == it) {
-                        W = Wp;
-                    } else {
-                        W = items[it - ibase];
-                        if (lane == 0)
-                            stage_issue<PER_Q>(W, Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
-                                               &sh.mbar[warp][s]);
-                    }
-                    have = true;
-                }
-                pend = -1;
-                while (have) {
-                    int nxt = it + NW;
-                    bool more = nxt < r1, carry = false;
-                    if (!more && r1 == ce) {
-                        const int c1 = __shfl_sync(0xffffffffu, *next_slot, 0);
-                        if (c1 >= 0 && c1 < A.n_chunks) {
-                            const int cand = A.chunk_begin[c1] + warp;
-                            if (cand < A.chunk_begin[c1 + 1] && cand < iend) {
-                                nxt = cand;
-                                more = carry = true;
-                            }
-                        }
-                    }
-                    WorkItem Wn = W;
-                    if (more) {
-                        Wn = items[nxt - ibase];
-                        if (lane == 0)
-                            stage_issue<PER_Q>(Wn, Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
-                                               &sh.mbar[warp][s ^ 1]);
-                    }
-                    const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
-                    phase ^= 1u << s;
-                    if (!__all_sync(0xffffffffu, ok)) {
-                        // give up: let the copy in flight land, then only count items
-                        timed_out = true;
-                        if (more)
-                            mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
-                        break;
-                    }
-                    char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
-                    if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                        sh, dv, ks, drift, rerr, st, tasks, ake, ap,
-                                                                        mseg);
-                    else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
-                                                                         diff, sh, dv, ks, drift, rerr, st, tasks,
-                                                                         ake, ap, mseg);
-                    __syncwarp();
-                    if (!posted) {
-                        if (lane == 0)
-                            *next_slot = c_next;
-                        posted = true;
-                    }
-                    s ^= 1;
-                    if (!more)
-                        break;
-                    if (carry) {
-                        pend = nxt;
-                        Wp = Wn;
-                        break;
-                    }
-                    it = nxt;
-                    W = Wn;
-                }
-            } else {
-                for (int it = r0 + warp; it < r1; it += NW) {
-                    const WorkItem W = items[it - ibase];
-                    if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                         sh, dv, ks, drift, rerr, my_stage, tasks,
-                                                                         ake, ap, mseg);
-                    else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
-                                                                          diff, sh, dv, ks, drift, rerr, my_stage,
-                                                                          tasks, ake, ap, mseg);
-                }
-            }
-            taken += r1 - r0;
-            r0 = r1;
         }
-        if (tid == 0) {
-            if (!posted)
-                *next_slot = c_next;
-            sh.ring[(k + 2) % 3] = kNoChunk;  // the slot of chunk k - 1, free now
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int m2 = __shfl_down_sync(0xffffffffu, most, o);
+            const int b2 = __shfl_down_sync(0xffffffffu, best, o);
+            if (m2 > most) {
+                most = m2;
+                best = b2;
+            }
+        }
+        if (lane == 0) {
+            sh.pick_n[warp] = most;
+            sh.pick_s[warp] = best;
         }
         __syncthreads();
+        most = 0;
+        cur = -1;
+        for (int w = 0; w < NW; ++w)
+            if (sh.pick_n[w] > most) {
+                most = sh.pick_n[w];
+                cur = sh.pick_s[w];
+            }
+        __syncthreads();  // the picks and the epilogue's scratch are free again
     }
-    if (cur >= 0)
-        leave();
+
+    // the last block out rewinds the claim cursors for the next launch
     if (tid == 0) {
-        // the last block out rewinds the chunk counter for the next launch
         __threadfence();
-        const unsigned d = atomicAdd(A.claim + 1, 1u);
-        if (d + 1 == gridDim.x) {
-            A.claim[0] = 0u;
-            A.claim[1] = 0u;
-        }
+        sh.last = (atomicAdd(A.done, 1u) + 1 == gridDim.x) ? 1 : 0;
+    }
+    __syncthreads();
+    if (sh.last) {
+        for (int j = tid; j < A.n_slots; j += B)
+            A.cursor[j] = 0u;
+        if (tid == 0)
+            *A.done = 0u;
     }
 }
 
