@@ -114,6 +114,23 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def kernel_traffic(segments):
+    """DRAM bytes of one step-kernel launch over `segments` segments, scaled
+    from an ncu capture of a smaller case (profiles/k_step_traffic.json), or
+    None when the kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+    src = os.path.join(ROOT, "paper_1506_07207_gb300", "csrc", "sic_kernels.cu")
+    try:
+        d = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("kernel_sha256") != sha:
+            return None
+        return float(d["dram_bytes_per_segment"]) * segments
+    except Exception:
+        return None
+
+
 def sample_requests(n, rate=None):
     from paper_1506_07207_gb300 import inputs
     return inputs.serving_mix(n_requests=n, seed=SEED, rate=rate)
@@ -219,6 +236,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sic", choices=["sic", "reference"])
+    ap.add_argument("--workload", default="serving", choices=["serving", "two_stream"],
+                    help="serving: the request-mix sample; two_stream: the 8.4M-segment two-stream run alone")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
     ap.add_argument("--no-serving", action="store_true")
@@ -245,14 +264,26 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    from paper_1506_07207_gb300 import serving
+    from paper_1506_07207_gb300 import inputs, serving
     from paper_1506_07207_gb300.sic import Batch, Sim, sic_launch_count
 
-    reqs = sample_requests(args.requests)
-    probs = [r.problem() for r in reqs]
+    serving_mode = args.workload == "serving"
+    if serving_mode:
+        reqs = sample_requests(args.requests)
+        probs = [r.problem() for r in reqs]
+        config = describe(reqs, probs)
+    else:
+        probs = [inputs.two_stream_config()]
+        config = {"workload": "two-stream instability, 512 sheets x 16384 tracers (8,388,608 segments), "
+                              "Nx 1024, one simulation", "segments_resident": probs[0].n_segments,
+                  "l2": "256 MB read before every timed step (L2 flush)"}
 
-    # ---- value: the whole sample resident, one batch, one launch per step
+    # ---- value: every sampled problem resident, one batch, one launch per step
     stream = torch.cuda.Stream()
+    flush = None
+    if not serving_mode:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        flush.fill_(1.0)
     sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream) for p in probs]
     batch = Batch(sims)
     S = batch.sic_batch_segments()
@@ -273,6 +304,9 @@ def main():
     with Clocks(uuid) as clk:
         t_wall = time.perf_counter()
         for a, b in evs:
+            if flush is not None:
+                with torch.cuda.stream(stream):
+                    flush.sum()
             a.record(stream)
             batch.sic_batch_step(1)
             b.record(stream)
@@ -300,22 +334,22 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 push/deposit, i64 fixed-point charge, exact integer field solve",
-        "data": "synthetic", "config": describe(reqs, probs),
+        "data": "synthetic", "config": config,
     }
     peak, peak_src = peaks()
     avg_s = statistics.mean(step_ms) / 1e3
     achieved = ALGO_BYTES_PER_SEGMENT * S / avg_s / 1e9
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": kernel_traffic(S),
                         "kernel": "k_step (fused gather-kick-drift-deposit + field epilogue), one launch "
-                                  "per step over every resident request",
+                                  "per step over every resident simulation",
                         "algorithmic_bytes_per_launch": ALGO_BYTES_PER_SEGMENT * S,
                         "avg_launch_ms": avg_s * 1e3, "peak_source": peak_src}
     line["clocks"] = clocks
     line["gpu_launches"] = int(launches)
     line["wall_s_timed_region"] = t_wall
 
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and serving_mode and not args.no_serving:
         works = [p.n_segments * p.n_steps for p in probs]
         rate = args.load * value / (sum(works) / len(works))
         arrivals = []
@@ -335,30 +369,49 @@ def main():
         out["load"] = args.load
         line["serving"] = out
     if rank == 0 and not args.no_e2e:
-        arrivals0 = [0.0] * len(probs)
-        r = serving.run_trace(probs, arrivals0, plain=False, max_active=64, chunk_steps=32)
-        steps_total = sum(p.n_steps for p in probs)
-        h2d = sum(8 * (p.x_template.size + 2 * p.n_sheets) for p in probs)
-        line["e2e"] = {"value": r["throughput"], "unit": UNIT,
-                       "h2d_bytes_per_step": h2d / steps_total,
-                       "d2h_bytes_per_step": 96 * len(probs) / steps_total,
-                       "note": "request server fed from host arrays (position template, per-sheet "
-                               "velocity and weight), all requests at t = 0, results read back; "
-                               "per-step bytes averaged over all requests' steps",
-                       "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "makespan_s": r["makespan_s"]}
-    if rank == 0 and not args.no_single:
+        if serving_mode:
+            arrivals0 = [0.0] * len(probs)
+            r = serving.run_trace(probs, arrivals0, plain=False, max_active=64, chunk_steps=32)
+            steps_total = sum(p.n_steps for p in probs)
+            h2d = sum(8 * (p.x_template.size + 2 * p.n_sheets) for p in probs)
+            line["e2e"] = {"value": r["throughput"], "unit": UNIT,
+                           "h2d_bytes_per_step": h2d / steps_total,
+                           "d2h_bytes_per_step": 96 * len(probs) / steps_total,
+                           "note": "request server fed from host arrays (position template, per-sheet "
+                                   "velocity and weight), all requests at t = 0, results read back; "
+                                   "per-step bytes averaged over all requests' steps",
+                           "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "makespan_s": r["makespan_s"]}
+        else:
+            line["e2e"] = e2e_single(torch, Sim, probs[0])
+    if rank == 0 and serving_mode and not args.no_single:
         line["single_sim"] = single_sim(torch, Sim, args.steps, args.warmup)
     if rank == 0 and not args.no_cpu_baseline:
         v, upd, el = oracle_rate(probs)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"4 steps each of the sampled requests of at most 2^24 segments, in order, until 12 s "
-                                          f"({upd} segment-updates in {el:.1f} s), FP64 C oracle, "
-                                          f"single thread"}
+                                "sample": f"4 steps each of the sampled problems of at most 2^24 segments, "
+                                          f"in order, until 12 s ({upd} segment-updates in {el:.1f} s), "
+                                          f"FP64 C oracle, single thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def e2e_single(torch, Sim, p, n_steps=200):
+    """sic_create from host arrays, n_steps steps, state read back: end to end."""
+    x, v, w = p.x, p.v, p.w
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = Sim.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, x, v, w, history_len=1)
+    sim.sic_step(n_steps)
+    xs, vs = sim.sic_get_state()
+    el = time.perf_counter() - t0
+    sim.sic_destroy()
+    return {"value": p.n_segments * n_steps / el, "unit": UNIT,
+            "h2d_bytes_per_step": 24 * p.n_tracers / n_steps, "d2h_bytes_per_step": 16 * p.n_tracers / n_steps,
+            "note": f"sic_create from host float64 x, v, w (full arrays), {n_steps} steps, positions and "
+                    f"velocities read back; bytes averaged over the steps"}
 
 
 if __name__ == "__main__":

@@ -1,19 +1,23 @@
 // sic_kernels.cu -- sm_103a kernel of the SIC step.
 //
-// k_step runs one whole step (or one of its halves) in a single launch:
-//   1. every warp takes work items of up to 256 consecutive tracers of one
-//      sheet (8 per lane) from its block's run of items, gathers E at each
-//      tracer (linear weighting between the two nodes), kicks, drifts, and
-//      writes the tracer to the other state buffer;
+// k_step runs one whole step (or one of its halves) in a single launch, over
+// one or many simulations:
+//   1. a block works on one simulation at a time; each of its warps claims
+//      runs of work items (up to 256 consecutive tracers of one sheet, 8 per
+//      lane) from that simulation's cursor, gathers E at each tracer (linear
+//      weighting between the two nodes), kicks, drifts, and writes the tracer
+//      to the other state buffer;
 //   2. it deposits the segment from each of its tracers to the next one
 //      (Sec. 2.3, Eq. overlap and Eq. rho_sum) into the block's shared-memory
 //      copy of the simulation's int64 charge mesh.  The tracer after the
 //      warp's last one is read from the input buffer and pushed again by the
 //      warp itself, so warps and blocks never wait for one another;
-//   3. when a block leaves a simulation it adds its mesh into the global mesh
-//      with int64 atomics and takes a ticket; the block that takes the last
-//      ticket of that simulation runs its epilogue: the exact integer field
-//      solve, the field energy, the diagnostic row, and the buffer swap.
+//   3. when the simulation has no unclaimed items left, the block adds its
+//      mesh into the global mesh with int64 atomics and counts its items on
+//      the simulation's ticket; the block that completes the count runs the
+//      epilogue: the exact integer field solve, the field energy, the
+//      diagnostic row, and the buffer swap.  The block then moves to the
+//      simulation with the most unclaimed items, until none has any.
 //
 // Deposit arithmetic: a segment [a, b] of q units in 32.32 fixed-point cell
 // coordinates gives its first cell F = round(q (e_1 - a) / (b - a)) (FP32),
