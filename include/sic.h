@@ -263,6 +263,35 @@ int sic_server_stats(sic_server *srv, sic_server_info *out);
  * simulations of results not yet taken. */
 void sic_server_destroy(sic_server *srv);
 
+/* ---- stepping without allocation (no counterpart in the paper) ------------
+ *
+ * sic_step_batch_static: the same steps, and bit-identical results, as
+ * sic_step_batch, for callers that may not allocate device memory while they
+ * step.  One example is a serving loop whose whole device-memory budget is
+ * already promised to resident simulations, so a plan allocation could fail or
+ * push it over budget mid-run.  Another is a loop that cannot afford the
+ * device-wide synchronisation of cudaFree.  The launch plan is written into
+ * one fixed scratch array in device memory per device (64 KiB); the call
+ * makes no allocation (no cudaMalloc, cudaMallocAsync or cudaFree, no host
+ * heap).
+ *
+ *   sims     n_sims distinct handles, all on one device (SIC_EINVAL if not);
+ *            at most SIC_STATIC_MAX_SIMS, else SIC_EINVAL and nothing is done.
+ *   n_steps  per simulation, >= 0; every member with steps left advances in
+ *            the same launches, and each stops at its own count.
+ *
+ * The launches run on sims[0]'s stream, after the other members' streams have
+ * been synchronised, and the call returns once they are done.  The plan's
+ * counters (claim cursors, item tickets, finished blocks) are cleared before
+ * every use.  The first call on a device looks up the scratch address there
+ * (one runtime query with that device current); make that first call before
+ * any stream capture.  The scratch is shared: calls on the same device that
+ * overlap in time (two host threads) race on it, and the caller must
+ * serialise them.  Errors as for sic_step_batch; device-side errors of the
+ * steps show at the next sic_sync or sic_diagnostics of a member. */
+#define SIC_STATIC_MAX_SIMS 64
+int sic_step_batch_static(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -993,3 +993,180 @@ const char *sic_strerror(int code)
 int64_t sic_launch_count(void) { return sic::launches(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sic_step_batch_static: sic_step_batch with its launch plan in a fixed,
+// file-scope device array instead of a per-call allocation.  The paper has no
+// counterpart; this serves callers that must not allocate device memory while
+// stepping.
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 64 * 1024;
+constexpr int kStaticMaxDevices = 64;
+
+// per charge-mode group: descriptor table, item offsets, claim cursors, item
+// tickets, finished-block count
+constexpr size_t round256(size_t n) { return (n + 255) / 256 * 256; }
+constexpr size_t kStaticTable = round256(sizeof(SimDev) * SIC_STATIC_MAX_SIMS);
+constexpr size_t kStaticSlots = round256(4 * (SIC_STATIC_MAX_SIMS + 1));
+constexpr size_t kStaticCounters = round256(4 * (2 * SIC_STATIC_MAX_SIMS + 1));
+constexpr size_t kStaticGroup = kStaticTable + kStaticSlots + kStaticCounters;
+static_assert(2 * kStaticGroup <= kStaticScratchBytes, "static plan scratch too small");
+
+static __device__ __align__(256) unsigned char g_step_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void *g_static_addr[kStaticMaxDevices] = {};
+
+// The scratch's address on device dev, looked up once per device with dev
+// current (the caller made it current).
+cudaError_t static_scratch(int dev, unsigned char **out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (dev < 0 || dev >= kStaticMaxDevices)
+        return cudaErrorInvalidDevice;
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_step_scratch);
+        if (e != cudaSuccess)
+            return e;
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    return cudaSuccess;
+}
+
+// Write the plan of one group into its part of the scratch (stream-ordered
+// after the previous launches), clear its counters, and return its arguments.
+cudaError_t static_plan(unsigned char *region, sic_sim *const *grp, int n, cudaStream_t s, LaunchArgs &a, int &grid,
+                        bool &pow2)
+{
+    SimDev table[SIC_STATIC_MAX_SIMS];
+    int32_t slot_begin[SIC_STATIC_MAX_SIMS + 1];
+    int nx_max = 2;
+    pow2 = true;
+    int64_t n_items = 0;
+    for (int i = 0; i < n; ++i) {
+        table[i] = grp[i]->h;
+        nx_max = std::max(nx_max, grp[i]->nx);
+        pow2 = pow2 && ((grp[i]->nx & (grp[i]->nx - 1)) == 0);
+        slot_begin[i] = (int32_t)n_items;
+        n_items += (int64_t)grp[i]->items.size();
+    }
+    slot_begin[n] = (int32_t)n_items;
+    const bool per_q = grp[0]->per_q;
+    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
+    if (per_sm < 1)
+        per_sm = 1;
+    const int by_items = (int)((n_items + SIC_K1_WARPS - 1) / SIC_K1_WARPS);
+    grid = std::max(1, std::min(by_items, env_int("SIC_GRID", num_sms() * per_sm)));
+    unsigned char *t = region, *sb = region + kStaticTable, *ctr = sb + kStaticSlots;
+    cudaError_t e = cudaMemcpyAsync(t, table, sizeof(SimDev) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sb, slot_begin, 4 * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctr, 0, 4 * (size_t)(2 * n + 1), s);  // cursors, tickets, done start at zero
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);  // the host tables are on this stack frame
+    if (e != cudaSuccess)
+        return e;
+    a = LaunchArgs{};
+    a.sims = reinterpret_cast<const SimDev *>(t);
+    a.slot_begin = reinterpret_cast<const int32_t *>(sb);
+    a.cursor = reinterpret_cast<unsigned *>(ctr);
+    a.tickets = reinterpret_cast<unsigned *>(ctr) + n;
+    a.done = reinterpret_cast<unsigned *>(ctr) + 2 * n;
+    a.n_items = (int32_t)n_items;
+    a.claim_q = (float)(1.0 / ((double)env_int("SIC_CLAIM_DIV", 4) * grid * SIC_K1_WARPS));
+    a.n_slots = n;
+    a.nx_max = nx_max;
+    a.drift = 1;
+    a.record = 1;
+    a.kick_scale = 1.0f;
+    return cudaSuccess;
+}
+
+int static_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)
+{
+    cudaStream_t bs = sims[0]->stream;
+    // the first member's stream runs the launches: wait for the others' work
+    for (int i = 1; i < n_sims; ++i)
+        if (cudaStreamSynchronize(sims[i]->stream) != cudaSuccess)
+            return SIC_ECUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return SIC_ECUDA;
+    unsigned char *scratch = nullptr;
+    if (static_scratch(dev, &scratch) != cudaSuccess)
+        return SIC_ECUDA;
+    int32_t left[SIC_STATIC_MAX_SIMS];
+    for (int i = 0; i < n_sims; ++i)
+        left[i] = n_steps[i];
+    while (true) {
+        int32_t k = INT32_MAX;
+        sic_sim *grp[2][SIC_STATIC_MAX_SIMS];
+        int ng[2] = {0, 0};
+        for (int i = 0; i < n_sims; ++i)
+            if (left[i] > 0) {
+                k = std::min(k, left[i]);
+                const int g = sims[i]->per_q ? 1 : 0;
+                grp[g][ng[g]++] = sims[i];
+            }
+        if (ng[0] == 0 && ng[1] == 0)
+            break;
+        LaunchArgs a[2];
+        int grid[2] = {0, 0};
+        bool pow2[2] = {true, true};
+        for (int g = 0; g < 2; ++g)
+            if (ng[g] && static_plan(scratch + g * kStaticGroup, grp[g], ng[g], bs, a[g], grid[g], pow2[g]) !=
+                             cudaSuccess)
+                return SIC_ECUDA;
+        for (int32_t st = 0; st < k; ++st)
+            for (int g = 0; g < 2; ++g)
+                if (ng[g] && launch_step_kernel(a[g], grid[g], MODE_STEP, g == 1, pow2[g], bs) != cudaSuccess)
+                    return SIC_ECUDA;
+        for (int i = 0; i < n_sims; ++i)
+            if (left[i] > 0)
+                left[i] -= k;
+    }
+    // later work on any member's stream comes after these steps
+    return cudaStreamSynchronize(bs) == cudaSuccess ? SIC_OK : SIC_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int sic_step_batch_static(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)
+{
+    if (!sims || n_sims < 1 || !n_steps)
+        return SIC_EINVAL;
+    if (n_sims > SIC_STATIC_MAX_SIMS)
+        return SIC_EINVAL;  // more simulations than the fixed scratch holds
+    int dev = -1;
+    for (int i = 0; i < n_sims; ++i) {
+        if (!sims[i] || n_steps[i] < 0)
+            return SIC_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (sims[k] == sims[i])
+                return SIC_EINVAL;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, sims[i]->dmem) != cudaSuccess)
+            return SIC_ECUDA;
+        if (dev < 0)
+            dev = at.device;
+        else if (at.device != dev)
+            return SIC_EINVAL;  // all members on one device
+    }
+    // run with the members' device current; put the caller's back after
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess)
+        return SIC_ECUDA;
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess)
+        return SIC_ECUDA;
+    const int rc = static_batch(sims, n_sims, n_steps);
+    if (prev != dev)
+        cudaSetDevice(prev);
+    return rc;
+}

@@ -32,6 +32,7 @@ EXPORTS = [
     "sic_batch_create", "sic_batch_step", "sic_batch_segments", "sic_batch_destroy",
     "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
     "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
+    "sic_step_batch_static",
 ]
 
 
@@ -121,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_push": ([simp], ctypes.c_int),
         "sic_step": ([simp, ctypes.c_int32], ctypes.c_int),
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
+        "sic_step_batch_static": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
         "sic_history": ([simp, dp, ip], ctypes.c_int),
         "sic_get_state": ([simp, dp, dp], ctypes.c_int),
@@ -336,6 +338,20 @@ def sic_step_batch(sims, n_steps):
         raise ValueError("one step count per simulation")
     _check(_lib.sic_step_batch(arr, len(sims), steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
            "sic_step_batch")
+
+
+SIC_STATIC_MAX_SIMS = 64
+
+
+def sic_step_batch_static(sims, n_steps):
+    """``sic_step_batch`` with the launch plan in the library's fixed device
+    scratch: no allocation; at most SIC_STATIC_MAX_SIMS simulations."""
+    arr = (ctypes.c_void_p * len(sims))(*[s.handle for s in sims])
+    steps = np.ascontiguousarray(n_steps, dtype=np.int32)
+    if steps.size != len(sims):
+        raise ValueError("one step count per simulation")
+    _check(_lib.sic_step_batch_static(arr, len(sims), steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "sic_step_batch_static")
 
 
 class Batch:
