@@ -1,10 +1,11 @@
 // sic_api.cu -- host runtime behind the C ABI of include/sic.h.
 //
-// Owns each simulation's device memory (one stream-ordered allocation), the
-// work-item plan (up to 256 consecutive tracers of one sheet per item, one
-// warp's task; contiguous runs of items per block, balanced over a
-// persistent grid of SMs x resident blocks), CUDA-graph capture of the step kernel, and
-// batching of several simulations into shared launches.
+// Owns each simulation's device memory (one stream-ordered allocation), its
+// work items (up to 32 R consecutive tracers of one sheet, one warp's task at
+// a time), the launch plans (the simulations of a launch, their claim cursors
+// and tickets, a persistent grid of SMs x resident blocks), CUDA-graph
+// capture of the step kernel, and batching of several simulations into
+// shared launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -132,7 +133,7 @@ int validate(const sic_config *c, bool need_sheets)
     return SIC_OK;
 }
 
-// Split every sheet into items of at most 256 tracers (one warp's task);
+// Split every sheet into items of at most 32 R tracers (one warp's task);
 // each item knows the tracer after its last one (its halo).
 void plan_items(sic_sim *sim)
 {

@@ -27,10 +27,10 @@
 #define SIC_ALIGN_TRACERS 32
 #define SIC_K1_BLOCK 256
 #ifndef SIC_K1_R
-#define SIC_K1_R 8
+#define SIC_K1_R 4           // tracers per lane: a work item is 32 R tracers
 #endif
 #ifndef SIC_K1_MIN_BLOCKS
-#define SIC_K1_MIN_BLOCKS 2
+#define SIC_K1_MIN_BLOCKS 3  // resident blocks per SM the registers allow
 #endif
 #define SIC_K1_WARPS (SIC_K1_BLOCK / 32)
 #define SIC_K1_WARP_TRACERS (32 * SIC_K1_R)
@@ -42,7 +42,7 @@
 
 // Per-warp double-buffered staging of the next work item in shared memory
 // (filled by bulk copies): positions, velocities and, per-tracer charge mode,
-// half charges, each with room for the item's 256 tracers plus its halo.
+// half charges, each with room for the item's 32 R tracers plus its halo.
 #define SIC_STAGE_U_BYTES (((SIC_K1_WARP_TRACERS + 1) * 8 + 15) / 16 * 16)
 #define SIC_STAGE_V_BYTES (((SIC_K1_WARP_TRACERS + 1) * 4 + 15) / 16 * 16)
 #define SIC_STAGE_Q_BYTES SIC_STAGE_V_BYTES
@@ -56,7 +56,7 @@ struct NxDiv {
     int32_t offset;    // multiple of nx >= 2^30, added before the division
 };
 
-// One work item, the task of one warp: up to 256 consecutive tracers of one sheet.
+// One work item, the task of one warp: up to 32 R consecutive tracers of one sheet.
 struct WorkItem {
     int32_t sim;        // slot in the launch's simulation table
     int32_t local;      // index of the item inside its simulation

@@ -3,7 +3,7 @@
 // k_step runs one whole step (or one of its halves) in a single launch, over
 // one or many simulations:
 //   1. a block works on one simulation at a time; each of its warps claims
-//      runs of work items (up to 256 consecutive tracers of one sheet, 8 per
+//      runs of work items (up to 32 R consecutive tracers of one sheet, R per
 //      lane) from that simulation's cursor, gathers E at each tracer (linear
 //      weighting between the two nodes), kicks, drifts, and writes the tracer
 //      to the other state buffer;
@@ -29,6 +29,8 @@
 // array, so a segment costs O(1) shared-memory atomics at any length.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "sic_internal.h"
 
@@ -621,8 +623,8 @@ __device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int 
 
 // ---------------------------------------------------------------- kernel ----
 
-// One work item (up to 256 tracers, 8 per lane) of the current simulation.
-// FULL: the item has all 256 tracers, so no lane needs a bounds test.
+// One work item (up to 32 R tracers, R per lane) of the current simulation.
+// FULL: the item has all 32 R tracers, so no lane needs a bounds test.
 template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED>
 __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
                                         const float *__restrict__ Vin, long long *__restrict__ Uout,
@@ -1366,8 +1368,29 @@ size_t step_smem_bytes(int nx_max, bool staged, bool per_q)
     return stage_offset(nx_max) + (size_t)NW * buf + (size_t)NW * WT * sizeof(unsigned short);
 }
 
-// Stage items through shared memory when two blocks still fit on an SM.
-bool step_staged(int nx_max, bool per_q) { return step_smem_bytes(nx_max, true, per_q) <= 113 * 1024; }
+// Blocks of the step kernel that the SM's shared memory holds (registers cap
+// them at SIC_K1_MIN_BLOCKS by the launch bounds).
+static int blocks_by_smem(size_t smem)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && v > 0)
+            per_sm = v;
+        else
+            per_sm = 228 * 1024;
+    }
+    const int n = (int)((size_t)per_sm / (smem + 1024));  // 1 KB reserved per block
+    return std::min(n, SIC_K1_MIN_BLOCKS);
+}
+
+// Stage items through shared memory unless the staging buffers would cost an
+// SM a block (large meshes): occupancy hides more latency than staging.
+bool step_staged(int nx_max, bool per_q)
+{
+    return blocks_by_smem(step_smem_bytes(nx_max, true, per_q)) >= blocks_by_smem(step_smem_bytes(nx_max, false, per_q));
+}
 
 static long long g_launches = 0;
 void count_launches(int64_t n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
