@@ -53,6 +53,8 @@ def _load():
             lib.orc_deposit.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                         ip, bp, ip, dp, dp, dp]
             lib.orc_deposit.restype = ctypes.c_int
+            lib.orc_deposit_linear.argtypes = lib.orc_deposit.argtypes
+            lib.orc_deposit_linear.restype = ctypes.c_int
             lib.orc_field.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             lib.orc_field.restype = None
             lib.orc_gather.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_long,
@@ -63,7 +65,7 @@ def _load():
             lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                     ip, bp, ip, ctypes.c_long, dp, dp, dp,
-                                    ctypes.c_int, dp, dp, dp]
+                                    ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.orc_run.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -88,15 +90,17 @@ def _sheets(counts, closed, winding):
     return counts, closed, winding
 
 
-def deposit(nx, L, counts, closed, winding, x, w):
-    """Charge per cell (Eq. overlap and Eq. rho_sum, times dx)."""
+def deposit(nx, L, counts, closed, winding, x, w, order=0):
+    """Charge per cell (Eq. overlap and Eq. rho_sum, times dx); order 1 uses
+    the piecewise-linear particles of Sec. 2.5."""
     lib = _load()
     counts, closed, winding = _sheets(counts, closed, winding)
     x, w = _f64(x), _f64(w)
     if x.shape != w.shape or x.size != int(counts.sum()):
         raise ValueError("x and w need one entry per tracer")
     out = np.zeros(int(nx), dtype=np.float64)
-    rc = lib.orc_deposit(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
+    fn = lib.orc_deposit_linear if order == 1 else lib.orc_deposit
+    rc = fn(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
                          _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
                          _ptr(x, ctypes.c_double), _ptr(w, ctypes.c_double),
                          _ptr(out, ctypes.c_double))
@@ -105,9 +109,9 @@ def deposit(nx, L, counts, closed, winding, x, w):
     return out
 
 
-def density(nx, L, counts, closed, winding, x, w):
+def density(nx, L, counts, closed, winding, x, w, order=0):
     """Cell-averaged number density n_j = charge_j / dx."""
-    return deposit(nx, L, counts, closed, winding, x, w) / (float(L) / int(nx))
+    return deposit(nx, L, counts, closed, winding, x, w, order) / (float(L) / int(nx))
 
 
 def field(nx, L, charge):
@@ -137,7 +141,7 @@ def field_energy(nx, L, E):
 
 
 def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
-        half_step_init=True, record_E=False):
+        half_step_init=True, record_E=False, order=0):
     """Leapfrog SIC run; returns dict(x, v, E, hist[, E_hist]).
 
     hist has n_steps+1 rows [W_E, KE, P, Q_total]; KE and P are time-centred
@@ -157,7 +161,7 @@ def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
                      _ptr(winding, ctypes.c_int32), n, _ptr(x, ctypes.c_double),
                      _ptr(v, ctypes.c_double), _ptr(w, ctypes.c_double), int(n_steps),
                      _ptr(hist, ctypes.c_double), _ptr(e_hist, ctypes.c_double),
-                     _ptr(E, ctypes.c_double))
+                     _ptr(E, ctypes.c_double), int(order))
     if rc:
         raise ValueError("every sheet needs at least two tracers")
     out = dict(x=x, v=v, E=E, hist=hist)
@@ -166,8 +170,8 @@ def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
     return out
 
 
-def run_problem(p, n_steps=None, record_E=False):
+def run_problem(p, n_steps=None, record_E=False, order=0):
     """``run`` on a problem from ``paper_1506_07207_gb300.inputs``."""
     return run(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
                p.n_steps if n_steps is None else n_steps, qm=p.qm,
-               half_step_init=p.half_step_init, record_E=record_E)
+               half_step_init=p.half_step_init, record_E=record_E, order=order)

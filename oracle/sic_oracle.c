@@ -113,6 +113,122 @@ int orc_deposit(int nx, double L, int n_sheets, const int32_t *counts,
 }
 
 /*
+ * Piecewise-linear particles (Sec. 2.5, Eq. piecewise_linear with the
+ * gradient of Eq. gradient_rho_estimate).
+ *
+ * Particle s between tracers x_i and x_{i+1} keeps its charge q_s and its
+ * zeroth-order density rho0_s = q_s / |x_{i+1} - x_i|, centred on its centroid
+ * c_s = (x_i + x_{i+1}) / 2; on its extent the density is
+ *     rho0_s + (x - c_s) g_s,
+ * with g_s the central difference over the two particles next to it along
+ * the sheet:
+ *     g_s = (rho0_{s+1} - rho0_{s-1}) / (c_{s+1} - c_{s-1}).
+ * g_s is 0 (the particle stays a box) when a neighbour is missing (the two
+ * ends of an open sheet), when any of the three particles has zero length,
+ * or when the centroids are not in order along the sheet, i.e. neither
+ * c_{s-1} < c_s < c_{s+1} nor the reverse (the corner of a fold, Sec. 2.5).
+ * On a closed sheet the closing particle (x_{n-1}, x_0 + winding L) is the
+ * neighbour of the first and the last ones; its centroid is shifted by one
+ * winding when it is compared with theirs.
+ *
+ * The charge of the piece [lo, hi] of a particle inside a cell is the integral
+ * of its density: rho0 (hi - lo) + g ((hi - c)^2 - (lo - c)^2) / 2, summed over
+ * the periodic images like deposit_segment.  Over the whole particle the
+ * linear term integrates to zero, so every particle still carries exactly q.
+ */
+static void deposit_linear_segment(double xa, double xb, double q, double g,
+                                   int nx, double dx, double *charge)
+{
+    double a = xa < xb ? xa : xb;
+    double b = xa < xb ? xb : xa;
+    long ma = (long)floor(a / dx);
+    long mb = (long)floor(b / dx);
+    if (b == a) {
+        charge[wrap_cell(ma, nx)] += q;
+        return;
+    }
+    double rho0 = q / (b - a);
+    double c = 0.5 * (a + b);
+    for (long m = ma - 1; m <= mb + 1; ++m) {
+        double lo = a > m * dx ? a : m * dx;
+        double hi = b < (m + 1) * dx ? b : (m + 1) * dx;
+        if (hi > lo)
+            charge[wrap_cell(m, nx)] +=
+                rho0 * (hi - lo) + g * ((hi - c) * (hi - c) - (lo - c) * (lo - c)) / 2.0;
+    }
+}
+
+int orc_deposit_linear(int nx, double L, int n_sheets, const int32_t *counts,
+                       const uint8_t *closed, const int32_t *winding,
+                       const double *x, const double *w, double *charge)
+{
+    double dx = L / nx;
+    memset(charge, 0, sizeof(double) * (size_t)nx);
+    long base = 0;
+    for (int s = 0; s < n_sheets; ++s) {
+        long n = counts[s];
+        if (n < 2)
+            return -1;
+        /* the sheet's particles: endpoints, charge, density, centroid */
+        long np = closed[s] ? n : n - 1;
+        double *xa = (double *)malloc(sizeof(double) * (size_t)np);
+        double *xb = (double *)malloc(sizeof(double) * (size_t)np);
+        double *q = (double *)malloc(sizeof(double) * (size_t)np);
+        double *rho0 = (double *)malloc(sizeof(double) * (size_t)np);
+        double *c = (double *)malloc(sizeof(double) * (size_t)np);
+        double shift = (double)winding[s] * L;
+        for (long k = 0; k < np; ++k) {
+            long i = k, j = k + 1;
+            xa[k] = x[base + i];
+            if (j < n) {
+                xb[k] = x[base + j];
+                q[k] = 0.5 * (w[base + i] + w[base + j]);
+            } else {
+                xb[k] = x[base] + shift;
+                q[k] = 0.5 * (w[base + i] + w[base]);
+            }
+            double len = fabs(xb[k] - xa[k]);
+            rho0[k] = len > 0.0 ? q[k] / len : 0.0;
+            c[k] = 0.5 * (xa[k] + xb[k]);
+        }
+        for (long k = 0; k < np; ++k) {
+            double g = 0.0;
+            int has_prev = closed[s] || k > 0;
+            int has_next = closed[s] || k + 1 < np;
+            if (has_prev && has_next) {
+                long kp = k > 0 ? k - 1 : np - 1;
+                long kn = k + 1 < np ? k + 1 : 0;
+                double cp = c[kp] - (k == 0 ? shift : 0.0);
+                double cn = c[kn] + (k + 1 == np ? shift : 0.0);
+                int lengths = xa[kp] != xb[kp] && xa[k] != xb[k] && xa[kn] != xb[kn];
+                int ordered = (cp < c[k] && c[k] < cn) || (cp > c[k] && c[k] > cn);
+                if (lengths && ordered)
+                    g = (rho0[kn] - rho0[kp]) / (cn - cp);
+            }
+            deposit_linear_segment(xa[k], xb[k], q[k], g, nx, dx, charge);
+        }
+        free(xa);
+        free(xb);
+        free(q);
+        free(rho0);
+        free(c);
+        base += n;
+    }
+    return 0;
+}
+
+/* The deposit of the given order: 0 box particles, 1 piecewise linear. */
+static int deposit_order(int order, int nx, double L, int n_sheets,
+                         const int32_t *counts, const uint8_t *closed,
+                         const int32_t *winding, const double *x,
+                         const double *w, double *charge)
+{
+    if (order == 1)
+        return orc_deposit_linear(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+    return orc_deposit(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+}
+
+/*
  * Field solve (Sec. 2.1 with C = 1): n_j = charge_j / dx, rho_j = n_j - mean(n),
  * dE/dx = rho integrated exactly across each cell: E'_0 = 0,
  * E'_{j+1} = E'_j + dx rho_j; E_j = E'_j - mean(E').  rho and E may be NULL.
@@ -194,17 +310,19 @@ double orc_field_energy(int nx, double L, const double *E)
  * m_i = w_i / qm.  Row n_steps has W_E of the final field and NaN for KE, P.
  * e_hist (n_steps+1 rows of nx, may be NULL) gets every E^n.
  * On exit x = x^{n_steps}, v = v^{n_steps-1/2}, E_out = E^{n_steps} (may be NULL).
+ * order selects the deposit: 0 box particles (Sec. 2.3), 1 piecewise linear
+ * (Sec. 2.5).
  */
 int orc_run(int nx, double L, double dt, double qm, int half_step_init,
             int n_sheets, const int32_t *counts, const uint8_t *closed,
             const int32_t *winding, long n_tracers, double *x, double *v,
             const double *w, int n_steps, double *hist, double *e_hist,
-            double *E_out)
+            double *E_out, int order)
 {
     double *charge = (double *)malloc(sizeof(double) * (size_t)nx);
     double *E = (double *)malloc(sizeof(double) * (size_t)nx);
     double *ex = (double *)malloc(sizeof(double) * (size_t)n_tracers);
-    int rc = orc_deposit(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+    int rc = deposit_order(order, nx, L, n_sheets, counts, closed, winding, x, w, charge);
     if (rc)
         goto done;
     orc_field(nx, L, charge, NULL, E);
@@ -248,7 +366,7 @@ int orc_run(int nx, double L, double dt, double qm, int half_step_init,
             h[2] = p;
             h[3] = qtot;
         }
-        rc = orc_deposit(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+        rc = deposit_order(order, nx, L, n_sheets, counts, closed, winding, x, w, charge);
         if (rc)
             goto done;
         orc_field(nx, L, charge, NULL, E);

@@ -291,3 +291,110 @@ def test_two_stream_growth_rate():
     a = np.abs(fits.mode(r["E_hist"], 1))
     g = fits.growth_rate(t, a, 10.0, 28.0)
     assert abs(g / theory.warm_two_stream_rate(0.2, 2.4, 0.1) - 1) < 0.01
+
+
+# -------------------------------------------- piecewise-linear particles ----
+# Sec. 2.5: each particle's density is linear about its centroid, with the
+# central-difference gradient over its two neighbours along the sheet.
+
+def test_linear_particles_reproduce_a_linear_density():
+    """Tracers at the equal-charge quantiles of rho(x) = alpha + beta x: the
+    mean of a linear density over a particle is its value at the centroid, so
+    the central difference is exactly beta and every interior particle is
+    the true density.  Cells covered by interior particles get the exact
+    integral; the box particles of Sec. 2.3 do not."""
+    alpha, beta, X, n = 1.0, 0.6, 3.0, 201
+    nx, L = 16, 4.0
+    dx = L / nx
+    total = alpha * X + beta * X * X / 2
+    q = total / (n - 1)
+    k = np.arange(n)
+    x = (-alpha + np.sqrt(alpha * alpha + 2 * beta * k * q)) / beta
+    x[-1] = X
+    w = np.full(n, q)
+    lin = oracle.deposit(nx, L, [n], [0], [0], x, w, order=1)
+    box = oracle.deposit(nx, L, [n], [0], [0], x, w, order=0)
+    j = np.arange(nx)
+    exact = alpha * dx + beta * ((j + 1) ** 2 - j ** 2) * dx * dx / 2
+    inner = (j * dx >= x[1]) & ((j + 1) * dx <= x[-2])
+    assert inner.sum() >= 8
+    np.testing.assert_allclose(lin[inner], exact[inner], rtol=1e-12)
+    assert np.abs(box[inner] - exact[inner]).max() > 1e-6
+    assert math.isclose(lin.sum(), total, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_linear_particles_conserve_charge(seed):
+    rng = np.random.default_rng(100 + seed)
+    nx, L = int(rng.integers(3, 11)), float(rng.choice([1.0, 2.5]))
+    counts = [int(c) for c in rng.integers(2, 9, size=3)]
+    closed = [int(c) for c in rng.integers(0, 2, size=3)]
+    winding = [int(c) for c in rng.integers(-1, 3, size=3)]
+    x = _dyadic(rng, sum(counts), L)
+    w = rng.integers(1, 9, size=sum(counts)) / 8.0
+    lin = oracle.deposit(nx, L, counts, closed, winding, x, w, order=1)
+    want = 0.0
+    base = 0
+    for n, c in zip(counts, closed):
+        ws = w[base:base + n]
+        want += 0.5 * (ws[:-1] + ws[1:]).sum() + (0.5 * (ws[-1] + ws[0]) if c else 0.0)
+        base += n
+    assert math.isclose(lin.sum(), want, rel_tol=1e-12)
+
+
+def test_fold_corner_keeps_the_box_particle():
+    """The middle particle's centroid lies beyond both neighbours' (a fold
+    corner) and the two others are sheet ends: no gradient anywhere, so the
+    deposit is the box deposit.  Without the fold the middle particle gets a
+    gradient and the deposits differ."""
+    nx, L = 8, 2.0
+    w = np.full(4, 0.5)
+    folded = np.array([0.1, 0.9, 0.4, 0.2])      # centroids 0.5, 0.65, 0.3
+    np.testing.assert_allclose(oracle.deposit(nx, L, [4], [0], [0], folded, w, order=1),
+                               oracle.deposit(nx, L, [4], [0], [0], folded, w, order=0), rtol=1e-14, atol=1e-16)
+    straight = np.array([0.1, 0.4, 0.9, 1.7])    # centroids 0.25, 0.65, 1.3
+    lin = oracle.deposit(nx, L, [4], [0], [0], straight, w, order=1)
+    box = oracle.deposit(nx, L, [4], [0], [0], straight, w, order=0)
+    assert np.abs(lin - box).max() > 1e-3
+    assert math.isclose(lin.sum(), box.sum(), rel_tol=1e-14)
+
+
+def test_linear_particles_converge_faster():
+    """Cell charges of rho = 1 + A cos(2 pi x / L) sampled by N tracers at its
+    equal-charge quantiles (one closed sheet): the box particles converge at
+    second order, the piecewise-linear ones at third order or better."""
+    from scipy.optimize import brentq
+    L, nx, A = 1.0, 16, 0.5
+    dx = L / nx
+
+    def cdf(x):
+        return x + A * L / (2 * np.pi) * np.sin(2 * np.pi * x / L)
+
+    exact = np.diff(cdf(np.arange(nx + 1) * dx))
+    Ns = [40, 80, 160, 320, 640]
+    err = {0: [], 1: []}
+    for N in Ns:
+        xs = np.array([brentq(lambda t: cdf(t) - k / N, -1e-9, L + 1e-9) for k in range(N)])
+        w = np.full(N, 1.0 / N)
+        for order in (0, 1):
+            got = oracle.deposit(nx, L, [N], [1], [1], xs, w, order=order)
+            err[order].append(np.abs(got - exact).max())
+    s0 = np.polyfit(np.log(Ns), np.log(err[0]), 1)[0]
+    s1 = np.polyfit(np.log(Ns), np.log(err[1]), 1)[0]
+    assert -2.6 < s0 < -1.4, s0
+    assert s1 < -2.8, s1
+    assert err[1][-1] < 1e-2 * err[0][-1]
+
+
+def test_linear_particles_run_keeps_charge_and_oscillates():
+    """A run with piecewise-linear particles keeps the total charge and still
+    oscillates at the leapfrog plasma frequency (Langmuir sheet)."""
+    p = inputs.langmuir(n_tracers=512, nx=64)
+    r = oracle.run_problem(p, n_steps=80, order=1)
+    q = r["hist"][:, 3]
+    np.testing.assert_allclose(q, q[0], rtol=1e-13)
+    W = r["hist"][:-1, 0]
+    t = np.arange(80) * p.dt
+    tm, _ = fits.local_maxima(t, W)
+    period = 2 * np.mean(np.diff(tm))       # W_E peaks twice per period
+    assert abs(2 * np.pi / period / theory.leapfrog_omega(p.dt) - 1) < 2e-3
