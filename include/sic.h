@@ -85,6 +85,12 @@ typedef struct {
                                           every periodic image counting */
     int32_t history_len;               /* rows of the per-step diagnostic ring, >= 1 */
     void *stream;                      /* cudaStream_t the simulation runs on, NULL = its own */
+    int32_t deposit_order;             /* 0: box particles, uniform density between two
+                                          tracers (Sec. 2.3); 1: piecewise-linear particles,
+                                          density linear about the centroid with the
+                                          central-difference gradient of Sec. 2.5
+                                          (Eq. gradient_rho_estimate), none at a fold corner
+                                          or an open end; other values SIC_EINVAL */
 } sic_config;
 
 /* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum

@@ -129,7 +129,9 @@ int orc_deposit(int nx, double L, int n_sheets, const int32_t *counts,
  * c_{s-1} < c_s < c_{s+1} nor the reverse (the corner of a fold, Sec. 2.5).
  * On a closed sheet the closing particle (x_{n-1}, x_0 + winding L) is the
  * neighbour of the first and the last ones; its centroid is shifted by one
- * winding when it is compared with theirs.
+ * winding when it is compared with theirs.  A particle at least one box
+ * length long also stays a box (the paper stops a run at such a particle,
+ * Sec. 3.2; keeping it a box bounds the per-particle work).
  *
  * The charge of the piece [lo, hi] of a particle inside a cell is the integral
  * of its density: rho0 (hi - lo) + g ((hi - c)^2 - (lo - c)^2) / 2, summed over
@@ -202,7 +204,8 @@ int orc_deposit_linear(int nx, double L, int n_sheets, const int32_t *counts,
                 double cn = c[kn] + (k + 1 == np ? shift : 0.0);
                 int lengths = xa[kp] != xb[kp] && xa[k] != xb[k] && xa[kn] != xb[kn];
                 int ordered = (cp < c[k] && c[k] < cn) || (cp > c[k] && c[k] > cn);
-                if (lengths && ordered)
+                int shorter = fabs(xb[k] - xa[k]) < L;
+                if (lengths && ordered && shorter)
                     g = (rho0[kn] - rho0[kp]) / (cn - cp);
             }
             deposit_linear_segment(xa[k], xb[k], q[k], g, nx, dx, charge);

@@ -118,6 +118,8 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (c->history_len < 1)
         return SIC_EINVAL;
+    if (c->deposit_order != 0 && c->deposit_order != 1)
+        return SIC_EINVAL;
     if (need_sheets) {
         if (!c->tracers_per_sheet || !c->sheet_closed)
             return SIC_EINVAL;
@@ -139,6 +141,7 @@ void plan_items(sic_sim *sim)
 {
     const int item = SIC_K1_WARP_TRACERS;
     sim->items.clear();
+    sim->pl_items.clear();
     for (int s = 0; s < sim->M; ++s) {
         const int n = sim->counts[s];
         for (int k = 0; k * item < n; ++k) {
@@ -160,6 +163,31 @@ void plan_items(sic_sim *sim)
                 w.halo_shift = 0;
             }
             sim->items.push_back(w);
+            if (sim->order == 1) {
+                // the tracer before the first one and the one after the halo
+                const int64_t wind = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
+                const int64_t off = sim->sheet_off[s];
+                WorkItemPL p{-1, 0, -1, 0};
+                if (k > 0)
+                    p.prev = w.t0 - 1;
+                else if (sim->closed[s]) {
+                    p.prev = off + n - 1;
+                    p.prev_shift = -wind;
+                }
+                const int64_t after = (int64_t)k * item + w.count + 1;  // sheet index after the halo
+                if (!last) {
+                    if (after < n)
+                        p.next2 = off + after;
+                    else if (sim->closed[s]) {
+                        p.next2 = off;
+                        p.next2_shift = wind;
+                    }
+                } else if (sim->closed[s]) {
+                    p.next2 = off + 1;
+                    p.next2_shift = wind;
+                }
+                sim->pl_items.push_back(p);
+            }
         }
     }
 }
@@ -202,6 +230,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     sim->strict = cfg->strict_segments ? 1 : 0;
     sim->hist_len = cfg->history_len;
     sim->half_step_init = cfg->half_step_init ? 1 : 0;
+    sim->order = cfg->deposit_order;
     sim->sheet_off.assign(sim->M, 0);
     int64_t off = 0;
     for (int s = 0; s < sim->M; ++s) {
@@ -220,7 +249,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     const int n_items = (int)sim->items.size();
 
     const int nx = sim->nx;
-    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len);
+    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len, sim->order);
     const size_t oU0 = L.oU0, oU1 = L.oU1, oV0 = L.oV0, oV1 = L.oV1, oQ = L.oQ, oMesh = L.oMesh, oLast = L.oLast,
                  oEk = L.oEk, oE64 = L.oE64, oRho = L.oRho, oAcc = L.oAcc, oItems = L.oItems, oHist = L.oHist,
                  oSc = L.oSc;
@@ -244,6 +273,12 @@ int setup(sic_sim *sim, const sic_config *cfg)
     h.items = (const WorkItem *)(b + oItems);
     CK(cudaMemcpyAsync((void *)h.items, sim->items.data(), sizeof(WorkItem) * (size_t)n_items, cudaMemcpyHostToDevice,
                        sim->stream));
+    h.pl = nullptr;
+    if (sim->order == 1) {
+        h.pl = (const WorkItemPL *)(b + L.oPL);
+        CK(cudaMemcpyAsync((void *)h.pl, sim->pl_items.data(), sizeof(WorkItemPL) * (size_t)n_items,
+                           cudaMemcpyHostToDevice, sim->stream));
+    }
     h.hist = (double *)(b + oHist);
     h.sc = (SimScalars *)(b + oSc);
     h.n_items = n_items;
@@ -356,6 +391,9 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     p.args.claim_q = claim_q;
     p.args.n_slots = n;
     p.args.nx_max = nx_max;
+    p.args.pl = 0;
+    for (int slot = 0; slot < n; ++slot)
+        p.args.pl |= sims[slot]->order == 1 ? 1 : 0;
     p.grid = grid;
     p.per_q = per_q;
     p.pow2 = pow2;
@@ -372,7 +410,7 @@ cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int re
 }
 
 
-SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len)
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int order)
 {
     Layout lay;
     SimLayout L;
@@ -388,6 +426,7 @@ SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int h
     L.oRho = lay.take(8 * (size_t)nx);
     L.oAcc = lay.take(sizeof(SimAccum));
     L.oItems = lay.take(sizeof(WorkItem) * (size_t)n_items);
+    L.oPL = order == 1 ? lay.take(sizeof(WorkItemPL) * (size_t)n_items) : 0;
     L.oHist = lay.take(32 * (size_t)hist_len);
     L.oSc = lay.take(sizeof(SimScalars));
     L.total = lay.off;
@@ -1087,6 +1126,9 @@ cudaError_t static_plan(unsigned char *region, sic_sim *const *grp, int n, cudaS
     a.drift = 1;
     a.record = 1;
     a.kick_scale = 1.0f;
+    a.pl = 0;
+    for (int i = 0; i < n; ++i)
+        a.pl |= grp[i]->order == 1 ? 1 : 0;
     return cudaSuccess;
 }
 

@@ -69,6 +69,17 @@ struct WorkItem {
     int64_t halo_shift; // added to the halo position (winding * nx * 2^32)
 };
 
+// The two more tracers a piecewise-linear particle's gradient needs (Sec. 2.5):
+// the one before the item's first and the one after its halo; -1 when the
+// sheet has none there (open ends).  The shifts move a closed sheet's other
+// end by one winding (winding * nx * 2^32).
+struct WorkItemPL {
+    int64_t prev;
+    int64_t prev_shift;
+    int64_t next2;
+    int64_t next2_shift;
+};
+
 // Per-step sums every block adds into and the epilogue reads: the kinetic
 // energy and momentum terms as 128-bit fixed-point integers (2^-32 units,
 // each item's FP32 partial converted exactly), so the totals do not depend
@@ -102,6 +113,7 @@ struct SimDev {
     double *hist;               // [hist_len][4]
     SimScalars *sc;
     const WorkItem *items;      // [n_items] this simulation's work items
+    const WorkItemPL *pl;       // [n_items] for piecewise-linear particles, else null
     int32_t n_items;
     int32_t hist_len;
     NxDiv div;
@@ -133,6 +145,7 @@ struct LaunchArgs {
     int32_t drift;
     int32_t record;
     float kick_scale;
+    int32_t pl;                  // some simulation has piecewise-linear particles
 };
 
 #include <cuda_runtime.h>

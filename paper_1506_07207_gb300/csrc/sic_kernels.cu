@@ -246,6 +246,110 @@ __device__ __forceinline__ void emit_cross(long long ua, int ja, long long ub, i
     acc.add(jb, (long long)q - F - inner);
 }
 
+// Piecewise-linear particles (Sec. 2.5).  The particle from ua to ub (tracers
+// i, i+1) has neighbours from up (tracer i-1) and to un (tracer i+2) along
+// the sheet, all in 32.32 cell coordinates, with charges qp, qs, qn.  Its
+// density rho0 + g (x - c) gives, from its lower end, the cumulative charge
+// qs (t + kappa t (t - 1)) at the fraction t of its length, with
+// kappa = g l / (2 rho0) and g the central difference of Eq.
+// gradient_rho_estimate.  The centroids are in order along the sheet exactly
+// when up < ub and ua < un (or both reversed); otherwise (a fold corner), or
+// when a length or the charge is zero, kappa = 0: the box particle.
+__device__ __forceinline__ float pl_kappa(long long up, long long ua, long long ub, long long un, int qp, int qs,
+                                          int qn)
+{
+    const bool inc = up < ub && ua < un, dec = up > ub && ua > un;
+    const long long lp = ua > up ? ua - up : up - ua;
+    const long long ls = ub > ua ? ub - ua : ua - ub;
+    const long long ln = un > ub ? un - ub : ub - un;
+    if (!(inc || dec) || lp == 0 || ls == 0 || ln == 0 || qs == 0)
+        return 0.f;
+    const float fp = __ll2float_rn(lp), fs = __ll2float_rn(ls), fn = __ll2float_rn(ln);
+    const float rp = __fdiv_rn(__int2float_rn(qp), fp);
+    const float rs = __fdiv_rn(__int2float_rn(qs), fs);
+    const float rn = __fdiv_rn(__int2float_rn(qn), fn);
+    // twice the centroid distance c_{s+1} - c_{s-1}, signed
+    const float dc2 = __ll2float_rn((ub - up) + (un - ua));
+    const float k = __fdiv_rn(__fmul_rn(__fsub_rn(rn, rp), fs), __fmul_rn(rs, dc2));
+    return fabsf(k) < 1e30f ? k : 0.f;
+}
+
+// Deposit one piecewise-linear particle shorter than the box (at most nx
+// cells, so the loop is bounded) that crosses at least one cell edge:
+// the cell between the cuts k and k+1 gets round(q phi(t_{k+1})) -
+// round(q phi(t_k)), phi(t) = t + kappa t (t - 1), t_k the fraction of the
+// length at the k-th edge (phi(0) = 0, phi(1) = 1), so the pieces sum to q
+// exactly.  A piece may be negative when |kappa| > 1 (the linear density
+// changes sign inside the particle).
+template <class ACC>
+__device__ __forceinline__ void emit_cross_linear(long long ua, int ja, long long ub, int jb, int q, float kappa,
+                                                  int nx, ACC &acc, unsigned &maxseg)
+{
+    if (ub < ua) {
+        const long long t = ua;
+        ua = ub;
+        ub = t;
+        const int tj = ja;
+        ja = jb;
+        jb = tj;
+    }
+    const long long span = ub - ua;
+    maxseg = max(maxseg, (unsigned)min((unsigned long long)span >> 16, 0xffffffffull));
+    const float inv = __frcp_rn(__ll2float_rn(span));
+    const float fq = __int2float_rn(q);
+    const long long ncut = (long long)cell_of(ub) - (long long)cell_of(ua);
+    const long long lo = (long long)frac_of(ua);
+    long long prev = 0;
+    int j = ja;
+    for (long long k = 1; k <= ncut; ++k) {
+        const float t = __fmul_rn(__ll2float_rn((k << 32) - lo), inv);
+        const float phi = __fmaf_rn(__fmul_rn(kappa, t), __fsub_rn(t, 1.0f), t);
+        const long long c = __float2ll_rn(__fmul_rn(fq, phi));
+        acc.add(j, c - prev);
+        prev = c;
+        j = (j + 1 == nx) ? 0 : j + 1;
+    }
+    acc.add(jb, (long long)q - prev);
+}
+
+// The same pieces as emit_cross_linear, with the particle's cells shared out
+// over the 32 lanes of the warp (all lanes call it with the same particle).
+template <class ACC>
+__device__ __forceinline__ void emit_linear_warp(long long ua, int ja, long long ub, int jb, int q, float kappa,
+                                                 int nx, ACC &acc, unsigned &maxseg, int lane)
+{
+    if (ub < ua) {
+        const long long t = ua;
+        ua = ub;
+        ub = t;
+        const int tj = ja;
+        ja = jb;
+        jb = tj;
+    }
+    const long long span = ub - ua;
+    maxseg = max(maxseg, (unsigned)min((unsigned long long)span >> 16, 0xffffffffull));
+    const float inv = __frcp_rn(__ll2float_rn(span));
+    const float fq = __int2float_rn(q);
+    const long long ncut = (long long)cell_of(ub) - (long long)cell_of(ua);
+    const long long lo = (long long)frac_of(ua);
+    auto cum = [&](long long k) -> long long {  // round(q phi(t_k)) at the k-th edge
+        const float t = __fmul_rn(__ll2float_rn((k << 32) - lo), inv);
+        const float phi = __fmaf_rn(__fmul_rn(kappa, t), __fsub_rn(t, 1.0f), t);
+        return __float2ll_rn(__fmul_rn(fq, phi));
+    };
+    for (long long k0 = 0; k0 <= ncut; k0 += 32) {
+        const long long k = k0 + lane;  // cell ja + k, between the edges k and k + 1
+        if (k <= ncut) {
+            const long long c_lo = k == 0 ? 0 : cum(k);
+            const long long c_hi = k == ncut ? (long long)q : cum(k + 1);
+            int j = ja + (int)k;  // k <= ncut <= nx
+            if (j >= nx)
+                j -= nx;
+            acc.add(j, c_hi - c_lo);
+        }
+    }
+}
+
 // A 128-bit fixed-point sum (2^-32 units) held in registers; adding the
 // same FP32 values in any order gives the same bits.
 struct Acc128 {
@@ -415,6 +519,8 @@ struct Shared {
     unsigned long long mbar[NW][2];
     int diff_used;
     int last;
+    long long pl_prev[NW];   // piecewise-linear particles: each warp's tracer before its item
+    int pl_prevq[NW];
     int taken;               // items of the current simulation the block's warps took
     int pick_n[NW], pick_s[NW];  // per warp: most unclaimed items, in which slot
     unsigned long long ke[2], p[2], maxseg;
@@ -425,6 +531,7 @@ struct Shared {
 };
 
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
+constexpr int kWarpCuts = 8;  // piecewise-linear particles this many cells long use the whole warp
 
 // shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx]; staging starts on a
 // 128-byte boundary (bulk copies need 16)
@@ -625,13 +732,14 @@ __device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int 
 
 // One work item (up to 32 R tracers, R per lane) of the current simulation.
 // FULL: the item has all 32 R tracers, so no lane needs a bounds test.
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED, bool PL>
 __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
                                         const float *__restrict__ Vin, long long *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
                                         const float2 *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
-                                        char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg)
+                                        char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg,
+                                        const WorkItemPL *pw)
 {
     const long long *stU = reinterpret_cast<const long long *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
@@ -799,6 +907,42 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             hj = wrap_cell<POW2>(cell_of(hu), dv);
     }
 
+    // piecewise-linear particles (pw set): the tracer before the item and the
+    // one after its halo too, for the gradients of the item's first and last
+    // particles (Sec. 2.5)
+    long long pu = 0, nu2 = 0;
+    int pq = W.qh, nq2 = W.qh;
+    bool has_prev = false, has_next2 = false;
+    if (PL && DEPOSIT && pw != nullptr) {
+        const long long ip = pw->prev, in2 = pw->next2;
+        has_prev = ip >= 0;
+        has_next2 = in2 >= 0;
+        if (lane == 0 && has_prev) {
+            pu = Uin[ip];
+            if (PER_Q)
+                pq = Qh[ip];
+            if (PUSH) {
+                float pv = Vin[ip];
+                int pj;
+                unsigned ignore = 0;
+                push_one<POW2>(pu, pv, pj, ek, dv, ks, drift, ignore);
+            }
+            pu += pw->prev_shift;
+        }
+        if (lane == lane_last && has_next2) {
+            nu2 = Uin[in2];
+            if (PER_Q)
+                nq2 = Qh[in2];
+            if (PUSH) {
+                float nv = Vin[in2];
+                int nj;
+                unsigned ignore = 0;
+                push_one<POW2>(nu2, nv, nj, ek, dv, ks, drift, ignore);
+            }
+            nu2 += pw->next2_shift;
+        }
+    }
+
     if (DEPOSIT) {
         hu += W.halo_shift;  // closing segment: the sheet's first tracer one winding on
         // publish the new positions (and charges) of the item in shared
@@ -829,6 +973,15 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             pts[m] = hu;
             if (PER_Q)
                 qpts[m] = hq;
+        }
+        if (PL && lane == lane_last && has_next2) {
+            pts[m + 1] = nu2;
+            if (PER_Q)
+                qpts[m + 1] = nq2;
+        }
+        if (PL && lane == 0 && has_prev) {
+            sh.pl_prev[threadIdx.x >> 5] = pu;
+            sh.pl_prevq[threadIdx.x >> 5] = pq;
         }
         // the next tracer of each lane's last one comes from the lane above
         const long long nu = __shfl_down_sync(0xffffffffu, u[0], 1);
@@ -929,12 +1082,58 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             }
             __syncwarp();
             DirectAdd acc{hist};
+            // piecewise-linear particles: kappa of the particle at idx; 0 keeps
+            // it a box (no neighbour on one side, or a box length or longer)
+            auto kappa_of = [&](int idx, long long ua, long long ub, int qs) -> float {
+                const bool hp = idx > 0 || has_prev;
+                const bool hn = idx + 2 < m || (idx + 2 == m && W.halo >= 0) || (idx + 2 == m + 1 && has_next2);
+                const long long len = ub > ua ? ub - ua : ua - ub;
+                if (!(hp && hn && len < ((long long)nx << 32)))
+                    return 0.f;
+                const int w8 = threadIdx.x >> 5;
+                const long long up = idx > 0 ? pts[idx - 1] : sh.pl_prev[w8];
+                const long long un = pts[idx + 2];
+                const int qp = PER_Q ? (idx > 0 ? qpts[idx - 1] : sh.pl_prevq[w8]) + qpts[idx] : qs_sheet;
+                const int qn = PER_Q ? qpts[idx + 1] + qpts[idx + 2] : qs_sheet;
+                return pl_kappa(up, ua, ub, un, qp, qs, qn);
+            };
+            bool any_long = false;
             for (int k = lane; k < total; k += 32) {
                 const int idx = tasks[k];
                 const long long ua = pts[idx], ub = pts[idx + 1];
                 const int qs = PER_Q ? qpts[idx] + qpts[idx + 1] : qs_sheet;
-                emit_cross(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs, nx, acc,
-                           diff, &sh.diff_used, mseg);
+                const float kappa = (PL && pw != nullptr) ? kappa_of(idx, ua, ub, qs) : 0.f;
+                if (kappa == 0.f) {
+                    emit_cross(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs, nx,
+                               acc, diff, &sh.diff_used, mseg);
+                } else {
+                    const int cuts = cell_of(ua) > cell_of(ub) ? cell_of(ua) - cell_of(ub) : cell_of(ub) - cell_of(ua);
+                    if (cuts >= kWarpCuts) {
+                        tasks[k] = (unsigned short)(idx | 0x8000);  // for the whole warp, below
+                        any_long = true;
+                    } else {
+                        emit_cross_linear(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv),
+                                          qs, kappa, nx, acc, mseg);
+                    }
+                }
+            }
+            // long piecewise-linear particles: every lane takes some of the
+            // particle's cells (the pieces do not depend on who computes them)
+            if (PL && pw != nullptr && __any_sync(0xffffffffu, any_long)) {
+                __syncwarp();
+                for (int base = 0; base < total; base += 32) {
+                    const int k = base + lane;
+                    unsigned bal = __ballot_sync(0xffffffffu, k < total && (tasks[k] & 0x8000));
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1u;
+                        const int idx = tasks[base + src] & 0x7fff;
+                        const long long ua = pts[idx], ub = pts[idx + 1];
+                        const int qs = PER_Q ? qpts[idx] + qpts[idx + 1] : qs_sheet;
+                        emit_linear_warp(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs,
+                                         kappa_of(idx, ua, ub, qs), nx, acc, mseg, lane);
+                    }
+                }
             }
         }
         __syncwarp();  // pts and tasks are rewritten by the next item
@@ -953,7 +1152,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
     }
 }
 
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED, bool PL>
 __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1078,6 +1277,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     nxt = nn > 0 ? na : -1;
                 }
                 const WorkItem W = items[i];
+                const WorkItemPL *plw = (PL && S.pl != nullptr) ? S.pl + i : nullptr;
                 if (STAGED) {
                     if (nxt >= 0 && lane == 0)
                         stage_issue<PER_Q>(items[nxt], Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
@@ -1095,24 +1295,24 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     }
                     char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
                     if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                         sh, dv, ks, drift, rerr, st, tasks, ake, ap,
-                                                                        mseg);
+                                                                        mseg, plw);
                     else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                          diff, sh, dv, ks, drift, rerr, st, tasks,
-                                                                         ake, ap, mseg);
+                                                                         ake, ap, mseg, plw);
                     __syncwarp();
                     s ^= 1;
                 } else {
                     if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                          sh, dv, ks, drift, rerr, my_stage, tasks,
-                                                                         ake, ap, mseg);
+                                                                         ake, ap, mseg, plw);
                     else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                           diff, sh, dv, ks, drift, rerr, my_stage,
-                                                                          tasks, ake, ap, mseg);
+                                                                          tasks, ake, ap, mseg, plw);
                 }
             }
             if (!took)
@@ -1233,12 +1433,12 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     }
 }
 
-template <bool P, bool D, bool Q, bool T, bool G>
+template <bool P, bool D, bool Q, bool T, bool G, bool L>
 cudaError_t prep(size_t smem)
 {
     static size_t done = 0;
     if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, T, G, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess)
             return e;
@@ -1247,14 +1447,14 @@ cudaError_t prep(size_t smem)
     return cudaSuccess;
 }
 
-template <bool P, bool D, bool Q, bool T, bool G>
+template <bool P, bool D, bool Q, bool T, bool G, bool L>
 cudaError_t run(const LaunchArgs &a, int grid, cudaStream_t s)
 {
     const size_t smem = step_smem_bytes(a.nx_max, G, Q);
-    cudaError_t e = prep<P, D, Q, T, G>(smem);
+    cudaError_t e = prep<P, D, Q, T, G, L>(smem);
     if (e != cudaSuccess)
         return e;
-    k_step<P, D, Q, T, G><<<grid, B, smem, s>>>(a);
+    k_step<P, D, Q, T, G, L><<<grid, B, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1263,20 +1463,27 @@ template <bool P, bool D, bool Q, bool T, bool G>
 int occ(int nx_max)
 {
     const size_t smem = step_smem_bytes(nx_max, G, Q);
-    if (prep<P, D, Q, T, G>(smem) != cudaSuccess)
+    if (prep<P, D, Q, T, G, false>(smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, T, G>, B, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, T, G, false>, B, smem) != cudaSuccess)
         return 0;
     return n;
 }
 
+// a.pl: some simulation of the launch has piecewise-linear particles; that
+// variant handles both kinds
 template <bool P, bool D, bool G>
 cudaError_t run_pd(const LaunchArgs &a, int grid, bool per_q, bool pow2, cudaStream_t s)
 {
+    if (a.pl) {
+        if (per_q)
+            return pow2 ? run<P, D, true, true, G, true>(a, grid, s) : run<P, D, true, false, G, true>(a, grid, s);
+        return pow2 ? run<P, D, false, true, G, true>(a, grid, s) : run<P, D, false, false, G, true>(a, grid, s);
+    }
     if (per_q)
-        return pow2 ? run<P, D, true, true, G>(a, grid, s) : run<P, D, true, false, G>(a, grid, s);
-    return pow2 ? run<P, D, false, true, G>(a, grid, s) : run<P, D, false, false, G>(a, grid, s);
+        return pow2 ? run<P, D, true, true, G, false>(a, grid, s) : run<P, D, true, false, G, false>(a, grid, s);
+    return pow2 ? run<P, D, false, true, G, false>(a, grid, s) : run<P, D, false, false, G, false>(a, grid, s);
 }
 
 template <bool P, bool D, bool G>

@@ -50,6 +50,7 @@ class sic_config(ctypes.Structure):
         ("strict_segments", ctypes.c_int32),
         ("history_len", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("deposit_order", ctypes.c_int32),
     ]
 
 
@@ -180,7 +181,7 @@ def sic_launch_count() -> int:
 
 
 def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
-            half_step_init=True, strict=False, history_len=1, stream=None):
+            half_step_init=True, strict=False, history_len=1, stream=None, order=0):
     cfg = sic_config()
     cfg.nx = int(nx)
     cfg.box_length = float(L)
@@ -200,6 +201,7 @@ def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
     cfg.strict_segments = int(bool(strict))
     cfg.history_len = int(history_len)
     cfg.stream = ctypes.c_void_p(int(stream) if stream else 0)
+    cfg.deposit_order = int(order)
     return cfg, keep
 
 
@@ -215,10 +217,10 @@ class Sim:
     # -- construction -------------------------------------------------------
     @classmethod
     def sic_create(cls, nx, L, dt, counts, closed, winding, x, v, w, qm=1.0, half_step_init=True,
-                   strict=False, history_len=1, stream=None):
+                   strict=False, history_len=1, stream=None, order=0):
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         cfg, keep = _config(nx, L, dt, counts.size, counts, closed, winding, qm, half_step_init,
-                            strict, history_len, stream)
+                            strict, history_len, stream, order)
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -232,32 +234,33 @@ class Sim:
 
     @classmethod
     def sic_create_horizontal(cls, nx, L, dt, x_template, v_sheet, w_sheet, qm=1.0,
-                              half_step_init=True, strict=False, history_len=1, stream=None):
+                              half_step_init=True, strict=False, history_len=1, stream=None, order=0):
         xt = np.ascontiguousarray(x_template, dtype=np.float64)
         vs = np.ascontiguousarray(v_sheet, dtype=np.float64)
         ws = np.ascontiguousarray(w_sheet, dtype=np.float64)
         if vs.shape != ws.shape:
             raise ValueError("v_sheet and w_sheet need one entry per sheet")
         cfg, keep = _config(nx, L, dt, vs.size, None, None, None, qm, half_step_init, strict,
-                            history_len, stream)
+                            history_len, stream, order)
         h = ctypes.c_void_p()
         _check(_lib.sic_create_horizontal(ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs), _dptr(ws),
                                           ctypes.byref(h)), "sic_create_horizontal")
         return cls(h, nx, xt.size * vs.size, np.full(vs.size, xt.size))
 
     @classmethod
-    def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None):
-        """Create from an ``inputs.Problem`` (compact form when it has one)."""
+    def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None, order=0):
+        """Create from an ``inputs.Problem`` (compact form when it has one); order 1
+        selects the piecewise-linear particles of Sec. 2.5."""
         hl = history_len if history_len is not None else max(1, p.n_steps)
         if horizontal is None:
             horizontal = p.is_horizontal
         if horizontal:
             return cls.sic_create_horizontal(p.nx, p.L, p.dt, p.x_template, p.v_sheet, p.w_sheet,
                                              qm=p.qm, half_step_init=p.half_step_init, strict=strict,
-                                             history_len=hl, stream=stream)
+                                             history_len=hl, stream=stream, order=order)
         return cls.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
                               qm=p.qm, half_step_init=p.half_step_init, strict=strict,
-                              history_len=hl, stream=stream)
+                              history_len=hl, stream=stream, order=order)
 
     # -- the C ABI, one method per entry point ------------------------------
     @property

@@ -33,19 +33,19 @@ def sic():
     return binding
 
 
-def _oracle_fields(p, x):
-    charge = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, x, p.w)
+def _oracle_fields(p, x, order=0):
+    charge = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, x, p.w, order=order)
     n = charge / (p.L / p.nx)
     rho, E = oracle.field(p.nx, p.L, charge)
     return n, rho, E
 
 
-def _check_step_parity(sim, p, tol=TOL_STEP):
+def _check_step_parity(sim, p, tol=TOL_STEP, order=0):
     """A-14: deposit + field of the GPU's own state against the oracle."""
     mesh, rho = sim.sic_deposit()
     E = sim.sic_field()
     x, _ = sim.sic_get_state()
-    n_ref, rho_ref, E_ref = _oracle_fields(p, x)
+    n_ref, rho_ref, E_ref = _oracle_fields(p, x, order)
     gross = np.abs(n_ref).max()
     e_rho = np.abs(rho - rho_ref).max() / gross
     e_E = np.abs(E - E_ref).max() / (p.L * gross)
