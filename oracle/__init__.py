@@ -55,6 +55,12 @@ def _load():
             lib.orc_deposit.restype = ctypes.c_int
             lib.orc_deposit_linear.argtypes = lib.orc_deposit.argtypes
             lib.orc_deposit_linear.restype = ctypes.c_int
+            lib.orc_moments.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ip, bp, ip,
+                                        dp, dp, dp, ctypes.c_int, dp, dp]
+            lib.orc_moments.restype = ctypes.c_int
+            lib.orc_deposit_pic.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_long, dp, dp,
+                                            ctypes.c_int, dp]
+            lib.orc_deposit_pic.restype = ctypes.c_int
             lib.orc_field.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             lib.orc_field.restype = None
             lib.orc_gather.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_long,
@@ -92,13 +98,18 @@ def _sheets(counts, closed, winding):
 
 def deposit(nx, L, counts, closed, winding, x, w, order=0):
     """Charge per cell (Eq. overlap and Eq. rho_sum, times dx); order 1 uses
-    the piecewise-linear particles of Sec. 2.5."""
+    the piecewise-linear particles of Sec. 2.5, 2 and 3 the PIC point charges
+    of the tracers (nearest grid point, cloud in cell)."""
     lib = _load()
     counts, closed, winding = _sheets(counts, closed, winding)
     x, w = _f64(x), _f64(w)
     if x.shape != w.shape or x.size != int(counts.sum()):
         raise ValueError("x and w need one entry per tracer")
     out = np.zeros(int(nx), dtype=np.float64)
+    if order in (2, 3):
+        lib.orc_deposit_pic(int(nx), float(L), x.size, _ptr(x, ctypes.c_double), _ptr(w, ctypes.c_double),
+                            int(order), _ptr(out, ctypes.c_double))
+        return out
     fn = lib.orc_deposit_linear if order == 1 else lib.orc_deposit
     rc = fn(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
                          _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
@@ -112,6 +123,25 @@ def deposit(nx, L, counts, closed, winding, x, w, order=0):
 def density(nx, L, counts, closed, winding, x, w, order=0):
     """Cell-averaged number density n_j = charge_j / dx."""
     return deposit(nx, L, counts, closed, winding, x, w, order) / (float(L) / int(nx))
+
+
+def moments(nx, L, counts, closed, winding, x, v, w, weighting=0):
+    """(n, j): number and current density by zero-order (cells, Eq. rho_sum and
+    Eq. j_sum) or first-order (nodes, Sec. 2.4) weighting of the particles."""
+    lib = _load()
+    counts, closed, winding = _sheets(counts, closed, winding)
+    x, v, w = _f64(x), _f64(v), _f64(w)
+    if not (x.shape == v.shape == w.shape) or x.size != int(counts.sum()):
+        raise ValueError("x, v and w need one entry per tracer")
+    n = np.zeros(int(nx))
+    j = np.zeros(int(nx))
+    rc = lib.orc_moments(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
+                         _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
+                         _ptr(x, ctypes.c_double), _ptr(v, ctypes.c_double), _ptr(w, ctypes.c_double),
+                         int(weighting), _ptr(n, ctypes.c_double), _ptr(j, ctypes.c_double))
+    if rc:
+        raise ValueError("every sheet needs at least two tracers")
+    return n, j
 
 
 def field(nx, L, charge):

@@ -220,7 +220,36 @@ int orc_deposit_linear(int nx, double L, int n_sheets, const int32_t *counts,
     return 0;
 }
 
-/* The deposit of the given order: 0 box particles, 1 piecewise linear. */
+/*
+ * PIC deposits of the tracers themselves, for the comparison runs of Sec. 3
+ * (Sec. 2.4 gives the weightings): every tracer is a point charge w_i.
+ *   scheme 2, zero order (nearest grid point): the whole charge goes to the
+ *     cell holding the tracer (the cell whose centre is nearest);
+ *   scheme 3, first order (cloud in cell): the charge is shared between the
+ *     two cells whose centres (j + 1/2) dx bracket the tracer, linearly in
+ *     its distance to each centre.
+ */
+int orc_deposit_pic(int nx, double L, long n_tracers, const double *x,
+                    const double *w, int scheme, double *charge)
+{
+    double dx = L / nx;
+    memset(charge, 0, sizeof(double) * (size_t)nx);
+    for (long i = 0; i < n_tracers; ++i) {
+        if (scheme == 2) {
+            charge[wrap_cell((long)floor(x[i] / dx), nx)] += w[i];
+        } else {
+            double p = x[i] / dx - 0.5;
+            double m = floor(p);
+            double f = p - m;
+            charge[wrap_cell((long)m, nx)] += w[i] * (1.0 - f);
+            charge[wrap_cell((long)m + 1, nx)] += w[i] * f;
+        }
+    }
+    return 0;
+}
+
+/* The deposit of the given kind: 0 box particles (Sec. 2.3), 1 piecewise
+ * linear particles (Sec. 2.5), 2 and 3 PIC point charges (NGP, CIC). */
 static int deposit_order(int order, int nx, double L, int n_sheets,
                          const int32_t *counts, const uint8_t *closed,
                          const int32_t *winding, const double *x,
@@ -228,7 +257,110 @@ static int deposit_order(int order, int nx, double L, int n_sheets,
 {
     if (order == 1)
         return orc_deposit_linear(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+    if (order == 2 || order == 3) {
+        long n = 0;
+        for (int s = 0; s < n_sheets; ++s)
+            n += counts[s];
+        return orc_deposit_pic(nx, L, n, x, w, order, charge);
+    }
     return orc_deposit(nx, L, n_sheets, counts, closed, winding, x, w, charge);
+}
+
+/*
+ * Moments of the particles on the mesh: number density n and current density
+ * j, by zero-order or first-order weighting of the box particles (Sec. 2.3
+ * and Sec. 2.4).
+ *
+ * Particle s between tracers i and i+1 carries charge q_s = (w_i + w_{i+1})/2
+ * spread uniformly over its extent (density q_s / |x_{i+1} - x_i|).
+ *   weighting 0 (Eq. rho_sum, Eq. j_sum): cell j gets n_j = sum_s q_s o_js / dx
+ *     and j_j = sum_s q_s v~_s o_js / dx, o_js the overlap fraction of
+ *     Eq. overlap and v~_s = (m_i v_i + m_{i+1} v_{i+1}) / (m_i + m_{i+1}) the
+ *     particle velocity of Sec. 2.3 (masses m = w / qm, so the weights);
+ *   weighting 1 (Sec. 2.4): node X_j = j dx gets
+ *     n_j = sum_s (1/dx) int q_s b_s(x) W1(x - X_j) dx,
+ *     j_j = sum_s (1/dx) int q_s v_s(x) b_s(x) W1(x - X_j) dx,
+ *     W1 the hat of half-width dx and v_s(x) the velocity interpolated
+ *     linearly along the particle from v_i at x_i to v_{i+1} at x_{i+1}.
+ * A zero-length particle is a point charge (first order: the hat weights of
+ * its point; velocity v~_s).  Every periodic image counts.  n and j each
+ * have nx entries.
+ */
+static void moments_segment(double xa, double va, double xb, double vb, double q,
+                            double vbar, int weighting, int nx, double dx,
+                            double *n, double *j)
+{
+    double a = xa < xb ? xa : xb;
+    double b = xa < xb ? xb : xa;
+    long ma = (long)floor(a / dx);
+    long mb = (long)floor(b / dx);
+    if (b == a) {
+        if (weighting == 0) {
+            int c = wrap_cell(ma, nx);
+            n[c] += q / dx;
+            j[c] += q * vbar / dx;
+        } else {
+            double f = a / dx - (double)ma;
+            int c0 = wrap_cell(ma, nx), c1 = wrap_cell(ma + 1, nx);
+            n[c0] += q * (1.0 - f) / dx;
+            n[c1] += q * f / dx;
+            j[c0] += q * vbar * (1.0 - f) / dx;
+            j[c1] += q * vbar * f / dx;
+        }
+        return;
+    }
+    double len = xb - xa;            /* signed: the velocity runs from xa to xb */
+    double rho0 = q / fabs(len);
+    for (long m = ma - 1; m <= mb + 1; ++m) {
+        double lo = a > m * dx ? a : m * dx;
+        double hi = b < (m + 1) * dx ? b : (m + 1) * dx;
+        if (!(hi > lo))
+            continue;
+        int c0 = wrap_cell(m, nx), c1 = wrap_cell(m + 1, nx);
+        if (weighting == 0) {
+            n[c0] += rho0 * (hi - lo) / dx;
+            j[c0] += rho0 * vbar * (hi - lo) / dx;
+            continue;
+        }
+        /* s = (x - X_m) / dx in [0, 1): node m weighs 1 - s, node m+1 weighs s */
+        double s0 = lo / dx - (double)m, s1 = hi / dx - (double)m;
+        double I0 = (s1 - s0) * dx;                       /* int 1 dx         */
+        double I1 = 0.5 * (s1 * s1 - s0 * s0) * dx;       /* int s dx         */
+        double I2 = (s1 * s1 * s1 - s0 * s0 * s0) / 3.0 * dx; /* int s^2 dx  */
+        /* v(x) = va + (vb - va) (x - xa) / len = p + r s on this cell */
+        double r = (vb - va) * dx / len;
+        double p = va + (vb - va) * ((double)m * dx - xa) / len;
+        n[c0] += rho0 * (I0 - I1) / dx;
+        n[c1] += rho0 * I1 / dx;
+        j[c0] += rho0 * (p * (I0 - I1) + r * (I1 - I2)) / dx;
+        j[c1] += rho0 * (p * I1 + r * I2) / dx;
+    }
+}
+
+int orc_moments(int nx, double L, int n_sheets, const int32_t *counts,
+                const uint8_t *closed, const int32_t *winding, const double *x,
+                const double *v, const double *w, int weighting, double *n,
+                double *j)
+{
+    double dx = L / nx;
+    memset(n, 0, sizeof(double) * (size_t)nx);
+    memset(j, 0, sizeof(double) * (size_t)nx);
+    long base = 0;
+    for (int s = 0; s < n_sheets; ++s) {
+        long cnt = counts[s];
+        if (cnt < 2)
+            return -1;
+        long np = closed[s] ? cnt : cnt - 1;
+        for (long k = 0; k < np; ++k) {
+            long i = base + k, i1 = k + 1 < cnt ? base + k + 1 : base;
+            double xb = x[i1] + (k + 1 < cnt ? 0.0 : (double)winding[s] * L);
+            double q = 0.5 * (w[i] + w[i1]);
+            double vbar = (w[i] * v[i] + w[i1] * v[i1]) / (w[i] + w[i1]);
+            moments_segment(x[i], v[i], xb, v[i1], q, vbar, weighting, nx, dx, n, j);
+        }
+        base += cnt;
+    }
+    return 0;
 }
 
 /*
@@ -314,7 +446,7 @@ double orc_field_energy(int nx, double L, const double *E)
  * e_hist (n_steps+1 rows of nx, may be NULL) gets every E^n.
  * On exit x = x^{n_steps}, v = v^{n_steps-1/2}, E_out = E^{n_steps} (may be NULL).
  * order selects the deposit: 0 box particles (Sec. 2.3), 1 piecewise linear
- * (Sec. 2.5).
+ * (Sec. 2.5), 2 PIC nearest grid point, 3 PIC cloud in cell (Sec. 2.4).
  */
 int orc_run(int nx, double L, double dt, double qm, int half_step_init,
             int n_sheets, const int32_t *counts, const uint8_t *closed,

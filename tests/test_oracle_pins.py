@@ -398,3 +398,86 @@ def test_linear_particles_run_keeps_charge_and_oscillates():
     tm, _ = fits.local_maxima(t, W)
     period = 2 * np.mean(np.diff(tm))       # W_E peaks twice per period
     assert abs(2 * np.pi / period / theory.leapfrog_omega(p.dt) - 1) < 2e-3
+
+
+# --------------------------------------------------- moments (n and j) ----
+# Sec. 2.3 (Eq. rho_sum, Eq. j_sum: zero order on cells) and Sec. 2.4 (first
+# order: hats on the nodes, velocity linear along each particle).
+
+def test_zero_order_moments_agree_with_the_deposit():
+    rng = np.random.default_rng(7)
+    nx, L = 12, 2.0
+    counts, closed, winding = [40, 17, 9], [1, 0, 1], [1, 0, -1]
+    x = _dyadic(rng, 66, L)
+    w = rng.integers(1, 9, size=66) / 8.0
+    u = 0.375
+    n, j = oracle.moments(nx, L, counts, closed, winding, x, np.full(66, u), w, weighting=0)
+    np.testing.assert_allclose(n, oracle.deposit(nx, L, counts, closed, winding, x, w) / (L / nx), rtol=1e-13)
+    np.testing.assert_allclose(j, u * n, rtol=1e-13, atol=1e-15)
+
+
+def test_first_order_moments_of_a_cosine_density():
+    """CIC weighting of a density 1 + A cos(kx) on the nodes is
+    1 + A cos(k X_j) sinc^2(k dx / 2) (the hat's Fourier transform); the
+    weights form a partition of unity, so the total is kept."""
+    from scipy.optimize import brentq
+    L, nx, A, N = 1.0, 16, 0.4, 4000
+    k = 2 * np.pi / L
+    dx = L / nx
+
+    def cdf(x):
+        return x + A / k * np.sin(k * x)
+
+    xs = np.array([brentq(lambda t: cdf(t) - L * i / N, -1e-9, L + 1e-9) for i in range(N)])
+    w = np.full(N, L / N)
+    n, _ = oracle.moments(nx, L, [N], [1], [1], xs, np.zeros(N), w, weighting=1)
+    X = np.arange(nx) * dx
+    want = 1 + A * np.cos(k * X) * np.sinc(k * dx / 2 / np.pi) ** 2
+    np.testing.assert_allclose(n, want, atol=2e-6)
+    assert math.isclose(n.sum() * dx, w.sum(), rel_tol=1e-13)
+
+
+def test_first_order_current_of_a_linear_velocity_field():
+    """A uniform open sheet with v = c x: the velocity interpolated along each
+    particle is exactly c x, and the hat average of c x about a node is c X_j,
+    so every node whose hat lies inside the sheet gets j = n c X_j."""
+    nx, L, c = 20, 5.0, 0.7
+    dx = L / nx
+    x = np.linspace(0.8, 4.2, 341)
+    w = np.full(x.size, 0.01)
+    n, j = oracle.moments(nx, L, [x.size], [0], [0], x, c * x, w, weighting=1)
+    X = np.arange(nx) * dx
+    inside = (X - dx >= x[0]) & (X + dx <= x[-1])
+    assert inside.sum() >= 10
+    dens = 0.01 / (x[1] - x[0])
+    np.testing.assert_allclose(n[inside], dens, rtol=1e-12)
+    np.testing.assert_allclose(j[inside], dens * c * X[inside], rtol=1e-12)
+
+
+# ------------------------------------------------- PIC comparison deposits ----
+
+def test_pic_deposits_by_hand():
+    """Point charges: nearest grid point puts a tracer in its own cell; cloud
+    in cell shares it between the two cells whose centres bracket it."""
+    nx, L = 8, 4.0                                   # dx = 0.5, centres 0.25, 0.75, ...
+    x = np.array([0.25, 0.5, 0.6, 3.99, -0.1])
+    w = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
+    ngp = oracle.deposit(nx, L, [5], [0], [0], x, w, order=2)
+    np.testing.assert_array_equal(ngp, [1.0, 6.0, 0, 0, 0, 0, 0, 24.0])
+    cic = oracle.deposit(nx, L, [5], [0], [0], x, w, order=3)
+    want = np.zeros(nx)
+    want[0] += 1.0                                   # on a centre: all of it
+    want[0] += 1.0; want[1] += 1.0                   # on an edge: half each
+    want[0] += 4.0 * 0.3; want[1] += 4.0 * 0.7       # 0.6 is 0.35 dx past centre 0
+    want[7] += 8.0 * (1 - 0.48); want[0] += 8.0 * 0.48   # past the last centre: wraps
+    want[7] += 16.0 * 0.7; want[0] += 16.0 * 0.3     # -0.1: 0.3 dx from centre -1 (= 7)
+    np.testing.assert_allclose(cic, want, rtol=1e-14, atol=1e-14)
+    assert math.isclose(cic.sum(), w.sum(), rel_tol=1e-15)
+
+
+def test_pic_cloud_in_cell_of_a_uniform_lattice_is_uniform():
+    nx, L, per = 16, 2.0, 5
+    x = (np.arange(nx * per) + 0.37) * (L / (nx * per))
+    w = np.full(x.size, 0.125)
+    cic = oracle.deposit(nx, L, [x.size], [1], [1], x, w, order=3)
+    np.testing.assert_allclose(cic, cic.mean(), rtol=1e-13)
