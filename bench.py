@@ -238,8 +238,8 @@ def main():
     ap.add_argument("--impl", default="sic", choices=["sic", "reference"])
     ap.add_argument("--workload", default="serving", choices=["serving", "two_stream"],
                     help="serving: the request-mix sample; two_stream: the 8.4M-segment two-stream run alone")
-    ap.add_argument("--order", type=int, default=0, choices=[0, 1],
-                    help="deposit order: 0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5)")
+    ap.add_argument("--deposit", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
     ap.add_argument("--no-serving", action="store_true")
@@ -286,7 +286,7 @@ def main():
     if not serving_mode:
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         flush.fill_(1.0)
-    sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream, order=args.order) for p in probs]
+    sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream, order=args.deposit) for p in probs]
     batch = Batch(sims)
     S = batch.sic_batch_segments()
     for _ in range(args.warmup):
@@ -336,7 +336,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 push/deposit, i64 fixed-point charge, exact integer field solve",
-        "data": "synthetic", "config": dict(config, deposit_order=args.order),
+        "data": "synthetic", "config": dict(config, deposit=args.deposit),
     }
     peak, peak_src = peaks()
     avg_s = statistics.mean(step_ms) / 1e3

@@ -61,6 +61,20 @@ extern "C" {
 
 typedef struct sic_sim sic_sim;
 
+/* Charge deposits (sic_config.deposit). */
+#define SIC_DEPOSIT_BOX 0     /* box particles: uniform density between two adjacent
+                                 tracers (Sec. 2.3, Eq. overlap, Eq. rho_sum) */
+#define SIC_DEPOSIT_LINEAR 1  /* piecewise-linear particles: density linear about the
+                                 centroid with the central-difference gradient of
+                                 Sec. 2.5 (Eq. gradient_rho_estimate), none at a fold
+                                 corner, at an open end or for a particle a box
+                                 length or longer */
+#define SIC_DEPOSIT_PIC_NGP 2 /* PIC comparison: every tracer a point charge w_i in
+                                 its cell (nearest grid point, Sec. 2.4) */
+#define SIC_DEPOSIT_PIC_CIC 3 /* PIC comparison: every tracer a point charge shared
+                                 between the two cells whose centres bracket it
+                                 (cloud in cell, Sec. 2.4) */
+
 /*
  * Problem statement (Sec. 2.2-2.3): M sheets of ordered tracers on a periodic
  * box [0, box_length) split into nx cells, stepped with time step dt.
@@ -85,12 +99,8 @@ typedef struct {
                                           every periodic image counting */
     int32_t history_len;               /* rows of the per-step diagnostic ring, >= 1 */
     void *stream;                      /* cudaStream_t the simulation runs on, NULL = its own */
-    int32_t deposit_order;             /* 0: box particles, uniform density between two
-                                          tracers (Sec. 2.3); 1: piecewise-linear particles,
-                                          density linear about the centroid with the
-                                          central-difference gradient of Sec. 2.5
-                                          (Eq. gradient_rho_estimate), none at a fold corner
-                                          or an open end; other values SIC_EINVAL */
+    int32_t deposit;                   /* SIC_DEPOSIT_*: what carries the charge onto the mesh;
+                                          other values SIC_EINVAL */
 } sic_config;
 
 /* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum
@@ -137,6 +147,24 @@ int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host);
 
 /* The node field E_j (host, nx entries) of the latest deposit. */
 int sic_field(sic_sim *sim, double *E_host);
+
+/*
+ * Moments of the current state: number density n (charge per length) and
+ * current density j = n v of the box particles, into host arrays of nx
+ * doubles (either may be NULL).
+ *   weighting 0: zero order onto the cells [j dx, (j+1) dx) (Sec. 2.3,
+ *     Eq. rho_sum and Eq. j_sum); a particle moves with the mass-weighted
+ *     mean velocity of its two tracers;
+ *   weighting 1: first order onto the nodes x_j = j dx (Sec. 2.4): each slice
+ *     of a particle weighted by the hat of half-width dx about the node, its
+ *     velocity interpolated linearly between the tracers' velocities.
+ * The velocities are the stored ones (v^{n-1/2} after a step), the charges
+ * the fixed-point ones of the deposit.  Diagnostic only: FP64 with atomics,
+ * equal to the FP64 definition within rounding but not bit-reproducible; a
+ * particle longer than 64 box lengths is left out (the paper stops a run at
+ * one box length, Sec. 3.2).  Other weightings: SIC_EINVAL.
+ */
+int sic_moments(sic_sim *sim, int32_t weighting, double *n_host, double *j_host);
 
 /* Gather, kick and drift every tracer with the current field; no deposit. */
 int sic_push(sic_sim *sim);

@@ -118,7 +118,7 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (c->history_len < 1)
         return SIC_EINVAL;
-    if (c->deposit_order != 0 && c->deposit_order != 1)
+    if (c->deposit < SIC_DEPOSIT_BOX || c->deposit > SIC_DEPOSIT_PIC_CIC)
         return SIC_EINVAL;
     if (need_sheets) {
         if (!c->tracers_per_sheet || !c->sheet_closed)
@@ -163,7 +163,7 @@ void plan_items(sic_sim *sim)
                 w.halo_shift = 0;
             }
             sim->items.push_back(w);
-            if (sim->order == 1) {
+            if (sim->deposit == SIC_DEPOSIT_LINEAR) {
                 // the tracer before the first one and the one after the halo
                 const int64_t wind = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
                 const int64_t off = sim->sheet_off[s];
@@ -230,7 +230,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     sim->strict = cfg->strict_segments ? 1 : 0;
     sim->hist_len = cfg->history_len;
     sim->half_step_init = cfg->half_step_init ? 1 : 0;
-    sim->order = cfg->deposit_order;
+    sim->deposit = cfg->deposit;
     sim->sheet_off.assign(sim->M, 0);
     int64_t off = 0;
     for (int s = 0; s < sim->M; ++s) {
@@ -249,7 +249,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     const int n_items = (int)sim->items.size();
 
     const int nx = sim->nx;
-    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len, sim->order);
+    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len, sim->deposit);
     const size_t oU0 = L.oU0, oU1 = L.oU1, oV0 = L.oV0, oV1 = L.oV1, oQ = L.oQ, oMesh = L.oMesh, oLast = L.oLast,
                  oEk = L.oEk, oE64 = L.oE64, oRho = L.oRho, oAcc = L.oAcc, oItems = L.oItems, oHist = L.oHist,
                  oSc = L.oSc;
@@ -274,7 +274,8 @@ int setup(sic_sim *sim, const sic_config *cfg)
     CK(cudaMemcpyAsync((void *)h.items, sim->items.data(), sizeof(WorkItem) * (size_t)n_items, cudaMemcpyHostToDevice,
                        sim->stream));
     h.pl = nullptr;
-    if (sim->order == 1) {
+    h.deposit = sim->deposit;
+    if (sim->deposit == SIC_DEPOSIT_LINEAR) {
         h.pl = (const WorkItemPL *)(b + L.oPL);
         CK(cudaMemcpyAsync((void *)h.pl, sim->pl_items.data(), sizeof(WorkItemPL) * (size_t)n_items,
                            cudaMemcpyHostToDevice, sim->stream));
@@ -391,9 +392,9 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     p.args.claim_q = claim_q;
     p.args.n_slots = n;
     p.args.nx_max = nx_max;
-    p.args.pl = 0;
+    p.args.gen = 0;
     for (int slot = 0; slot < n; ++slot)
-        p.args.pl |= sims[slot]->order == 1 ? 1 : 0;
+        p.args.gen |= sims[slot]->deposit != SIC_DEPOSIT_BOX ? 1 : 0;
     p.grid = grid;
     p.per_q = per_q;
     p.pow2 = pow2;
@@ -410,7 +411,7 @@ cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int re
 }
 
 
-SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int order)
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int deposit)
 {
     Layout lay;
     SimLayout L;
@@ -426,7 +427,7 @@ SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int h
     L.oRho = lay.take(8 * (size_t)nx);
     L.oAcc = lay.take(sizeof(SimAccum));
     L.oItems = lay.take(sizeof(WorkItem) * (size_t)n_items);
-    L.oPL = order == 1 ? lay.take(sizeof(WorkItemPL) * (size_t)n_items) : 0;
+    L.oPL = deposit == SIC_DEPOSIT_LINEAR ? lay.take(sizeof(WorkItemPL) * (size_t)n_items) : 0;
     L.oHist = lay.take(32 * (size_t)hist_len);
     L.oSc = lay.take(sizeof(SimScalars));
     L.total = lay.off;
@@ -654,6 +655,21 @@ int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host)
                            sim->stream));
     if (rho_host)
         CK(cudaMemcpyAsync(rho_host, sim->h.rho64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
+    return check_device_errors(sim);
+}
+
+int sic_moments(sic_sim *sim, int32_t weighting, double *n_host, double *j_host)
+{
+    if (!sim || (weighting != 0 && weighting != 1))
+        return SIC_EINVAL;
+    // E64 and rho64 serve as the device buffers: sic_field and sic_deposit
+    // rewrite them before reading them
+    CK(launch_moments(sim->h, weighting, sim->dx, 1.0 / sim->sigma, sim->dx / sim->dt, sim->h.rho64, sim->h.E64,
+                      sim->stream));
+    if (n_host)
+        CK(cudaMemcpyAsync(n_host, sim->h.rho64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
+    if (j_host)
+        CK(cudaMemcpyAsync(j_host, sim->h.E64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
     return check_device_errors(sim);
 }
 
@@ -1126,9 +1142,9 @@ cudaError_t static_plan(unsigned char *region, sic_sim *const *grp, int n, cudaS
     a.drift = 1;
     a.record = 1;
     a.kick_scale = 1.0f;
-    a.pl = 0;
+    a.gen = 0;
     for (int i = 0; i < n; ++i)
-        a.pl |= grp[i]->order == 1 ? 1 : 0;
+        a.gen |= grp[i]->deposit != SIC_DEPOSIT_BOX ? 1 : 0;
     return cudaSuccess;
 }
 

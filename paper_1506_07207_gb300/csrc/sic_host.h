@@ -25,7 +25,7 @@ struct Plan {
 struct SimLayout {
     size_t oU0, oU1, oV0, oV1, oQ, oMesh, oLast, oEk, oE64, oRho, oAcc, oItems, oPL, oHist, oSc, total;
 };
-SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int order);
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int deposit);
 
 // Tracer slots (sheets padded to SIC_ALIGN_TRACERS) and work items of M
 // sheets of n tracers each.
@@ -48,7 +48,7 @@ struct sic_sim {
     int64_t n_tracers = 0, n_alloc = 0;
     double sigma = 1.0;
     std::vector<WorkItem> items;
-    int order = 0;                    // deposit order: 0 box, 1 piecewise linear
+    int deposit = SIC_DEPOSIT_BOX;    // SIC_DEPOSIT_*
     std::vector<WorkItemPL> pl_items;
     cudaStream_t stream = nullptr;
     bool own_stream = false;

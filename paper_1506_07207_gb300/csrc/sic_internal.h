@@ -114,6 +114,7 @@ struct SimDev {
     SimScalars *sc;
     const WorkItem *items;      // [n_items] this simulation's work items
     const WorkItemPL *pl;       // [n_items] for piecewise-linear particles, else null
+    int32_t deposit;            // SIC_DEPOSIT_*
     int32_t n_items;
     int32_t hist_len;
     NxDiv div;
@@ -145,7 +146,7 @@ struct LaunchArgs {
     int32_t drift;
     int32_t record;
     float kick_scale;
-    int32_t pl;                  // some simulation has piecewise-linear particles
+    int32_t gen;                 // some simulation deposits other than box particles
 };
 
 #include <cuda_runtime.h>
@@ -153,6 +154,8 @@ namespace sic {
 enum Mode { MODE_STEP = 0, MODE_DEPOSIT = 1, MODE_PUSH = 2 };
 cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s);
 cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s);
+cudaError_t launch_moments(const SimDev &sim, int weighting, double dx, double unit_q, double unit_v, double *n,
+                           double *j, cudaStream_t s);
 cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,
                                      const float *v_sheet, const int64_t *sheet_offset, int32_t n_sheets,
                                      cudaStream_t s);

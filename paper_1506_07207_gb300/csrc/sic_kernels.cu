@@ -732,14 +732,14 @@ __device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int 
 
 // One work item (up to 32 R tracers, R per lane) of the current simulation.
 // FULL: the item has all 32 R tracers, so no lane needs a bounds test.
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED, bool PL>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED, bool GEN>
 __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
                                         const float *__restrict__ Vin, long long *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
                                         const float2 *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg,
-                                        const WorkItemPL *pw)
+                                        const WorkItemPL *pw, int dep)
 {
     const long long *stU = reinterpret_cast<const long long *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
@@ -913,7 +913,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
     long long pu = 0, nu2 = 0;
     int pq = W.qh, nq2 = W.qh;
     bool has_prev = false, has_next2 = false;
-    if (PL && DEPOSIT && pw != nullptr) {
+    if (GEN && DEPOSIT && pw != nullptr) {
         const long long ip = pw->prev, in2 = pw->next2;
         has_prev = ip >= 0;
         has_next2 = in2 >= 0;
@@ -943,7 +943,32 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         }
     }
 
-    if (DEPOSIT) {
+    if (GEN && DEPOSIT && dep >= SIC_DEPOSIT_PIC_NGP) {
+        // PIC comparison deposits (Sec. 2.4): every tracer a point charge of
+        // 2 Qh units, in its cell (nearest grid point) or shared between the
+        // two cells whose centres bracket it (cloud in cell: the second gets
+        // round(Q f), f the distance past the first centre in cells)
+        DirectAdd acc{hist};
+        RunAcc run(hist);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (FULL || r < rn) {
+                const long long Qt = 2ll * (long long)q[r];
+                if (dep == SIC_DEPOSIT_PIC_NGP) {
+                    run.add(jn[r], Qt);
+                } else {
+                    const long long pc = u[r] - (1ll << 31);  // half a cell back: centres on integers
+                    const int j0 = wrap_cell<POW2>(cell_of(pc), dv);
+                    const int j1 = (j0 + 1 == nx) ? 0 : j0 + 1;
+                    const long long p1 =
+                        (long long)(((unsigned long long)Qt * (unsigned long long)frac_of(pc) + (1ull << 31)) >> 32);
+                    acc.add(j0, Qt - p1);
+                    acc.add(j1, p1);
+                }
+            }
+        }
+        run.flush();
+    } else if (DEPOSIT) {
         hu += W.halo_shift;  // closing segment: the sheet's first tracer one winding on
         // publish the new positions (and charges) of the item in shared
         // memory, so the cross-cell segments can be shared out over the warp
@@ -974,12 +999,12 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             if (PER_Q)
                 qpts[m] = hq;
         }
-        if (PL && lane == lane_last && has_next2) {
+        if (GEN && lane == lane_last && has_next2) {
             pts[m + 1] = nu2;
             if (PER_Q)
                 qpts[m + 1] = nq2;
         }
-        if (PL && lane == 0 && has_prev) {
+        if (GEN && lane == 0 && has_prev) {
             sh.pl_prev[threadIdx.x >> 5] = pu;
             sh.pl_prevq[threadIdx.x >> 5] = pq;
         }
@@ -1102,7 +1127,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 const int idx = tasks[k];
                 const long long ua = pts[idx], ub = pts[idx + 1];
                 const int qs = PER_Q ? qpts[idx] + qpts[idx + 1] : qs_sheet;
-                const float kappa = (PL && pw != nullptr) ? kappa_of(idx, ua, ub, qs) : 0.f;
+                const float kappa = (GEN && pw != nullptr) ? kappa_of(idx, ua, ub, qs) : 0.f;
                 if (kappa == 0.f) {
                     emit_cross(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs, nx,
                                acc, diff, &sh.diff_used, mseg);
@@ -1119,7 +1144,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             }
             // long piecewise-linear particles: every lane takes some of the
             // particle's cells (the pieces do not depend on who computes them)
-            if (PL && pw != nullptr && __any_sync(0xffffffffu, any_long)) {
+            if (GEN && pw != nullptr && __any_sync(0xffffffffu, any_long)) {
                 __syncwarp();
                 for (int base = 0; base < total; base += 32) {
                     const int k = base + lane;
@@ -1152,7 +1177,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
     }
 }
 
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED, bool PL>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED, bool GEN>
 __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1277,7 +1302,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     nxt = nn > 0 ? na : -1;
                 }
                 const WorkItem W = items[i];
-                const WorkItemPL *plw = (PL && S.pl != nullptr) ? S.pl + i : nullptr;
+                const WorkItemPL *plw = (GEN && S.pl != nullptr) ? S.pl + i : nullptr;
                 if (STAGED) {
                     if (nxt >= 0 && lane == 0)
                         stage_issue<PER_Q>(items[nxt], Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
@@ -1295,24 +1320,24 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     }
                     char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
                     if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                         sh, dv, ks, drift, rerr, st, tasks, ake, ap,
-                                                                        mseg, plw);
+                                                                        mseg, plw, S.deposit);
                     else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                          diff, sh, dv, ks, drift, rerr, st, tasks,
-                                                                         ake, ap, mseg, plw);
+                                                                         ake, ap, mseg, plw, S.deposit);
                     __syncwarp();
                     s ^= 1;
                 } else {
                     if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                          sh, dv, ks, drift, rerr, my_stage, tasks,
-                                                                         ake, ap, mseg, plw);
+                                                                         ake, ap, mseg, plw, S.deposit);
                     else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false, PL>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
+                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                           diff, sh, dv, ks, drift, rerr, my_stage,
-                                                                          tasks, ake, ap, mseg, plw);
+                                                                          tasks, ake, ap, mseg, plw, S.deposit);
                 }
             }
             if (!took)
@@ -1471,12 +1496,12 @@ int occ(int nx_max)
     return n;
 }
 
-// a.pl: some simulation of the launch has piecewise-linear particles; that
-// variant handles both kinds
+// a.gen: some simulation of the launch deposits other than box particles;
+// that variant handles every kind
 template <bool P, bool D, bool G>
 cudaError_t run_pd(const LaunchArgs &a, int grid, bool per_q, bool pow2, cudaStream_t s)
 {
-    if (a.pl) {
+    if (a.gen) {
         if (per_q)
             return pow2 ? run<P, D, true, true, G, true>(a, grid, s) : run<P, D, true, false, G, true>(a, grid, s);
         return pow2 ? run<P, D, false, true, G, true>(a, grid, s) : run<P, D, false, false, G, true>(a, grid, s);
@@ -1643,6 +1668,111 @@ cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_temp
                                      cudaStream_t s)
 {
     k_expand_horizontal<<<1216, 256, 0, s>>>(U, V, u_template, n_template, v_sheet, sheet_offset, n_sheets);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace sic
+
+namespace sic {
+namespace {
+
+// ------------------------------------------------------------ moments ----
+// Number density n and current density j of the box particles of the
+// current state (Sec. 2.3, Eq. rho_sum and Eq. j_sum: zero order on cells;
+// Sec. 2.4: first order on the nodes x_j = j dx, the velocity interpolated
+// linearly along each particle).  One thread per work item, FP64, atomics
+// into n and j (physical units: n = charge / length, j = n v).
+__device__ void moments_one(double xa, double va, double xb, double vb, double q, double vbar, int weighting, int nx,
+                            double dx, double *n, double *j)
+{
+    const double a = fmin(xa, xb), b = fmax(xa, xb);
+    const long long ma = (long long)floor(a / dx), mb = (long long)floor(b / dx);
+    auto cell = [&](long long m) {
+        const long long r = m % nx;
+        return (int)(r < 0 ? r + nx : r);
+    };
+    if (b == a) {
+        if (weighting == 0) {
+            atomicAdd(n + cell(ma), q / dx);
+            atomicAdd(j + cell(ma), q * vbar / dx);
+        } else {
+            const double f = a / dx - (double)ma;
+            atomicAdd(n + cell(ma), q * (1.0 - f) / dx);
+            atomicAdd(n + cell(ma + 1), q * f / dx);
+            atomicAdd(j + cell(ma), q * vbar * (1.0 - f) / dx);
+            atomicAdd(j + cell(ma + 1), q * vbar * f / dx);
+        }
+        return;
+    }
+    const double len = xb - xa;
+    const double dens = q / fabs(len);
+    if (mb - ma > 64ll * nx)
+        return;  // longer than 64 box lengths: left out (bounded work per thread)
+    for (long long m = ma; m <= mb; ++m) {
+        const double lo = fmax(a, (double)m * dx), hi = fmin(b, (double)(m + 1) * dx);
+        if (!(hi > lo))
+            continue;
+        const int c0 = cell(m), c1 = cell(m + 1);
+        if (weighting == 0) {
+            atomicAdd(n + c0, dens * (hi - lo) / dx);
+            atomicAdd(j + c0, dens * vbar * (hi - lo) / dx);
+            continue;
+        }
+        // s = (x - m dx) / dx: node m weighs 1 - s, node m + 1 weighs s; the
+        // velocity on the piece is p + r s
+        const double s0 = lo / dx - (double)m, s1 = hi / dx - (double)m;
+        const double i0 = (s1 - s0) * dx;
+        const double i1 = 0.5 * (s1 * s1 - s0 * s0) * dx;
+        const double i2 = (s1 * s1 * s1 - s0 * s0 * s0) * dx / 3.0;
+        const double r = (vb - va) * dx / len;
+        const double p = va + (vb - va) * ((double)m * dx - xa) / len;
+        atomicAdd(n + c0, dens * (i0 - i1) / dx);
+        atomicAdd(n + c1, dens * i1 / dx);
+        atomicAdd(j + c0, dens * (p * (i0 - i1) + r * (i1 - i2)) / dx);
+        atomicAdd(j + c1, dens * (p * i1 + r * i2) / dx);
+    }
+}
+
+__global__ void k_moments(const SimDev S, int weighting, double dx, double unit_q, double unit_v, double *n,
+                          double *j)
+{
+    const int nx = S.div.nx;
+    const int src = (int)S.sc->buf;
+    const long long *U = reinterpret_cast<const long long *>(S.U[src]);
+    const float *V = S.V[src];
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < S.n_items; it += gridDim.x * blockDim.x) {
+        const WorkItem W = S.items[it];
+        const long long last = W.t0 + W.count - 1;
+        for (long long t = W.t0; t <= last; ++t) {
+            long long t1 = t + 1, shift = 0;
+            if (t == last) {
+                if (W.halo < 0)
+                    break;
+                t1 = W.halo;
+                shift = W.halo_shift;
+            }
+            const double xa = (double)U[t] * dx * 0x1p-32, xb = (double)(U[t1] + shift) * dx * 0x1p-32;
+            const double va = (double)V[t] * unit_v, vb = (double)V[t1] * unit_v;
+            const double qa = S.Qh ? (double)S.Qh[t] : (double)W.qh, qb = S.Qh ? (double)S.Qh[t1] : (double)W.qh;
+            const double vbar = (qa + qb) > 0 ? (qa * va + qb * vb) / (qa + qb) : 0.5 * (va + vb);
+            moments_one(xa, va, xb, vb, (qa + qb) * unit_q, vbar, weighting, nx, dx, n, j);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_moments(const SimDev &sim, int weighting, double dx, double unit_q, double unit_v, double *n,
+                           double *j, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(n, 0, sizeof(double) * (size_t)sim.div.nx, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(j, 0, sizeof(double) * (size_t)sim.div.nx, s);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = (int)std::min<long long>(4096, ((long long)sim.n_items + 255) / 256);
+    k_moments<<<std::max(grid, 1), 256, 0, s>>>(sim, weighting, dx, unit_q, unit_v, n, j);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -177,6 +177,23 @@ def two_stream(v0, sigma, k, nx, n_sheets, n_tracers, eps=0.01, dt=0.05,
                        dict(v0=v0, sigma=sigma, k=k, eps=eps))
 
 
+def vertical(p: Problem, name=None) -> Problem:
+    """The same tracers as the horizontal set-up ``p``, connected the other way
+    (Sec. 3.3, phase-space geometry): one open sheet per position, its tracers
+    ordered by velocity, each with the weight it has in ``p``.  Every particle
+    starts with zero length (all tracers of a sheet share x)."""
+    if not p.is_horizontal:
+        raise ValueError("needs a horizontal set-up")
+    n, m = p.x_template.size, p.v_sheet.size
+    x = np.repeat(p.x_template, m)
+    v = np.tile(p.v_sheet, n)
+    w = np.tile(p.w_sheet, n)
+    return Problem(name=name or p.name + "_vertical", nx=p.nx, L=p.L, dt=p.dt, n_steps=p.n_steps,
+                   counts=np.full(n, m, dtype=np.int32), closed=np.zeros(n, dtype=np.uint8),
+                   winding=np.zeros(n, dtype=np.int32), qm=p.qm, half_step_init=p.half_step_init,
+                   x_full=x, v_full=v, w_full=w, params=dict(p.params, connectivity="vertical"))
+
+
 def landau_linear(**kw):
     """Linear Landau damping: alpha 0.01, k 0.5, Nx 128, 256 x 1024, dt 0.05, t_end 50."""
     args = dict(alpha=0.01, k=0.5, nx=128, n_sheets=256, n_tracers=1024, dt=0.05,

@@ -32,7 +32,7 @@ EXPORTS = [
     "sic_batch_create", "sic_batch_step", "sic_batch_segments", "sic_batch_destroy",
     "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
     "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
-    "sic_step_batch_static",
+    "sic_step_batch_static", "sic_moments",
 ]
 
 
@@ -50,7 +50,7 @@ class sic_config(ctypes.Structure):
         ("strict_segments", ctypes.c_int32),
         ("history_len", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
-        ("deposit_order", ctypes.c_int32),
+        ("deposit", ctypes.c_int32),
     ]
 
 
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_step": ([simp, ctypes.c_int32], ctypes.c_int),
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_step_batch_static": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
+        "sic_moments": ([simp, ctypes.c_int32, dp, dp], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
         "sic_history": ([simp, dp, ip], ctypes.c_int),
         "sic_get_state": ([simp, dp, dp], ctypes.c_int),
@@ -201,7 +202,7 @@ def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
     cfg.strict_segments = int(bool(strict))
     cfg.history_len = int(history_len)
     cfg.stream = ctypes.c_void_p(int(stream) if stream else 0)
-    cfg.deposit_order = int(order)
+    cfg.deposit = int(order)
     return cfg, keep
 
 
@@ -249,8 +250,9 @@ class Sim:
 
     @classmethod
     def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None, order=0):
-        """Create from an ``inputs.Problem`` (compact form when it has one); order 1
-        selects the piecewise-linear particles of Sec. 2.5."""
+        """Create from an ``inputs.Problem`` (compact form when it has one); order
+        is the deposit (SIC_DEPOSIT_*): 0 box particles, 1 piecewise linear
+        (Sec. 2.5), 2 and 3 PIC nearest grid point and cloud in cell."""
         hl = history_len if history_len is not None else max(1, p.n_steps)
         if horizontal is None:
             horizontal = p.is_horizontal
@@ -275,6 +277,14 @@ class Sim:
         _check(_lib.sic_deposit(self.handle, mesh.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                 _dptr(rho)), "sic_deposit")
         return mesh, rho
+
+    def sic_moments(self, weighting=0):
+        """(n, j): number and current density, zero order on cells (0) or first
+        order on nodes (1)."""
+        n = np.zeros(self.nx, dtype=np.float64)
+        j = np.zeros(self.nx, dtype=np.float64)
+        _check(_lib.sic_moments(self.handle, int(weighting), _dptr(n), _dptr(j)), "sic_moments")
+        return n, j
 
     def sic_field(self):
         E = np.zeros(self.nx, dtype=np.float64)
@@ -344,6 +354,7 @@ def sic_step_batch(sims, n_steps):
 
 
 SIC_STATIC_MAX_SIMS = 64
+SIC_DEPOSIT_BOX, SIC_DEPOSIT_LINEAR, SIC_DEPOSIT_PIC_NGP, SIC_DEPOSIT_PIC_CIC = 0, 1, 2, 3
 
 
 def sic_step_batch_static(sims, n_steps):

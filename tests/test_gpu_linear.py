@@ -1,4 +1,4 @@
-"""GPU parity of piecewise-linear particles (Sec. 2.5, deposit_order = 1)
+"""GPU parity of piecewise-linear particles (Sec. 2.5, SIC_DEPOSIT_LINEAR)
 against the FP64 oracle's piecewise-linear deposit, through the C ABI.
 
 Same tolerances as the box particles (reading A-14): per step on identical

@@ -481,3 +481,20 @@ def test_pic_cloud_in_cell_of_a_uniform_lattice_is_uniform():
     w = np.full(x.size, 0.125)
     cic = oracle.deposit(nx, L, [x.size], [1], [1], x, w, order=3)
     np.testing.assert_allclose(cic, cic.mean(), rtol=1e-13)
+
+
+def test_vertical_sheets_start_as_point_charges():
+    """Vertical connectivity (Sec. 3.3): every particle of a velocity-ordered
+    sheet starts with zero length, so the deposit puts each particle's whole
+    charge in its tracers' cell: the tracer weights, halved at the two ends of
+    every open sheet, in the cell of their position."""
+    p = inputs.vertical(inputs.landau(0.1, 0.5, 32, 12, 40, t_end=1.0))
+    got = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, p.x, p.w)
+    w = p.w.reshape(len(p.counts), -1).copy()
+    w[:, 0] *= 0.5
+    w[:, -1] *= 0.5
+    want = np.zeros(p.nx)
+    cells = np.floor(p.x.reshape(len(p.counts), -1)[:, 0] / (p.L / p.nx)).astype(int) % p.nx
+    for c, row in zip(cells, w):
+        want[c] += row.sum()
+    np.testing.assert_allclose(got, want, rtol=1e-13)
