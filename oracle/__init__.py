@@ -54,6 +54,8 @@ def _load():
                                         ip, bp, ip, dp, dp, dp]
             lib.orc_deposit.restype = ctypes.c_int
             lib.orc_deposit_linear.argtypes = lib.orc_deposit.argtypes
+            lib.orc_deposit_seg.argtypes = lib.orc_deposit.argtypes
+            lib.orc_deposit_seg.restype = ctypes.c_int
             lib.orc_deposit_linear.restype = ctypes.c_int
             lib.orc_moments.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ip, bp, ip,
                                         dp, dp, dp, ctypes.c_int, dp, dp]
@@ -198,6 +200,84 @@ def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
     if record_E:
         out["E_hist"] = e_hist
     return out
+
+
+def deposit_seg(nx, L, counts, closed, winding, x, qseg):
+    """Charge per cell of box particles whose charges are given per particle:
+    qseg[i] belongs to the particle starting at tracer i."""
+    lib = _load()
+    counts, closed, winding = _sheets(counts, closed, winding)
+    x, qseg = _f64(x), _f64(qseg)
+    out = np.zeros(int(nx))
+    rc = lib.orc_deposit_seg(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
+                             _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
+                             _ptr(x, ctypes.c_double), _ptr(qseg, ctypes.c_double), _ptr(out, ctypes.c_double))
+    if rc:
+        raise ValueError("every sheet needs at least two tracers")
+    return out
+
+
+def particle_charges(counts, closed, w):
+    """Per-particle charges q_s = (w_i + w_{i+1}) / 2 of tracer weights, in the
+    layout of deposit_seg (0 after the last tracer of an open sheet)."""
+    w = _f64(w)
+    q = np.zeros_like(w)
+    base = 0
+    for n, c in zip(counts, closed):
+        ws = w[base:base + n]
+        q[base:base + n - 1] = 0.5 * (ws[:-1] + ws[1:])
+        q[base + n - 1] = 0.5 * (ws[-1] + ws[0]) if c else 0.0
+        base += n
+    return q
+
+
+def refine(L, counts, closed, winding, x, v, qseg, l_ref):
+    """One pass of the refinement of Sec. 2.6: every particle longer than
+    l_ref gets a new tracer at its centre, with the mean velocity of its two
+    tracers; each half carries half the charge.  Returns the new
+    (counts, x, v, qseg)."""
+    xs, vs, qs, cs = [], [], [], []
+    base = 0
+    for n, c, wd in zip(counts, closed, winding):
+        xo, vo, qo = x[base:base + n], v[base:base + n], qseg[base:base + n]
+        nx_, nv_, nq_ = [], [], []
+        for i in range(n):
+            last = i + 1 == n
+            if last and not c:
+                nx_.append(xo[i]); nv_.append(vo[i]); nq_.append(qo[i])
+                break
+            xb = xo[0] + wd * L if last else xo[i + 1]
+            vb = vo[0] if last else vo[i + 1]
+            if abs(xb - xo[i]) > l_ref:
+                nx_ += [xo[i], 0.5 * (xo[i] + xb)]
+                nv_ += [vo[i], 0.5 * (vo[i] + vb)]
+                nq_ += [0.5 * qo[i], 0.5 * qo[i]]
+            else:
+                nx_.append(xo[i]); nv_.append(vo[i]); nq_.append(qo[i])
+        xs.append(nx_); vs.append(nv_); qs.append(nq_); cs.append(len(nx_))
+        base += n
+    cat = lambda a: np.array([t for part in a for t in part], dtype=np.float64)
+    return np.array(cs, dtype=np.int32), cat(xs), cat(vs), cat(qs)
+
+
+def run_refined(nx, L, dt, counts, closed, winding, x, v, qseg, n_steps, l_ref, every, qm=1.0):
+    """Leapfrog run of box particles with per-particle charges, refined
+    (``refine``) after every ``every`` steps.  The velocities are v^{-1/2} on
+    entry.  Returns dict(counts, x, v, qseg, W) with W the field energy of
+    every step's field before its kick (n_steps values)."""
+    counts = np.array(counts, dtype=np.int32)
+    x, v, qseg = _f64(x).copy(), _f64(v).copy(), _f64(qseg).copy()
+    W = []
+    charge = deposit_seg(nx, L, counts, closed, winding, x, qseg)
+    for step in range(n_steps):
+        _, E = field(nx, L, charge)
+        W.append(field_energy(nx, L, E))
+        v = v + dt * qm * gather(nx, L, E, x)
+        x = x + dt * v
+        if (step + 1) % every == 0:
+            counts, x, v, qseg = refine(L, counts, closed, winding, x, v, qseg, l_ref)
+        charge = deposit_seg(nx, L, counts, closed, winding, x, qseg)
+    return dict(counts=counts, x=x, v=v, qseg=qseg, W=np.array(W))
 
 
 def run_problem(p, n_steps=None, record_E=False, order=0):

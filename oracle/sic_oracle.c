@@ -113,6 +113,35 @@ int orc_deposit(int nx, double L, int n_sheets, const int32_t *counts,
 }
 
 /*
+ * The same deposit with the particles' charges given directly: qseg[i] is the
+ * charge of the particle that starts at tracer i (for the last tracer of a
+ * closed sheet, the closing particle; ignored for the last tracer of an open
+ * sheet).  Refinement (Sec. 2.6) splits particles and halves their charges,
+ * which tracer weights cannot express, so a refined sheet carries its charge
+ * on the particles, as Sec. 2.3 defines it.
+ */
+int orc_deposit_seg(int nx, double L, int n_sheets, const int32_t *counts,
+                    const uint8_t *closed, const int32_t *winding,
+                    const double *x, const double *qseg, double *charge)
+{
+    double dx = L / nx;
+    memset(charge, 0, sizeof(double) * (size_t)nx);
+    long base = 0;
+    for (int s = 0; s < n_sheets; ++s) {
+        long n = counts[s];
+        if (n < 2)
+            return -1;
+        for (long i = 0; i + 1 < n; ++i)
+            deposit_segment(x[base + i], x[base + i + 1], qseg[base + i], nx, dx, charge);
+        if (closed[s])
+            deposit_segment(x[base + n - 1], x[base] + (double)winding[s] * L, qseg[base + n - 1], nx, dx,
+                            charge);
+        base += n;
+    }
+    return 0;
+}
+
+/*
  * Piecewise-linear particles (Sec. 2.5, Eq. piecewise_linear with the
  * gradient of Eq. gradient_rho_estimate).
  *

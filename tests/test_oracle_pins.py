@@ -498,3 +498,64 @@ def test_vertical_sheets_start_as_point_charges():
     for c, row in zip(cells, w):
         want[c] += row.sum()
     np.testing.assert_allclose(got, want, rtol=1e-13)
+
+
+# ------------------------------------------------------------ refinement ----
+# Sec. 2.6: a particle longer than the refinement length gets a new tracer at
+# its centre (mean velocity), each half with half the charge.
+
+def _refine_case(seed):
+    rng = np.random.default_rng(seed)
+    L = 2.0
+    counts = [int(c) for c in rng.integers(3, 30, size=4)]
+    closed = [1, 0, 1, 0]
+    winding = [1, 0, -1, 0]
+    x = _dyadic(rng, sum(counts), L, denom=32)
+    v = rng.normal(size=sum(counts))
+    w = rng.integers(1, 9, size=sum(counts)) / 8.0
+    return L, counts, closed, winding, x, v, oracle.particle_charges(counts, closed, w)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_refinement_keeps_the_deposit_and_the_charge(seed):
+    """Splitting a box particle at its centre into two halves of half the
+    charge leaves its density, and so the deposit, unchanged; the inserted
+    tracers sit at the centres with the mean velocities."""
+    L, counts, closed, winding, x, v, q = _refine_case(seed)
+    nx, l_ref = 16, 0.3
+    c2, x2, v2, q2 = oracle.refine(L, counts, closed, winding, x, v, q, l_ref)
+    before = oracle.deposit_seg(nx, L, counts, closed, winding, x, q)
+    after = oracle.deposit_seg(nx, L, c2, closed, winding, x2, q2)
+    np.testing.assert_allclose(after, before, rtol=1e-12, atol=1e-13)
+    assert math.isclose(q2.sum(), q.sum(), rel_tol=1e-15)
+    # one new tracer per particle longer than l_ref
+    base, base2 = 0, 0
+    for n, n2, c, wd in zip(counts, c2, closed, winding):
+        xs = x[base:base + n]
+        ends = np.r_[xs[1:], xs[0] + wd * L] if c else xs[1:]
+        long_ = np.abs(ends - xs[:len(ends)]) > l_ref
+        assert n2 == n + long_.sum()
+        # the inserted tracers are the centres of the long particles
+        ins = []
+        k = base2
+        for i in range(n):
+            k += 1
+            if i < len(ends) and long_[i]:
+                ins.append(x2[k])
+                k += 1
+        np.testing.assert_allclose(ins, 0.5 * (xs[:len(ends)][long_] + ends[long_]), rtol=0, atol=1e-15)
+        base += n
+        base2 += n2
+
+
+def test_repeated_refinement_bounds_every_particle():
+    L, counts, closed, winding, x, v, q = _refine_case(11)
+    l_ref = 0.05
+    for _ in range(12):
+        counts, x, v, q = oracle.refine(L, counts, closed, winding, x, v, q, l_ref)
+    base = 0
+    for n, c, wd in zip(counts, closed, winding):
+        xs = x[base:base + n]
+        ends = np.r_[xs[1:], xs[0] + wd * L] if c else xs[1:]
+        assert np.abs(ends - xs[:len(ends)]).max() <= l_ref
+        base += n
