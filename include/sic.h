@@ -166,6 +166,26 @@ int sic_field(sic_sim *sim, double *E_host);
  */
 int sic_moments(sic_sim *sim, int32_t weighting, double *n_host, double *j_host);
 
+/*
+ * Refinement (Sec. 2.6): every particle of the current state longer than
+ * l_ref (same length unit as box_length) gets a new tracer at its centre,
+ * with the mean velocity of its two tracers; each half carries half the
+ * particle's charge (the first floor(Q/2) fixed-point units, the second the
+ * rest), so the total charge stays exact and the deposit does not change.
+ * One pass: a particle longer than 2 l_ref needs another call.  From the
+ * first refinement on, the simulation carries its charge per particle and a
+ * tracer's mass is the charge of the particle it starts (the last tracer of
+ * an open sheet has none).  The state is moved to a new, larger device
+ * allocation; batches and servers holding the simulation must be rebuilt.
+ * Box and piecewise-linear deposits only (SIC_EINVAL for the PIC ones);
+ * l_ref must be finite and > 0.  *n_added (nullable) gets the number of new
+ * tracers; sic_sheet_counts gives the new tracers per sheet.
+ */
+int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added);
+
+/* Tracers per sheet now (they grow with sic_refine), into counts_host[M]. */
+int sic_sheet_counts(sic_sim *sim, int32_t *counts_host);
+
 /* Gather, kick and drift every tracer with the current field; no deposit. */
 int sic_push(sic_sim *sim);
 
@@ -196,8 +216,9 @@ void sic_batch_destroy(sic_batch *batch);
 int sic_diagnostics(sic_sim *sim, sic_diag *out);
 
 /* Per-step history [rows][4] = {W_E, KE, P, charge_fixed} of the last
- * min(rows, history_len) steps, oldest first; returns the row count via *rows. */
-int sic_history(sic_sim *sim, double *hist_host, int32_t *rows);
+ * min(max_rows, history_len, steps taken) steps, oldest first, into hist_host
+ * (room for max_rows rows, max_rows >= 1); the row count goes to *rows. */
+int sic_history(sic_sim *sim, double *hist_host, int32_t max_rows, int32_t *rows);
 
 /* Copy the tracers back: unwrapped positions and current velocities
  * (v^{n-1/2} after n steps), host, sum(tracers_per_sheet) entries each. */

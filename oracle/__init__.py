@@ -56,6 +56,8 @@ def _load():
             lib.orc_deposit_linear.argtypes = lib.orc_deposit.argtypes
             lib.orc_deposit_seg.argtypes = lib.orc_deposit.argtypes
             lib.orc_deposit_seg.restype = ctypes.c_int
+            lib.orc_deposit_linear_seg.argtypes = lib.orc_deposit.argtypes
+            lib.orc_deposit_linear_seg.restype = ctypes.c_int
             lib.orc_deposit_linear.restype = ctypes.c_int
             lib.orc_moments.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ip, bp, ip,
                                         dp, dp, dp, ctypes.c_int, dp, dp]
@@ -202,14 +204,16 @@ def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
     return out
 
 
-def deposit_seg(nx, L, counts, closed, winding, x, qseg):
-    """Charge per cell of box particles whose charges are given per particle:
-    qseg[i] belongs to the particle starting at tracer i."""
+def deposit_seg(nx, L, counts, closed, winding, x, qseg, order=0):
+    """Charge per cell of particles whose charges are given per particle:
+    qseg[i] belongs to the particle starting at tracer i; order 1 makes them
+    piecewise linear (Sec. 2.5)."""
     lib = _load()
     counts, closed, winding = _sheets(counts, closed, winding)
     x, qseg = _f64(x), _f64(qseg)
     out = np.zeros(int(nx))
-    rc = lib.orc_deposit_seg(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
+    fn = lib.orc_deposit_linear_seg if order == 1 else lib.orc_deposit_seg
+    rc = fn(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
                              _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
                              _ptr(x, ctypes.c_double), _ptr(qseg, ctypes.c_double), _ptr(out, ctypes.c_double))
     if rc:

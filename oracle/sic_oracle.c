@@ -189,9 +189,12 @@ static void deposit_linear_segment(double xa, double xb, double q, double g,
     }
 }
 
-int orc_deposit_linear(int nx, double L, int n_sheets, const int32_t *counts,
-                       const uint8_t *closed, const int32_t *winding,
-                       const double *x, const double *w, double *charge)
+/* w (tracer weights) or qseg (per-particle charges, as for orc_deposit_seg):
+ * exactly one of them is given. */
+static int deposit_linear_sheets(int nx, double L, int n_sheets, const int32_t *counts,
+                                 const uint8_t *closed, const int32_t *winding,
+                                 const double *x, const double *w, const double *qseg,
+                                 double *charge)
 {
     double dx = L / nx;
     memset(charge, 0, sizeof(double) * (size_t)nx);
@@ -213,10 +216,10 @@ int orc_deposit_linear(int nx, double L, int n_sheets, const int32_t *counts,
             xa[k] = x[base + i];
             if (j < n) {
                 xb[k] = x[base + j];
-                q[k] = 0.5 * (w[base + i] + w[base + j]);
+                q[k] = qseg ? qseg[base + i] : 0.5 * (w[base + i] + w[base + j]);
             } else {
                 xb[k] = x[base] + shift;
-                q[k] = 0.5 * (w[base + i] + w[base]);
+                q[k] = qseg ? qseg[base + i] : 0.5 * (w[base + i] + w[base]);
             }
             double len = fabs(xb[k] - xa[k]);
             rho0[k] = len > 0.0 ? q[k] / len : 0.0;
@@ -275,6 +278,21 @@ int orc_deposit_pic(int nx, double L, long n_tracers, const double *x,
         }
     }
     return 0;
+}
+
+int orc_deposit_linear(int nx, double L, int n_sheets, const int32_t *counts,
+                       const uint8_t *closed, const int32_t *winding,
+                       const double *x, const double *w, double *charge)
+{
+    return deposit_linear_sheets(nx, L, n_sheets, counts, closed, winding, x, w, NULL, charge);
+}
+
+/* Piecewise-linear particles with per-particle charges (refined sheets). */
+int orc_deposit_linear_seg(int nx, double L, int n_sheets, const int32_t *counts,
+                           const uint8_t *closed, const int32_t *winding,
+                           const double *x, const double *qseg, double *charge)
+{
+    return deposit_linear_sheets(nx, L, n_sheets, counts, closed, winding, x, NULL, qseg, charge);
 }
 
 /* The deposit of the given kind: 0 box particles (Sec. 2.3), 1 piecewise

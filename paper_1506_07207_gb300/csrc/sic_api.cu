@@ -218,6 +218,40 @@ double choose_sigma(double max_w)
     return sigma;
 }
 
+// Point the descriptor at a device allocation laid out by L and upload the
+// work items (and piecewise-linear neighbours) into it.
+cudaError_t bind_layout(sic_sim *sim, char *b, const SimLayout &L)
+{
+    SimDev &h = sim->h;
+    const int n_items = (int)sim->items.size();
+    h.U[0] = (int64_t *)(b + L.oU0);
+    h.U[1] = (int64_t *)(b + L.oU1);
+    h.V[0] = (float *)(b + L.oV0);
+    h.V[1] = (float *)(b + L.oV1);
+    h.Qh = sim->per_q ? (const int32_t *)(b + L.oQ) : nullptr;
+    h.mesh = (unsigned long long *)(b + L.oMesh);
+    h.mesh_last = (long long *)(b + L.oLast);
+    h.Ek = (float2 *)(b + L.oEk);
+    h.E64 = (double *)(b + L.oE64);
+    h.rho64 = (double *)(b + L.oRho);
+    h.acc = (SimAccum *)(b + L.oAcc);
+    h.items = (const WorkItem *)(b + L.oItems);
+    cudaError_t e = cudaMemcpyAsync((void *)h.items, sim->items.data(), sizeof(WorkItem) * (size_t)n_items,
+                                    cudaMemcpyHostToDevice, sim->stream);
+    h.pl = nullptr;
+    h.deposit = sim->deposit;
+    h.seg_q = sim->seg_q ? 1 : 0;
+    if (e == cudaSuccess && sim->deposit == SIC_DEPOSIT_LINEAR) {
+        h.pl = (const WorkItemPL *)(b + L.oPL);
+        e = cudaMemcpyAsync((void *)h.pl, sim->pl_items.data(), sizeof(WorkItemPL) * (size_t)n_items,
+                            cudaMemcpyHostToDevice, sim->stream);
+    }
+    h.hist = (double *)(b + L.oHist);
+    h.sc = (SimScalars *)(b + L.oSc);
+    h.n_items = n_items;
+    return e;
+}
+
 // Common part of both constructors: sizes, device layout, descriptor, plan.
 // Expects counts, closed, winding, per_q, sigma and sheet_qh to be set.
 int setup(sic_sim *sim, const sic_config *cfg)
@@ -250,39 +284,13 @@ int setup(sic_sim *sim, const sic_config *cfg)
 
     const int nx = sim->nx;
     const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len, sim->deposit);
-    const size_t oU0 = L.oU0, oU1 = L.oU1, oV0 = L.oV0, oV1 = L.oV1, oQ = L.oQ, oMesh = L.oMesh, oLast = L.oLast,
-                 oEk = L.oEk, oE64 = L.oE64, oRho = L.oRho, oAcc = L.oAcc, oItems = L.oItems, oHist = L.oHist,
-                 oSc = L.oSc;
     sim->dbytes = L.total;
     CK(cudaMallocAsync(&sim->dmem, L.total, sim->stream));
     char *b = (char *)sim->dmem;
     CK(cudaMemsetAsync(b, 0, L.total, sim->stream));
 
     SimDev &h = sim->h;
-    h.U[0] = (int64_t *)(b + oU0);
-    h.U[1] = (int64_t *)(b + oU1);
-    h.V[0] = (float *)(b + oV0);
-    h.V[1] = (float *)(b + oV1);
-    h.Qh = sim->per_q ? (const int32_t *)(b + oQ) : nullptr;
-    h.mesh = (unsigned long long *)(b + oMesh);
-    h.mesh_last = (long long *)(b + oLast);
-    h.Ek = (float2 *)(b + oEk);
-    h.E64 = (double *)(b + oE64);
-    h.rho64 = (double *)(b + oRho);
-    h.acc = (SimAccum *)(b + oAcc);
-    h.items = (const WorkItem *)(b + oItems);
-    CK(cudaMemcpyAsync((void *)h.items, sim->items.data(), sizeof(WorkItem) * (size_t)n_items, cudaMemcpyHostToDevice,
-                       sim->stream));
-    h.pl = nullptr;
-    h.deposit = sim->deposit;
-    if (sim->deposit == SIC_DEPOSIT_LINEAR) {
-        h.pl = (const WorkItemPL *)(b + L.oPL);
-        CK(cudaMemcpyAsync((void *)h.pl, sim->pl_items.data(), sizeof(WorkItemPL) * (size_t)n_items,
-                           cudaMemcpyHostToDevice, sim->stream));
-    }
-    h.hist = (double *)(b + oHist);
-    h.sc = (SimScalars *)(b + oSc);
-    h.n_items = n_items;
+    CK(bind_layout(sim, b, L));
     h.hist_len = sim->hist_len;
     h.div = make_div(nx);
     const double nx2 = (double)nx * (double)nx;
@@ -673,6 +681,164 @@ int sic_moments(sic_sim *sim, int32_t weighting, double *n_host, double *j_host)
     return check_device_errors(sim);
 }
 
+int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
+{
+    if (!sim || !is_finite(l_ref) || l_ref <= 0)
+        return SIC_EINVAL;
+    if (sim->deposit != SIC_DEPOSIT_BOX && sim->deposit != SIC_DEPOSIT_LINEAR)
+        return SIC_EINVAL;
+    if (n_added)
+        *n_added = 0;
+    int rc = check_device_errors(sim);
+    if (rc)
+        return rc;
+    const double lc = l_ref / sim->dx * kTwo32;  // 32.32 cells
+    if (lc >= 4.0e18)
+        return SIC_OK;  // nothing can be that long
+    const long long lfix = (long long)lc;
+    const int n_items = (int)sim->items.size();
+
+    // 1. particles to split, per work item
+    void *scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, 12 * (size_t)n_items, sim->stream));
+    int64_t *d_base = (int64_t *)scratch;  // the 8-byte array first: both stay aligned
+    int32_t *d_splits = (int32_t *)((char *)scratch + 8 * (size_t)n_items);
+    std::vector<int32_t> splits(n_items);
+    cudaError_t e = launch_refine_count(sim->h, lfix, d_splits, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(splits.data(), d_splits, 4 * (size_t)n_items, cudaMemcpyDeviceToHost, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(scratch, sim->stream);
+        return fail_cuda(sim, e);
+    }
+
+    // 2. the new layout: sheet sizes, offsets, where each item's tracers go
+    std::vector<int32_t> counts = sim->counts;
+    int64_t added = 0;
+    {
+        int k = 0;
+        for (int s = 0; s < sim->M; ++s) {
+            const int items_s = (sim->counts[s] + SIC_K1_WARP_TRACERS - 1) / SIC_K1_WARP_TRACERS;
+            for (int i = 0; i < items_s; ++i, ++k)
+                counts[s] += splits[k];
+            added += counts[s] - sim->counts[s];
+        }
+    }
+    if (added == 0 || sim->n_tracers + added > SIC_TRACERS_MAX) {
+        cudaFreeAsync(scratch, sim->stream);
+        cudaStreamSynchronize(sim->stream);
+        return added == 0 ? SIC_OK : SIC_EINVAL;
+    }
+    std::vector<int64_t> off(sim->M);
+    int64_t n_alloc = 0;
+    for (int s = 0; s < sim->M; ++s) {
+        off[s] = n_alloc;
+        n_alloc += (counts[s] + SIC_ALIGN_TRACERS - 1) / SIC_ALIGN_TRACERS * SIC_ALIGN_TRACERS;
+    }
+    n_alloc = std::max<int64_t>(n_alloc, SIC_ALIGN_TRACERS);
+    std::vector<int64_t> base(n_items);
+    {
+        int k = 0;
+        for (int s = 0; s < sim->M; ++s) {
+            const int items_s = (sim->counts[s] + SIC_K1_WARP_TRACERS - 1) / SIC_K1_WARP_TRACERS;
+            int64_t at = off[s];
+            for (int i = 0; i < items_s; ++i, ++k) {
+                base[k] = at;
+                at += sim->items[k].count + splits[k];
+            }
+        }
+    }
+    const int64_t new_items = work_items(counts.data(), sim->M);
+    const SimLayout L = sim_layout(sim->nx, n_alloc, new_items, true, sim->hist_len, sim->deposit);
+    void *mem = nullptr;
+    e = cudaMemcpyAsync(d_base, base.data(), 8 * (size_t)n_items, cudaMemcpyHostToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync(&mem, L.total, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(mem, 0, L.total, sim->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(scratch, sim->stream);
+        if (mem)
+            cudaFreeAsync(mem, sim->stream);
+        return fail_cuda(sim, e);
+    }
+
+    // 3. the tracers, with the new ones, and per-particle charges; the mesh,
+    //    field, sums, history and scalars carry over unchanged (a box
+    //    particle split at its centre into halves deposits the same charge)
+    char *b = (char *)mem;
+    SimScalars sc;
+    CK(cudaMemcpyAsync(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    const int cur = (int)(sc.buf & 1);
+    const size_t oU = cur ? L.oU1 : L.oU0, oV = cur ? L.oV1 : L.oV0;
+    e = launch_refine_scatter(sim->h, lfix, d_base, (int64_t *)(b + oU), (float *)(b + oV), (int32_t *)(b + L.oQ),
+                              sim->stream);
+    const size_t nx8 = 8 * (size_t)sim->nx;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oMesh, sim->h.mesh, nx8, cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oLast, sim->h.mesh_last, nx8, cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oEk, sim->h.Ek, nx8, cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oE64, sim->h.E64, nx8, cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oRho, sim->h.rho64, nx8, cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oAcc, sim->h.acc, sizeof(SimAccum), cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oHist, sim->h.hist, 32 * (size_t)sim->hist_len, cudaMemcpyDeviceToDevice,
+                            sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.oSc, sim->h.sc, sizeof(SimScalars), cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(sim->stream);
+    cudaFreeAsync(scratch, sim->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(mem, sim->stream);
+        return fail_cuda(sim, e);
+    }
+
+    // 4. switch the simulation over: sheets, items, descriptor, plan
+    cudaFreeAsync(sim->dmem, sim->stream);
+    if (sim->gexec) {
+        cudaGraphExecDestroy(sim->gexec);
+        sim->gexec = nullptr;
+    }
+    free_plan(sim->plan, sim->stream);
+    const bool was_seg = sim->seg_q;
+    sim->counts = counts;
+    sim->sheet_off = off;
+    sim->n_tracers += added;
+    sim->n_alloc = n_alloc;
+    sim->per_q = true;
+    sim->seg_q = true;
+    sim->dmem = mem;
+    sim->dbytes = L.total;
+    plan_items(sim);
+    CK(bind_layout(sim, b, L));
+    if (!was_seg) {  // a tracer's mass is now its particle's charge, Q_s, not 2 Qh
+        sim->h.ke_scale *= 0.5;
+        sim->h.p_scale *= 0.5;
+    }
+    sic_sim *one[1] = {sim};
+    CK(build_plan(sim->plan, one, 1, sim->stream));
+    if (n_added)
+        *n_added = added;
+    return check_device_errors(sim);
+}
+
+int sic_sheet_counts(sic_sim *sim, int32_t *counts_host)
+{
+    if (!sim || !counts_host)
+        return SIC_EINVAL;
+    std::copy(sim->counts.begin(), sim->counts.end(), counts_host);
+    return SIC_OK;
+}
+
 int sic_field(sic_sim *sim, double *E_host)
 {
     if (!sim || !E_host)
@@ -931,15 +1097,15 @@ int sic_diagnostics(sic_sim *sim, sic_diag *out)
     return SIC_OK;
 }
 
-int sic_history(sic_sim *sim, double *hist_host, int32_t *rows)
+int sic_history(sic_sim *sim, double *hist_host, int32_t max_rows, int32_t *rows)
 {
-    if (!sim || !hist_host || !rows)
+    if (!sim || !hist_host || !rows || max_rows < 1)
         return SIC_EINVAL;
     SimScalars sc;
     int rc = check_device_errors(sim, &sc);
     if (rc)
         return rc;
-    const int64_t n = std::min<int64_t>(sc.step, sim->hist_len);
+    const int64_t n = std::min<int64_t>(std::min<int64_t>(sc.step, sim->hist_len), max_rows);
     std::vector<double> ring(4 * (size_t)sim->hist_len);
     CK(cudaMemcpy(ring.data(), sim->h.hist, 8 * ring.size(), cudaMemcpyDeviceToHost));
     for (int64_t i = 0; i < n; ++i) {

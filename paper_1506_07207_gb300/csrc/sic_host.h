@@ -49,6 +49,7 @@ struct sic_sim {
     double sigma = 1.0;
     std::vector<WorkItem> items;
     int deposit = SIC_DEPOSIT_BOX;    // SIC_DEPOSIT_*
+    bool seg_q = false;               // refined: Qh holds per-particle charges
     std::vector<WorkItemPL> pl_items;
     cudaStream_t stream = nullptr;
     bool own_stream = false;

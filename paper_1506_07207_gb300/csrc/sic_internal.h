@@ -9,7 +9,9 @@
 //   V[2][n_alloc] float  velocity in cells per step (v dt / dx).
 //   Qh[n_alloc]   int32  half charge of each tracer in fixed-point units (only
 //                        when weights differ inside a sheet; otherwise every
-//                        work item carries its sheet's value).
+//                        work item carries its sheet's value); after a
+//                        refinement (seg_q) the charge of the particle that
+//                        starts at the tracer instead.
 //   mesh[nx]      u64    int64 charge accumulator the deposit adds into.
 //   mesh_last     int64  charge of the latest completed deposit.
 //   Ek[nx]        float2 (Ek_j, Ek_{j+1} - Ek_j): the kick per step
@@ -115,6 +117,8 @@ struct SimDev {
     const WorkItem *items;      // [n_items] this simulation's work items
     const WorkItemPL *pl;       // [n_items] for piecewise-linear particles, else null
     int32_t deposit;            // SIC_DEPOSIT_*
+    int32_t seg_q;              // Qh holds each particle's own charge (refined
+                                // sheets: the particle starting at the tracer)
     int32_t n_items;
     int32_t hist_len;
     NxDiv div;
@@ -154,6 +158,9 @@ namespace sic {
 enum Mode { MODE_STEP = 0, MODE_DEPOSIT = 1, MODE_PUSH = 2 };
 cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s);
 cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s);
+cudaError_t launch_refine_count(const SimDev &sim, long long lfix, int32_t *splits, cudaStream_t s);
+cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, int64_t *U2, float *V2,
+                                  int32_t *Q2, cudaStream_t s);
 cudaError_t launch_moments(const SimDev &sim, int weighting, double dx, double unit_q, double unit_v, double *n,
                            double *j, cudaStream_t s);
 cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,

@@ -739,7 +739,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                                         const float2 *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg,
-                                        const WorkItemPL *pw, int dep)
+                                        const WorkItemPL *pw, int dep, int segq)
 {
     const long long *stU = reinterpret_cast<const long long *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
@@ -1042,7 +1042,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                     }
                     const int cr = cell_of(u[r]);
                     const bool same = seg && cr == cell_of(ub);
-                    const unsigned qv = (unsigned)(PER_Q ? q[r] + qb : qs_sheet);
+                    const unsigned qv = (unsigned)(PER_Q ? (segq ? q[r] : q[r] + qb) : qs_sheet);
                     const int d = cr - c0;
                     b0 += (same && d == 0) ? qv : 0u;
                     b1 += (same && d == 1) ? qv : 0u;
@@ -1080,7 +1080,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                             seg = has_halo;
                         }
                         if (seg && cell_of(u[r]) == cell_of(ub))
-                            acc.add(jn[r], PER_Q ? q[r] + qb : qs_sheet);
+                            acc.add(jn[r], PER_Q ? (segq ? q[r] : q[r] + qb) : qs_sheet);
                     }
                 }
                 acc.flush();
@@ -1118,15 +1118,15 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 const int w8 = threadIdx.x >> 5;
                 const long long up = idx > 0 ? pts[idx - 1] : sh.pl_prev[w8];
                 const long long un = pts[idx + 2];
-                const int qp = PER_Q ? (idx > 0 ? qpts[idx - 1] : sh.pl_prevq[w8]) + qpts[idx] : qs_sheet;
-                const int qn = PER_Q ? qpts[idx + 1] + qpts[idx + 2] : qs_sheet;
+                const int qp = PER_Q ? (idx > 0 ? qpts[idx - 1] : sh.pl_prevq[w8]) + (segq ? 0 : qpts[idx]) : qs_sheet;
+                const int qn = PER_Q ? qpts[idx + 1] + (segq ? 0 : qpts[idx + 2]) : qs_sheet;
                 return pl_kappa(up, ua, ub, un, qp, qs, qn);
             };
             bool any_long = false;
             for (int k = lane; k < total; k += 32) {
                 const int idx = tasks[k];
                 const long long ua = pts[idx], ub = pts[idx + 1];
-                const int qs = PER_Q ? qpts[idx] + qpts[idx + 1] : qs_sheet;
+                const int qs = PER_Q ? qpts[idx] + (segq ? 0 : qpts[idx + 1]) : qs_sheet;
                 const float kappa = (GEN && pw != nullptr) ? kappa_of(idx, ua, ub, qs) : 0.f;
                 if (kappa == 0.f) {
                     emit_cross(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs, nx,
@@ -1154,7 +1154,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                         bal &= bal - 1u;
                         const int idx = tasks[base + src] & 0x7fff;
                         const long long ua = pts[idx], ub = pts[idx + 1];
-                        const int qs = PER_Q ? qpts[idx] + qpts[idx + 1] : qs_sheet;
+                        const int qs = PER_Q ? qpts[idx] + (segq ? 0 : qpts[idx + 1]) : qs_sheet;
                         emit_linear_warp(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs,
                                          kappa_of(idx, ua, ub, qs), nx, acc, mseg, lane);
                     }
@@ -1322,22 +1322,22 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     if (W.count == WT)
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                         sh, dv, ks, drift, rerr, st, tasks, ake, ap,
-                                                                        mseg, plw, S.deposit);
+                                                                        mseg, plw, S.deposit, S.seg_q);
                     else
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                          diff, sh, dv, ks, drift, rerr, st, tasks,
-                                                                         ake, ap, mseg, plw, S.deposit);
+                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q);
                     __syncwarp();
                     s ^= 1;
                 } else {
                     if (W.count == WT)
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                          sh, dv, ks, drift, rerr, my_stage, tasks,
-                                                                         ake, ap, mseg, plw, S.deposit);
+                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q);
                     else
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                           diff, sh, dv, ks, drift, rerr, my_stage,
-                                                                          tasks, ake, ap, mseg, plw, S.deposit);
+                                                                          tasks, ake, ap, mseg, plw, S.deposit, S.seg_q);
                 }
             }
             if (!took)
@@ -1756,7 +1756,10 @@ __global__ void k_moments(const SimDev S, int weighting, double dx, double unit_
             const double va = (double)V[t] * unit_v, vb = (double)V[t1] * unit_v;
             const double qa = S.Qh ? (double)S.Qh[t] : (double)W.qh, qb = S.Qh ? (double)S.Qh[t1] : (double)W.qh;
             const double vbar = (qa + qb) > 0 ? (qa * va + qb * vb) / (qa + qb) : 0.5 * (va + vb);
-            moments_one(xa, va, xb, vb, (qa + qb) * unit_q, vbar, weighting, nx, dx, n, j);
+            // per-particle charges (refined sheets): the particle's own; else the
+            // mean of its tracers' weights
+            const double qs = S.seg_q ? qa : qa + qb;
+            moments_one(xa, va, xb, vb, qs * unit_q, vbar, weighting, nx, dx, n, j);
         }
     }
 }
@@ -1773,6 +1776,99 @@ cudaError_t launch_moments(const SimDev &sim, int weighting, double dx, double u
         return e;
     const int grid = (int)std::min<long long>(4096, ((long long)sim.n_items + 255) / 256);
     k_moments<<<std::max(grid, 1), 256, 0, s>>>(sim, weighting, dx, unit_q, unit_v, n, j);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace sic
+
+namespace sic {
+namespace {
+
+// ---------------------------------------------------------- refinement ----
+// Sec. 2.6: a particle longer than the refinement length (lfix, 32.32 cells)
+// gets a new tracer at its centre.  k_refine_count counts those particles per
+// work item; k_refine_scatter writes every tracer, and after each split
+// particle's first tracer the new one, into the new layout, with per-particle
+// charges: each half of a split particle gets half its charge (the first
+// floor(Q / 2), the second the rest).  One thread per work item.
+__device__ __forceinline__ bool refine_seg(const SimDev &S, const WorkItem &W, long long t, const long long *U,
+                                           long long &d, long long &t1)
+{
+    const long long last = W.t0 + W.count - 1;
+    long long shift = 0;
+    t1 = t + 1;
+    if (t == last) {
+        if (W.halo < 0)
+            return false;
+        t1 = W.halo;
+        shift = W.halo_shift;
+    }
+    d = U[t1] + shift - U[t];
+    return true;
+}
+
+__global__ void k_refine_count(const SimDev S, long long lfix, int32_t *splits)
+{
+    const long long *U = reinterpret_cast<const long long *>(S.U[S.sc->buf & 1]);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < S.n_items; it += gridDim.x * blockDim.x) {
+        const WorkItem W = S.items[it];
+        int c = 0;
+        for (long long t = W.t0; t < W.t0 + W.count; ++t) {
+            long long d, t1;
+            if (refine_seg(S, W, t, U, d, t1) && (d > lfix || -d > lfix))
+                ++c;
+        }
+        splits[it] = c;
+    }
+}
+
+__global__ void k_refine_scatter(const SimDev S, long long lfix, const int64_t *out_base, int64_t *U2, float *V2,
+                                 int32_t *Q2)
+{
+    const int b = (int)(S.sc->buf & 1);
+    const long long *U = reinterpret_cast<const long long *>(S.U[b]);
+    const float *V = S.V[b];
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < S.n_items; it += gridDim.x * blockDim.x) {
+        const WorkItem W = S.items[it];
+        long long out = out_base[it];
+        for (long long t = W.t0; t < W.t0 + W.count; ++t) {
+            long long d = 0, t1 = t;
+            const bool seg = refine_seg(S, W, t, U, d, t1);
+            // the particle's charge: its own (refined sheets), else the
+            // mean of its tracers' weights (the sheet's, or per tracer)
+            const int Q = !seg ? 0 : S.seg_q ? S.Qh[t] : S.Qh ? S.Qh[t] + S.Qh[t1] : 2 * W.qh;
+            U2[out] = U[t];
+            V2[out] = V[t];
+            if (seg && (d > lfix || -d > lfix)) {
+                Q2[out] = Q >> 1;
+                ++out;
+                U2[out] = U[t] + (d >> 1);
+                V2[out] = 0.5f * (V[t] + V[t1]);
+                Q2[out] = Q - (Q >> 1);
+            } else {
+                Q2[out] = Q;
+            }
+            ++out;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_refine_count(const SimDev &sim, long long lfix, int32_t *splits, cudaStream_t s)
+{
+    const int grid = (int)std::max<long long>(1, std::min<long long>(4096, ((long long)sim.n_items + 255) / 256));
+    k_refine_count<<<grid, 256, 0, s>>>(sim, lfix, splits);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, int64_t *U2, float *V2,
+                                  int32_t *Q2, cudaStream_t s)
+{
+    const int grid = (int)std::max<long long>(1, std::min<long long>(4096, ((long long)sim.n_items + 255) / 256));
+    k_refine_scatter<<<grid, 256, 0, s>>>(sim, lfix, out_base, U2, V2, Q2);
     count_launches(1);
     return cudaGetLastError();
 }

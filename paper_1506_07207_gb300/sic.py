@@ -32,7 +32,7 @@ EXPORTS = [
     "sic_batch_create", "sic_batch_step", "sic_batch_segments", "sic_batch_destroy",
     "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
     "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
-    "sic_step_batch_static", "sic_moments",
+    "sic_step_batch_static", "sic_moments", "sic_refine", "sic_sheet_counts",
 ]
 
 
@@ -125,8 +125,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_step_batch_static": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_moments": ([simp, ctypes.c_int32, dp, dp], ctypes.c_int),
+        "sic_refine": ([simp, ctypes.c_double, lp], ctypes.c_int),
+        "sic_sheet_counts": ([simp, ip], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
-        "sic_history": ([simp, dp, ip], ctypes.c_int),
+        "sic_history": ([simp, dp, ctypes.c_int32, ip], ctypes.c_int),
         "sic_get_state": ([simp, dp, dp], ctypes.c_int),
         "sic_device_state": ([simp, P(vp), P(vp), P(vp)], ctypes.c_int),
         "sic_sync": ([simp], ctypes.c_int),
@@ -286,6 +288,18 @@ class Sim:
         _check(_lib.sic_moments(self.handle, int(weighting), _dptr(n), _dptr(j)), "sic_moments")
         return n, j
 
+    def sic_refine(self, l_ref):
+        """Split every particle longer than l_ref at its centre (Sec. 2.6);
+        returns the number of new tracers and updates ``counts``."""
+        added = ctypes.c_int64()
+        _check(_lib.sic_refine(self.handle, float(l_ref), ctypes.byref(added)), "sic_refine")
+        counts = np.zeros(self.counts.size, dtype=np.int32)
+        _check(_lib.sic_sheet_counts(self.handle, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "sic_sheet_counts")
+        self.counts = counts.astype(np.int64)
+        self.n_tracers = int(counts.sum())
+        return int(added.value)
+
     def sic_field(self):
         E = np.zeros(self.nx, dtype=np.float64)
         _check(_lib.sic_field(self.handle, _dptr(E)), "sic_field")
@@ -303,9 +317,10 @@ class Sim:
         return {name: getattr(d, name) for name, _ in sic_diag._fields_}
 
     def sic_history(self, history_len: int):
-        buf = np.zeros((history_len, 4), dtype=np.float64)
+        """The last min(history_len, ring length, steps) rows [W_E, KE, P, Q]."""
+        buf = np.zeros((max(1, int(history_len)), 4), dtype=np.float64)
         rows = ctypes.c_int32()
-        _check(_lib.sic_history(self.handle, _dptr(buf), ctypes.byref(rows)), "sic_history")
+        _check(_lib.sic_history(self.handle, _dptr(buf), buf.shape[0], ctypes.byref(rows)), "sic_history")
         return buf[: rows.value]
 
     def sic_get_state(self):
