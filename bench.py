@@ -266,7 +266,7 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    from paper_1506_07207_gb300 import inputs, serving
+    from paper_1506_07207_gb300 import inputs, ranks, serving
     from paper_1506_07207_gb300.sic import Batch, Sim, sic_launch_count
 
     serving_mode = args.workload == "serving"
@@ -319,12 +319,7 @@ def main():
         torch.cuda.synchronize()
     launches = sic_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * S * args.steps / (total_ms / 1e3)
+    total_ms, value = ranks.combine(sum(step_ms), S * args.steps, world, dist, torch.device("cuda", local))
     batch.sic_batch_destroy()
     for s in sims:
         s.sic_destroy()
