@@ -98,3 +98,30 @@ def test_server_rejects_bad_config(sic):
         with pytest.raises(sic.SicError) as e:
             sic.Server(**args)
         assert e.value.code == sic.SIC_EINVAL
+
+
+def test_bad_deposit_scheme(sic):
+    a = _base()
+    for dep in (-1, 4, 99):
+        with pytest.raises(sic.SicError) as e:
+            sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                               a["x"], a["v"], a["w"], order=dep)
+        assert e.value.code == sic.SIC_EINVAL
+
+
+def test_null_handles_are_rejected(sic):
+    """Every entry point that takes a simulation refuses a null one before it
+    touches the GPU."""
+    lib = ctypes.CDLL(sic.LIB_PATH)
+    lib.sic_refine.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    lib.sic_moments.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    lib.sic_sheet_counts.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.sic_history.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    lib.sic_step.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.sic_step_batch_static.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    assert lib.sic_refine(None, 1.0, None) == sic.SIC_EINVAL
+    assert lib.sic_moments(None, 0, None, None) == sic.SIC_EINVAL
+    assert lib.sic_sheet_counts(None, None) == sic.SIC_EINVAL
+    assert lib.sic_history(None, None, 4, None) == sic.SIC_EINVAL
+    assert lib.sic_step(None, 1) == sic.SIC_EINVAL
+    assert lib.sic_step_batch_static(None, 1, None) == sic.SIC_EINVAL
