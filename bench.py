@@ -12,9 +12,10 @@ in log2 (``inputs.serving_mix``, seed 0x5EC5).
   dominant (only) kernel, the fused step, is timed per launch with CUDA
   events on the batch's stream for the roofline.
 * ``serving``: the same requests replayed with Poisson arrivals (rate 0.7 x
-  the measured batched capacity) through the request server, batched
-  (continuous batching) and plain (one simulation per launch sequence,
-  first come first served): throughput and p50/p99 latency.
+  the measured batched capacity, and again at 2 x, where requests queue up)
+  through the request server, batched (continuous batching) and plain (one
+  simulation per launch sequence, first come first served): throughput and
+  p50/p99 latency.
 * ``e2e``: the batched server fed from host arrays (compact horizontal-sheet
   inputs), every request arriving at t = 0, end to end.
 * ``single_sim``: the two-stream configuration (512 x 16384 = 8,388,608
@@ -242,6 +243,8 @@ def main():
                     help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
+    ap.add_argument("--overload", type=float, default=2.0,
+                    help="a second replay at this load (0: none): requests queue up")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-single", action="store_true")
@@ -347,24 +350,30 @@ def main():
     line["wall_s_timed_region"] = t_wall
 
     if rank == 0 and serving_mode and not args.no_serving:
-        works = [p.n_segments * p.n_steps for p in probs]
-        rate = args.load * value / (sum(works) / len(works))
-        arrivals = []
-        t = 0.0
         import numpy as np
-        rng = np.random.default_rng(SEED)
-        for _ in probs:
-            t += rng.exponential(1.0 / rate)
-            arrivals.append(t)
-        out = {}
-        for mode in ("batched", "plain"):
-            r = serving.run_trace(probs, arrivals, plain=(mode == "plain"), max_active=64, chunk_steps=32)
-            out[mode] = {"throughput": r["throughput"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
-                         "makespan_s": r["makespan_s"], "segment_updates": r["segment_updates"],
-                         "peak_device_bytes": r["bytes_peak"]}
-        out["arrival_rate_per_s"] = rate
-        out["load"] = args.load
-        line["serving"] = out
+        works = [p.n_segments * p.n_steps for p in probs]
+
+        def replay(load):
+            rate = load * value / (sum(works) / len(works))
+            arrivals = []
+            t = 0.0
+            rng = np.random.default_rng(SEED)
+            for _ in probs:
+                t += rng.exponential(1.0 / rate)
+                arrivals.append(t)
+            out = {}
+            for mode in ("batched", "plain"):
+                r = serving.run_trace(probs, arrivals, plain=(mode == "plain"), max_active=64, chunk_steps=32)
+                out[mode] = {"throughput": r["throughput"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                             "makespan_s": r["makespan_s"], "segment_updates": r["segment_updates"],
+                             "peak_device_bytes": r["bytes_peak"]}
+            out["arrival_rate_per_s"] = rate
+            out["load"] = load
+            return out
+
+        line["serving"] = replay(args.load)
+        if args.overload > 0:
+            line["serving"]["overload"] = replay(args.overload)
     if rank == 0 and not args.no_e2e:
         if serving_mode:
             arrivals0 = [0.0] * len(probs)
