@@ -366,7 +366,7 @@ def main():
                 r = serving.run_trace(probs, arrivals, plain=(mode == "plain"), max_active=64, chunk_steps=32)
                 out[mode] = {"throughput": r["throughput"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                              "makespan_s": r["makespan_s"], "segment_updates": r["segment_updates"],
-                             "peak_device_bytes": r["bytes_peak"]}
+                             "peak_device_bytes": r["bytes_peak"], "device_busy_s": r["busy_s"]}
             out["arrival_rate_per_s"] = rate
             out["load"] = load
             return out

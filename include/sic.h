@@ -290,6 +290,7 @@ typedef struct {
     int64_t completed;
     int64_t segment_updates; /* of completed requests */
     int64_t ticks;
+    double busy_s;           /* device time of the steps the ticks launched (CUDA events) */
 } sic_server_info;
 
 int sic_server_create(const sic_server_config *cfg, sic_server **out);

@@ -1392,8 +1392,15 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            const unsigned t = atomicAdd(A.tickets + cur, (unsigned)sh.taken);
-            sh.last = (t + (unsigned)sh.taken == (unsigned)n_s) ? 1 : 0;
+            // only a block that took items counts them: a block whose claims
+            // all came too late adds nothing, and must not read a completed
+            // count as its own (that simulation's epilogue would run twice)
+            const unsigned taken = (unsigned)sh.taken;
+            sh.last = 0;
+            if (taken) {
+                const unsigned t = atomicAdd(A.tickets + cur, taken);
+                sh.last = (t + taken == (unsigned)n_s) ? 1 : 0;
+            }
         }
         __syncthreads();
         if (sh.last) {

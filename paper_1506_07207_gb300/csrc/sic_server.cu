@@ -64,6 +64,8 @@ struct sic_server {
     bool plan_valid = false;
     Clock::time_point t0;
     int64_t completed = 0, segment_updates = 0, ticks = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // around each tick's steps
+    double busy_s = 0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -161,6 +163,14 @@ int sic_server_create(const sic_server_config *cfg, sic_server **out)
         return SIC_ECUDA;
     } else {
         s->own_stream = true;
+    }
+    if (cudaEventCreate(&s->ev[0]) != cudaSuccess || cudaEventCreate(&s->ev[1]) != cudaSuccess) {
+        if (s->ev[0])
+            cudaEventDestroy(s->ev[0]);
+        if (s->own_stream)
+            cudaStreamDestroy(s->stream);
+        delete s;
+        return SIC_ECUDA;
     }
     s->t0 = Clock::now();
     *out = s;
@@ -271,7 +281,9 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
     }
     if (!srv->active.empty()) {
         int rc = SIC_OK;
+        bool timed = false;
         if (srv->cfg.plain) {
+            timed = cudaEventRecord(srv->ev[0], srv->stream) == cudaSuccess;
             Active &a = srv->active.front();
             rc = sic_step(a.sim, a.left);
             a.left = 0;
@@ -293,6 +305,7 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
                             rc = SIC_ECUDA;
                     srv->plan_valid = (rc == SIC_OK);
                 }
+                timed = cudaEventRecord(srv->ev[0], srv->stream) == cudaSuccess;
                 for (int32_t st = 0; st < k && rc == SIC_OK; ++st)
                     for (int g = 0; g < 2 && rc == SIC_OK; ++g)
                         if (srv->plan[g].mem &&
@@ -302,8 +315,13 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
             for (Active &a : srv->active)
                 a.left -= k;
         }
+        if (timed)
+            timed = cudaEventRecord(srv->ev[1], srv->stream) == cudaSuccess;
         if (cudaStreamSynchronize(srv->stream) != cudaSuccess && rc == SIC_OK)
             rc = SIC_ECUDA;
+        float ms = 0.f;
+        if (timed && cudaEventElapsedTime(&ms, srv->ev[0], srv->ev[1]) == cudaSuccess)
+            srv->busy_s += 1e-3 * ms;
         const double t = srv->now();
         std::vector<Active> keep;
         for (Active &a : srv->active) {
@@ -349,6 +367,7 @@ int sic_server_stats(sic_server *srv, sic_server_info *out)
     out->completed = srv->completed;
     out->segment_updates = srv->segment_updates;
     out->ticks = srv->ticks;
+    out->busy_s = srv->busy_s;
     return SIC_OK;
 }
 
@@ -365,6 +384,9 @@ void sic_server_destroy(sic_server *srv)
         if (r.sim)
             sic_destroy(r.sim);
     cudaStreamSynchronize(srv->stream);
+    for (cudaEvent_t e : srv->ev)
+        if (e)
+            cudaEventDestroy(e);
     if (srv->own_stream)
         cudaStreamDestroy(srv->stream);
     delete srv;

@@ -55,4 +55,5 @@ def run_trace(problems, arrivals, plain=False, hbm_budget=64 << 30, max_active=6
         "throughput": float(seg / max(last_done - first, 1e-9)),
         "bytes_peak": int(stats["bytes_peak"]),
         "ticks": int(stats["ticks"]),
+        "busy_s": float(stats["busy_s"]),
     }

@@ -105,6 +105,7 @@ class sic_server_info(ctypes.Structure):
         ("completed", ctypes.c_int64),
         ("segment_updates", ctypes.c_int64),
         ("ticks", ctypes.c_int64),
+        ("busy_s", ctypes.c_double),
     ]
 
 

@@ -309,3 +309,34 @@ def test_persistent_batch_equals_alone(sic):
     finally:
         for s in sims:
             s.sic_destroy()
+
+
+def test_many_small_simulations_batch_equals_alone(sic):
+    """Many small simulations beside a few large ones in one launch: blocks
+    move between simulations and often arrive when every item is claimed.
+    Each simulation still takes exactly its steps, bit-identical to running
+    alone."""
+    probs = [inputs.tiny_problem(100 + i, n_sheets=2, max_tracers=300, nx=[16, 37, 64][i % 3], L=1.0)
+             for i in range(40)]
+    probs += [inputs.landau(0.1, 0.5, 128, 64, 4096, t_end=1.0), inputs.two_stream(1.5, 0.2, 0.3, 256, 32, 8192,
+                                                                                     t_end=1.0)]
+    steps = 25
+    alone = []
+    for p in probs:
+        sim = sic.Sim.from_problem(p, history_len=4)
+        sim.sic_step(steps)
+        alone.append(sim.sic_get_state())
+        sim.sic_destroy()
+    sims = [sic.Sim.from_problem(p, history_len=4) for p in probs]
+    try:
+        b = sic.Batch(sims)
+        b.sic_batch_step(steps)
+        b.sic_batch_destroy()
+        for s, (x, v) in zip(sims, alone):
+            assert s.sic_diagnostics()["step"] == steps
+            xg, vg = s.sic_get_state()
+            np.testing.assert_array_equal(xg, x)
+            np.testing.assert_array_equal(vg, v)
+    finally:
+        for s in sims:
+            s.sic_destroy()
