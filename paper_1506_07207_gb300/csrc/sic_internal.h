@@ -15,7 +15,9 @@
 //   mesh[nx]      u64    int64 charge accumulator the deposit adds into.
 //   mesh_last     int64  charge of the latest completed deposit.
 //   Ek[nx]        float2 (Ek_j, Ek_{j+1} - Ek_j): the kick per step
-//                        qm E_j dt^2 / dx at node j, paired for one load.
+//                        qm E_j dt^2 / dx at node j and its difference to the
+//                        next node (the step kernel stages Ek_j alone in
+//                        shared memory and forms the same difference).
 //   E64[nx]       double the node field E_j in physical units.
 //   rho64[nx]     double the neutralised density of the latest deposit.
 // Charge unit: a segment between tracers of weights w_i, w_{i+1} carries

@@ -77,13 +77,13 @@ __device__ __forceinline__ long long to_fixed(float v)
 // gather (linear weighting between nodes j and j+1), kick, drift; j is the
 // cell of the new position on return
 template <bool POW2>
-__device__ __forceinline__ void push_one(long long &u, float &v, int &j, const float2 *ek, const NxDiv &d,
+__device__ __forceinline__ void push_one(long long &u, float &v, int &j, const float *ek, const NxDiv &d,
                                          float ks, int drift, unsigned &rerr)
 {
     const int c = cell_of(u);
     j = wrap_cell<POW2>(c, d);
-    const float2 e = ek[j];
-    const float a = __fmaf_rn(frac_float(u), e.y, e.x);
+    const float e0 = ek[j], e1 = ek[j + 1];  // ek[nx] repeats ek[0]
+    const float a = __fmaf_rn(frac_float(u), __fsub_rn(e1, e0), e0);
     const float vn = __fmaf_rn(ks, a, v);
     v = vn;
     if (drift) {
@@ -533,11 +533,11 @@ struct Shared {
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
 constexpr int kWarpCuts = 8;  // piecewise-linear particles this many cells long use the whole warp
 
-// shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx]; staging starts on a
+// shared head, mesh lo/hi [nx], diff [nx + 2], E [nx + 1]; staging starts on a
 // 128-byte boundary (bulk copies need 16)
 __host__ __device__ __forceinline__ size_t stage_offset(int nx_max)
 {
-    const size_t end = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
+    const size_t end = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)4 * (nx_max + 1);
     return (end + 127) / 128 * 128;
 }
 
@@ -736,7 +736,7 @@ template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED
 __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
                                         const float *__restrict__ Vin, long long *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
-                                        const float2 *ek, const Hist &hist, unsigned long long *diff,
+                                        const float *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg,
                                         const WorkItemPL *pw, int dep, int segq)
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     hist.lo = reinterpret_cast<unsigned *>(mesh_region);
     hist.hi = hist.lo + nx_max;
     unsigned long long *diff = mesh_region + nx_max;  // nx_max + 2 entries
-    float2 *ek = reinterpret_cast<float2 *>(diff + nx_max + 2);
+    float *ek = reinterpret_cast<float *>(diff + nx_max + 2);
     char *stage_base = reinterpret_cast<char *>(smem) + stage_offset(nx_max);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1251,9 +1251,12 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             sh.taken = 0;
             sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
         }
-        if (PUSH)
+        if (PUSH) {
             for (int j = tid; j < nx; j += B)
-                ek[j] = S.Ek[j];
+                ek[j] = S.Ek[j].x;
+            if (tid == 0)
+                ek[nx] = S.Ek[0].x;
+        }
         __syncthreads();
 
         // ---- each warp claims runs of consecutive items (guided: a claim is
@@ -1406,7 +1409,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         if (sh.last) {
             __threadfence();
             if (DEPOSIT)
-                field_epilogue(S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
+                field_epilogue(S, A.record, mesh_region, ek, sh);
             if (tid == 0) {
                 if (PUSH)
                     S.sc->buf = (unsigned)(src ^ 1);
@@ -1599,8 +1602,8 @@ __global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int
 
 size_t step_smem_bytes(int nx_max, bool staged, bool per_q)
 {
-    // shared head, mesh lo/hi [nx], diff [nx + 2], ek [nx] (the epilogue
-    // reuses mesh and ek), then the warps' staging buffers
+    // shared head, mesh lo/hi [nx], diff [nx + 2], E [nx + 1] (the epilogue
+    // reuses mesh and E), then the warps' staging buffers
     // then per warp one staging buffer (two when staged) and a task list
     const size_t buf = staged ? (per_q ? WarpBuf<true, true>::bytes : WarpBuf<false, true>::bytes)
                               : (per_q ? WarpBuf<true, false>::bytes : WarpBuf<false, false>::bytes);
