@@ -241,6 +241,7 @@ def main():
                     help="serving: the request-mix sample; two_stream: the 8.4M-segment two-stream run alone")
     ap.add_argument("--deposit", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC")
+    ap.add_argument("--autotune", type=int, default=1, help="tune the batch schedule before timing (0: default)")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
     ap.add_argument("--overload", type=float, default=2.0,
@@ -294,6 +295,10 @@ def main():
     S = batch.sic_batch_segments()
     for _ in range(args.warmup):
         batch.sic_batch_step(1)
+    schedule = None
+    if args.autotune:
+        d, st = batch.sic_batch_autotune(3)   # untimed: 20 more warm-up steps
+        schedule = {"claim_divisor": d, "staging": ["auto", "off", "on"][st]}
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     uuid = None
@@ -334,7 +339,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 push/deposit, i64 fixed-point charge, exact integer field solve",
-        "data": "synthetic", "config": dict(config, deposit=args.deposit),
+        "data": "synthetic", "config": dict(config, deposit=args.deposit, schedule=schedule),
     }
     peak, peak_src = peaks()
     avg_s = statistics.mean(step_ms) / 1e3

@@ -409,6 +409,12 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     return cudaSuccess;
 }
 
+void set_schedule(Plan &p, int claim_div, int staging)
+{
+    p.args.claim_q = (float)(1.0 / ((double)std::max(1, claim_div) * p.grid * SIC_K1_WARPS));
+    p.args.staging = staging;
+}
+
 cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int record, cudaStream_t s)
 {
     LaunchArgs a = p.args;
@@ -1047,6 +1053,62 @@ int sic_batch_step(sic_batch *b, int32_t n_steps)
     }
     for (; left > 0; --left)
         CK(batch_launch(b));
+    return SIC_OK;
+}
+
+int sic_batch_autotune(sic_batch *b, int32_t steps_each, int32_t *claim_div, int32_t *staging)
+{
+    if (!b || steps_each < 1)
+        return SIC_EINVAL;
+    sic_sim *sim = b->sims[0];
+    // (claim divisor, staging): the default first
+    const int cand[][2] = {{4, 0}, {2, 0}, {8, 0}, {4, 1}, {4, 2}};
+    const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
+    if (b->gexec) {  // captured with the old arguments
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return SIC_ECUDA;
+    }
+    int best = 0;
+    float best_ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < n_cand && e == cudaSuccess; ++c) {
+        for (auto &p : b->plan)
+            if (p.mem)
+                set_schedule(p, cand[c][0], cand[c][1]);
+        e = batch_launch(b);  // settles caches and the function attributes
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev[0], b->stream);
+        for (int i = 0; i < steps_each && e == cudaSuccess; ++i)
+            e = batch_launch(b);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev[1], b->stream);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+            best = c;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess)
+        return fail_cuda(sim, e);
+    for (auto &p : b->plan)
+        if (p.mem)
+            set_schedule(p, cand[best][0], cand[best][1]);
+    if (claim_div)
+        *claim_div = cand[best][0];
+    if (staging)
+        *staging = cand[best][1];
     return SIC_OK;
 }
 

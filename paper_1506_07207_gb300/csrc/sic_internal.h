@@ -153,6 +153,8 @@ struct LaunchArgs {
     int32_t record;
     float kick_scale;
     int32_t gen;                 // some simulation deposits other than box particles
+    int32_t staging;             // 0: staged when it costs no resident block;
+                                 // 1: never; 2: whenever it fits (autotuning)
 };
 
 #include <cuda_runtime.h>

@@ -1641,10 +1641,16 @@ int64_t launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s)
 {
     switch (mode) {
-    case MODE_STEP:
-        if (step_staged(a.nx_max, per_q))
+    case MODE_STEP: {
+        bool staged = step_staged(a.nx_max, per_q);
+        if (a.staging == 1)
+            staged = false;
+        else if (a.staging == 2)
+            staged = step_smem_bytes(a.nx_max, true, per_q) <= 227 * 1024;
+        if (staged)
             return run_pd<true, true, true>(a, grid, per_q, pow2, s);
         return run_pd<true, true, false>(a, grid, per_q, pow2, s);
+    }
     case MODE_DEPOSIT:
         return run_pd<false, true, false>(a, grid, per_q, pow2, s);
     default:

@@ -32,7 +32,7 @@ EXPORTS = [
     "sic_batch_create", "sic_batch_step", "sic_batch_segments", "sic_batch_destroy",
     "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
     "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
-    "sic_step_batch_static", "sic_moments", "sic_refine", "sic_sheet_counts",
+    "sic_step_batch_static", "sic_moments", "sic_refine", "sic_sheet_counts", "sic_batch_autotune",
 ]
 
 
@@ -126,6 +126,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_step_batch_static": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_moments": ([simp, ctypes.c_int32, dp, dp], ctypes.c_int),
+        "sic_batch_autotune": ([vp, ctypes.c_int32, ip, ip], ctypes.c_int),
         "sic_refine": ([simp, ctypes.c_double, lp], ctypes.c_int),
         "sic_sheet_counts": ([simp, ip], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
@@ -396,6 +397,15 @@ class Batch:
 
     def sic_batch_step(self, n_steps):
         _check(_lib.sic_batch_step(self._h, int(n_steps)), "sic_batch_step")
+
+    def sic_batch_autotune(self, steps_each=3):
+        """Time the schedule candidates on real steps and keep the fastest;
+        advances every member by 5 (steps_each + 1) steps.  Returns
+        (claim divisor, staging)."""
+        d, st = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.sic_batch_autotune(self._h, int(steps_each), ctypes.byref(d), ctypes.byref(st)),
+               "sic_batch_autotune")
+        return d.value, st.value
 
     def sic_batch_segments(self):
         return int(_lib.sic_batch_segments(self._h))

@@ -340,3 +340,28 @@ def test_many_small_simulations_batch_equals_alone(sic):
     finally:
         for s in sims:
             s.sic_destroy()
+
+
+def test_autotuned_batch_equals_plain_batch(sic):
+    """The autotuner only changes the schedule: a batch tuned on its first
+    steps ends bit-identical to one stepped the same number of times."""
+    probs = [inputs.landau(0.1, 0.4, 128, 32, 3000, t_end=1.0),
+             inputs.two_stream(1.5, 0.2, 0.3, 512, 16, 5000, t_end=1.0),
+             inputs.tiny_problem(31, n_sheets=4, max_tracers=2000, nx=64, L=1.0)]
+    a = [sic.Sim.from_problem(p, history_len=8) for p in probs]
+    b = [sic.Sim.from_problem(p, history_len=8) for p in probs]
+    try:
+        ba, bb = sic.Batch(a), sic.Batch(b)
+        d, st = ba.sic_batch_autotune(2)
+        assert d in (2, 4, 8) and st in (0, 1, 2)
+        ba.sic_batch_step(9)                 # 5 * (2 + 1) + 9 = 24 steps in all
+        bb.sic_batch_step(24)
+        ba.sic_batch_destroy()
+        bb.sic_batch_destroy()
+        for s, t in zip(a, b):
+            assert s.sic_diagnostics()["step"] == t.sic_diagnostics()["step"] == 24
+            for u, w in zip(s.sic_get_state(), t.sic_get_state()):
+                np.testing.assert_array_equal(u, w)
+    finally:
+        for s in a + b:
+            s.sic_destroy()
