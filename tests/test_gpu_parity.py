@@ -365,3 +365,52 @@ def test_autotuned_batch_equals_plain_batch(sic):
     finally:
         for s in a + b:
             s.sic_destroy()
+
+
+def test_largest_mesh(sic):
+    """nx = SIC_NX_MAX (8192 cells): the largest shared-memory mesh (one block
+    per SM, unstaged), deposit and steps against the oracle."""
+    p = inputs.tiny_problem(77, n_sheets=4, max_tracers=20000, nx=sic.SIC_NX_MAX, L=3.0, spread=0.05)
+    sim = sic.Sim.from_problem(p, history_len=8)
+    try:
+        mesh, _, _ = _check_step_parity(sim, p)
+        q0 = sim.sic_diagnostics()["charge_fixed"]
+        sim.sic_step(4)
+        _check_step_parity(sim, p)
+        assert sim.sic_diagnostics()["charge_fixed"] == q0 == int(mesh.sum())
+    finally:
+        sim.sic_destroy()
+
+
+def test_serving_mix_full_size_batch(sic):
+    """The bench's launch configuration at full size: the 48 sampled requests
+    (282 M segments) resident in one batch.  Every simulation keeps its charge
+    to the unit; the largest and a mid-size one end bit-identical to running
+    alone; the mid-size one's deposit and field match the oracle."""
+    reqs = inputs.serving_mix(n_requests=48, seed=0x5EC5)
+    probs = [r.problem() for r in reqs]
+    sizes = np.array([p.n_segments for p in probs])
+    big = int(np.argmax(sizes))
+    mid = int(np.argmin(np.abs(sizes - (1 << 22))))
+    steps = 6
+    alone = {}
+    for k in (big, mid):
+        sim = sic.Sim.from_problem(probs[k], history_len=1)
+        sim.sic_step(steps)
+        alone[k] = sim.sic_deposit()[0]
+        sim.sic_destroy()
+    sims = [sic.Sim.from_problem(p, history_len=1) for p in probs]
+    try:
+        q0 = [s.sic_diagnostics()["charge_fixed"] for s in sims]
+        b = sic.Batch(sims)
+        b.sic_batch_step(steps)
+        b.sic_batch_destroy()
+        for s, q in zip(sims, q0):
+            d = s.sic_diagnostics()
+            assert d["step"] == steps and d["charge_fixed"] == q
+        for k in (big, mid):
+            np.testing.assert_array_equal(sims[k].sic_deposit()[0], alone[k])
+        _check_step_parity(sims[mid], probs[mid])
+    finally:
+        for s in sims:
+            s.sic_destroy()
