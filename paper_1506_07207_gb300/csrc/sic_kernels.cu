@@ -218,7 +218,10 @@ __device__ __forceinline__ void emit_cross(long long ua, int ja, long long ub, i
     maxseg = max(maxseg, (unsigned)min((unsigned long long)span >> 16, 0xffffffffull));
     const unsigned la = frac_of(ua);
     const float df = la ? __uint2float_rn(0u - la) : 4294967296.0f;  // a to the first edge
-    const float inv = __frcp_rn(span_to_float(span));
+    // an approximate reciprocal is enough: F is clamped to [0, q] and the
+    // other end takes q - F, so the charge stays exact
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(span_to_float(span)));
     int F = __float2int_rn(__fmul_rn(__fmul_rn(df, inv), __int2float_rn(q)));
     F = min(max(F, 0), q);
     const long long ncut = (long long)cell_of(ub) - (long long)cell_of(ua);
@@ -357,7 +360,7 @@ struct Acc128 {
     long long hi;
 };
 
-__device__ __noinline__ void acc_add_f32_wide(Acc128 &a, float x)
+__device__ __noinline__ Acc128 acc_add_f32_wide(Acc128 a, float x)
 {
     const unsigned b = __float_as_uint(x);
     const int e = (int)((b >> 23) & 0xffu);
@@ -375,26 +378,21 @@ __device__ __noinline__ void acc_add_f32_wide(Acc128 &a, float x)
         a.hi = a.hi + hi + (nlo < lo ? 1 : 0);
         a.lo = nlo;
     }
+    return a;
 }
 
 // Add x * 2^32, truncated to an integer, to the 128-bit sum: branch-free
 // for |x| < 2^31 (the common case), a call for larger values.
 __device__ __forceinline__ void acc_add_f32(Acc128 &a, float x)
 {
-    const unsigned b = __float_as_uint(x);
-    const int e = (int)((b >> 23) & 0xffu);
-    const int sh = e - 118;  // x * 2^32 = m * 2^(e - 150 + 32)
-    if (__builtin_expect(sh <= 39, 1)) {
-        const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
-        unsigned long long v = sh >= 0 ? (m << sh) : (m >> min(-sh, 63));
-        v = e ? v : 0ull;
-        const unsigned long long neg = (unsigned long long)((long long)(int)b >> 31);  // all ones if x < 0
-        const unsigned long long sv = (v ^ neg) - neg;                                 // +-v mod 2^64
-        const unsigned long long nlo = a.lo + sv;
-        a.hi += (long long)((v != 0ull) ? neg : 0ull) + (nlo < sv ? 1 : 0);
+    if (__builtin_expect(fabsf(x) < 2147483648.0f, 1)) {
+        // x * 2^32 is exact in FP32 and below 2^63: one truncating conversion
+        const long long v = __float2ll_rz(__fmul_rn(x, 4294967296.0f));
+        const unsigned long long nlo = a.lo + (unsigned long long)v;
+        a.hi += (v < 0 ? -1ll : 0ll) + (nlo < (unsigned long long)v ? 1 : 0);
         a.lo = nlo;
     } else {
-        acc_add_f32_wide(a, x);
+        a = acc_add_f32_wide(a, x);
     }
 }
 
@@ -497,6 +495,24 @@ struct WarpBuf {
     static constexpr int bytes = (STAGED ? 2 : 1) * stage;
 };
 
+// Lane 0 of a warp: copy a work item's descriptor into shared memory
+// without waiting for it (five 8-byte asynchronous copies, one group)
+__device__ __forceinline__ void desc_fetch(WorkItem *dst, const WorkItem *src)
+{
+    const unsigned d = smem_u32(dst);
+    unsigned long long g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 8 * k), "l"(g + 8 * k) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void desc_wait()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Lane 0 of a warp: start the bulk copies of item W (and its halo when the
 // halo is the next tracer in memory) into one stage.
 template <bool PER_Q>
@@ -517,6 +533,7 @@ __device__ __forceinline__ void stage_issue(const WorkItem &W, const long long *
 
 struct Shared {
     unsigned long long mbar[NW][2];
+    WorkItem desc[NW][2];    // staging: each warp's descriptors of the items in its two stages
     int diff_used;
     int last;
     long long pl_prev[NW];   // piecewise-linear particles: each warp's tracer before its item
@@ -732,14 +749,14 @@ __device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int 
 
 // One work item (up to 32 R tracers, R per lane) of the current simulation.
 // FULL: the item has all 32 R tracers, so no lane needs a bounds test.
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED, bool GEN>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED, bool GEN, class MID>
 __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
                                         const float *__restrict__ Vin, long long *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
                                         const float *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg,
-                                        const WorkItemPL *pw, int dep, int segq)
+                                        const WorkItemPL *pw, int dep, int segq, const MID &mid)
 {
     const long long *stU = reinterpret_cast<const long long *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
@@ -884,11 +901,11 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             longlong2 *pu = reinterpret_cast<longlong2 *>(Uout + base + l0);
 #pragma unroll
             for (int k = 0; k < R / 2; ++k)
-                pu[k] = make_longlong2(u[2 * k], u[2 * k + 1]);
+                __stcs(pu + k, make_longlong2(u[2 * k], u[2 * k + 1]));
             float4 *pv = reinterpret_cast<float4 *>(Vout + base + l0);
 #pragma unroll
             for (int k = 0; k < R / 4; ++k)
-                pv[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                __stcs(pv + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -906,6 +923,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         if (has_halo)
             hj = wrap_cell<POW2>(cell_of(hu), dv);
     }
+    mid();  // staging: the next item's copies start here
 
     // piecewise-linear particles (pw set): the tracer before the item and the
     // one after its halo too, for the gradients of the item's first and last
@@ -1088,18 +1106,20 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         }
 
         // cross-cell segments: compact them into a task list and let every
-        // lane take one in turn
+        // lane take one in turn; a lane's slot is the count before it, summed
+        // from one ballot per bit of the per-lane counts (0..R)
         const int cnt = __popc(cross);
-        int incl = cnt;
+        unsigned lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        int excl = 0, total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += t;
+        for (int bit = 0; (1 << bit) <= R; ++bit) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (cnt >> bit) & 1);
+            excl += __popc(bb & lt) << bit;
+            total += __popc(bb) << bit;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
         if (total) {
-            int pos = incl - cnt;
+            int pos = excl;
             while (cross) {
                 const int r = __ffs(cross) - 1;
                 tasks[pos++] = (unsigned short)(l0 + r);
@@ -1261,9 +1281,11 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
 
         // ---- each warp claims runs of consecutive items (guided: a claim is
         // the fraction claim_q of what it saw left, at least one item)
-        // and streams them through its two stages; the next run is claimed
-        // while the current one is processed, so its first copy can be issued
-        // before the current run's last item
+        // and streams them through its two stages.  A run's claim is made
+        // when the run before the previous one ends, so its result has had a
+        // whole run to arrive when it is needed.  With staging, an item's
+        // descriptor is copied into shared memory while the item before it is
+        // pushed, and its data copies start halfway through that item.
         const float q = A.claim_q;
         unsigned seen = 0, c_old = 0, c_want = 0;  // lane 0: cursor as last seen; claim in flight
         if (lane == 0)
@@ -1286,14 +1308,18 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         int a, n;
         claim_issue();
         claim_take(a, n);
+        claim_issue();  // the next run's claim, in flight through this run
         int count = 0;
         if (STAGED) {
-            if (n > 0 && !timed_out && lane == 0)
-                stage_issue<PER_Q>(items[a], Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
+            if (n > 0 && !timed_out && lane == 0) {
+                desc_fetch(&sh.desc[warp][s], items + a);
+                desc_wait();
+                stage_issue<PER_Q>(sh.desc[warp][s], Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
                                    &sh.mbar[warp][s]);
+            }
+            __syncwarp();
         }
         while (n > 0) {
-            claim_issue();  // the next run, taken at this run's last item
             int na = 0, nn = 0;
             bool took = false;
             count += n;
@@ -1301,50 +1327,68 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 int nxt = i + 1;
                 if (nxt == a + n) {
                     claim_take(na, nn);
+                    claim_issue();  // the run after it, in flight through the next run
                     took = true;
                     nxt = nn > 0 ? na : -1;
                 }
-                const WorkItem W = items[i];
+                if (!STAGED && lane == 0 && i + 2 < a + n) {
+                    // lane 0 reads the next descriptor to start its copies:
+                    // fetch the one after it into L1 now (both of its sectors),
+                    // so that read does not wait on L2
+                    const char *pf = reinterpret_cast<const char *>(items + i + 2);
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(pf));
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(pf + sizeof(WorkItem) - 1));
+                }
+                const WorkItem W = STAGED ? sh.desc[warp][s] : items[i];
                 const WorkItemPL *plw = (GEN && S.pl != nullptr) ? S.pl + i : nullptr;
                 if (STAGED) {
+                    // the next item's descriptor comes in while this one is
+                    // pushed; its copies start halfway through this item
                     if (nxt >= 0 && lane == 0)
-                        stage_issue<PER_Q>(items[nxt], Uin, Vin, Qh, my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage,
-                                           &sh.mbar[warp][s ^ 1]);
+                        desc_fetch(&sh.desc[warp][s ^ 1], items + nxt);
                     const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
                     phase ^= 1u << s;
                     if (!__all_sync(0xffffffffu, ok)) {
-                        // give up: let the copy in flight land, then only count items
+                        // give up (the next item's copies have not started): only count items
                         timed_out = true;
-                        if (nxt >= 0) {
-                            mbar_wait_bounded(&sh.mbar[warp][s ^ 1], (phase >> (s ^ 1)) & 1u);
-                            phase ^= 1u << (s ^ 1);
-                        }
+                        if (nxt >= 0 && lane == 0)
+                            desc_wait();
                         break;
                     }
+                    auto mid = [&]() {
+                        if (nxt >= 0 && lane == 0) {
+                            desc_wait();
+                            stage_issue<PER_Q>(sh.desc[warp][s ^ 1], Uin, Vin, Qh,
+                                               my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage, &sh.mbar[warp][s ^ 1]);
+                        }
+                    };
                     char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
                     if (W.count == WT)
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                         sh, dv, ks, drift, rerr, st, tasks, ake, ap,
-                                                                        mseg, plw, S.deposit, S.seg_q);
+                                                                        mseg, plw, S.deposit, S.seg_q, mid);
                     else
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                          diff, sh, dv, ks, drift, rerr, st, tasks,
-                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q);
+                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q, mid);
                     __syncwarp();
                     s ^= 1;
                 } else {
+                    auto mid = []() {};
                     if (W.count == WT)
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
                                                                          sh, dv, ks, drift, rerr, my_stage, tasks,
-                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q);
+                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q, mid);
                     else
                         do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
                                                                           diff, sh, dv, ks, drift, rerr, my_stage,
-                                                                          tasks, ake, ap, mseg, plw, S.deposit, S.seg_q);
+                                                                          tasks, ake, ap, mseg, plw, S.deposit, S.seg_q, mid);
                 }
             }
-            if (!took)
+            if (!took) {
                 claim_take(na, nn);
+                claim_issue();
+            }
             a = na;
             n = nn;
         }
