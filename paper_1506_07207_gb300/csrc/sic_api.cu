@@ -398,6 +398,7 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     p.args.done = (unsigned *)(b + oK) + 2 * n;
     p.args.n_items = (int32_t)n_items;
     p.args.claim_q = claim_q;
+    p.args.claim_min = 1;
     p.args.n_slots = n;
     p.args.nx_max = nx_max;
     p.args.gen = 0;
@@ -409,10 +410,11 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     return cudaSuccess;
 }
 
-void set_schedule(Plan &p, int claim_div, int staging)
+void set_schedule(Plan &p, int claim_div, int staging, int claim_min)
 {
     p.args.claim_q = (float)(1.0 / ((double)std::max(1, claim_div) * p.grid * SIC_K1_WARPS));
     p.args.staging = staging;
+    p.args.claim_min = std::max(1, claim_min);
 }
 
 cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int record, cudaStream_t s)
@@ -1056,13 +1058,15 @@ int sic_batch_step(sic_batch *b, int32_t n_steps)
     return SIC_OK;
 }
 
-int sic_batch_autotune(sic_batch *b, int32_t steps_each, int32_t *claim_div, int32_t *staging)
+int sic_batch_autotune(sic_batch *b, int32_t steps_each, int32_t *claim_div, int32_t *staging,
+                       int32_t *claim_min)
 {
     if (!b || steps_each < 1)
         return SIC_EINVAL;
     sic_sim *sim = b->sims[0];
-    // (claim divisor, staging): the default first
-    const int cand[][2] = {{4, 0}, {2, 0}, {8, 0}, {4, 1}, {4, 2}};
+    // (claim divisor, staging, smallest claim): the default first
+    const int cand[SIC_AUTOTUNE_CANDIDATES][3] = {{4, 0, 1}, {2, 0, 1}, {8, 0, 1}, {4, 1, 1},
+                                                  {4, 2, 1}, {2, 0, 2}, {4, 0, 2}, {2, 0, 4}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
     if (b->gexec) {  // captured with the old arguments
         cudaGraphExecDestroy(b->gexec);
@@ -1080,7 +1084,7 @@ int sic_batch_autotune(sic_batch *b, int32_t steps_each, int32_t *claim_div, int
     for (int c = 0; c < n_cand && e == cudaSuccess; ++c) {
         for (auto &p : b->plan)
             if (p.mem)
-                set_schedule(p, cand[c][0], cand[c][1]);
+                set_schedule(p, cand[c][0], cand[c][1], cand[c][2]);
         e = batch_launch(b);  // settles caches and the function attributes
         if (e == cudaSuccess)
             e = cudaEventRecord(ev[0], b->stream);
@@ -1104,11 +1108,13 @@ int sic_batch_autotune(sic_batch *b, int32_t steps_each, int32_t *claim_div, int
         return fail_cuda(sim, e);
     for (auto &p : b->plan)
         if (p.mem)
-            set_schedule(p, cand[best][0], cand[best][1]);
+            set_schedule(p, cand[best][0], cand[best][1], cand[best][2]);
     if (claim_div)
         *claim_div = cand[best][0];
     if (staging)
         *staging = cand[best][1];
+    if (claim_min)
+        *claim_min = cand[best][2];
     return SIC_OK;
 }
 
@@ -1365,6 +1371,7 @@ cudaError_t static_plan(unsigned char *region, sic_sim *const *grp, int n, cudaS
     a.done = reinterpret_cast<unsigned *>(ctr) + 2 * n;
     a.n_items = (int32_t)n_items;
     a.claim_q = (float)(1.0 / ((double)env_int("SIC_CLAIM_DIV", 4) * grid * SIC_K1_WARPS));
+    a.claim_min = 1;
     a.n_slots = n;
     a.nx_max = nx_max;
     a.drift = 1;

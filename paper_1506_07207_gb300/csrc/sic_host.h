@@ -67,7 +67,7 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s);
 // Scheduling knobs of a built plan (results do not depend on them): the claim
 // divisor D (a claim takes 1 / (D warps) of what is left) and the staging
 // choice (LaunchArgs::staging).
-void set_schedule(Plan &p, int claim_div, int staging);
+void set_schedule(Plan &p, int claim_div, int staging, int claim_min);
 void free_plan(Plan &p, cudaStream_t s);
 cudaError_t launch(const Plan &p, sic::Mode mode, float kick_scale, int drift, int record, cudaStream_t s);
 }  // namespace sic_host

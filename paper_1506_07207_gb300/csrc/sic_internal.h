@@ -147,6 +147,7 @@ struct LaunchArgs {
     int32_t n_items;             // slot_begin[slots]
     float claim_q;               // a claim takes this fraction of the items a
                                  // simulation has left (guided scheduling)
+    int32_t claim_min;           // and at least this many (>= 1)
     int32_t n_slots;
     int32_t nx_max;
     int32_t drift;

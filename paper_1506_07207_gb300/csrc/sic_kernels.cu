@@ -533,7 +533,9 @@ __device__ __forceinline__ void stage_issue(const WorkItem &W, const long long *
 
 struct Shared {
     unsigned long long mbar[NW][2];
-    WorkItem desc[NW][2];    // staging: each warp's descriptors of the items in its two stages
+    struct alignas(16) Slot {
+        WorkItem w;
+    } desc[NW][2];  // staging: each warp's descriptors of the items in its two stages
     int diff_used;
     int last;
     long long pl_prev[NW];   // piecewise-linear particles: each warp's tracer before its item
@@ -1213,7 +1215,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float ks = A.kick_scale;
-    const int drift = A.drift;
+    const int drift = (PUSH && DEPOSIT) ? 1 : A.drift;  // a full step always drifts
     char *my_stage = stage_base + (size_t)warp * WarpBuf<PER_Q, STAGED>::bytes;
     unsigned short *tasks =
         reinterpret_cast<unsigned short *>(stage_base + (size_t)NW * WarpBuf<PER_Q, STAGED>::bytes) + warp * WT;
@@ -1280,20 +1282,21 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         __syncthreads();
 
         // ---- each warp claims runs of consecutive items (guided: a claim is
-        // the fraction claim_q of what it saw left, at least one item)
+        // the fraction claim_q of what it saw left, at least claim_min items)
         // and streams them through its two stages.  A run's claim is made
         // when the run before the previous one ends, so its result has had a
         // whole run to arrive when it is needed.  With staging, an item's
         // descriptor is copied into shared memory while the item before it is
         // pushed, and its data copies start halfway through that item.
         const float q = A.claim_q;
+        const int claim_min = max(1, A.claim_min);
         unsigned seen = 0, c_old = 0, c_want = 0;  // lane 0: cursor as last seen; claim in flight
         if (lane == 0)
             seen = *(volatile unsigned *)cursor;
         auto claim_issue = [&]() {
             if (lane == 0) {
                 const int left = n_s - (int)min(seen, (unsigned)n_s);
-                c_want = left > 0 ? (unsigned)max(1, (int)((float)left * q)) : 0u;
+                c_want = left > 0 ? (unsigned)max(claim_min, (int)((float)left * q)) : 0u;
                 c_old = c_want ? atomicAdd(cursor, c_want) : (unsigned)n_s;
             }
         };
@@ -1312,9 +1315,9 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         int count = 0;
         if (STAGED) {
             if (n > 0 && !timed_out && lane == 0) {
-                desc_fetch(&sh.desc[warp][s], items + a);
+                desc_fetch(&sh.desc[warp][s].w, items + a);
                 desc_wait();
-                stage_issue<PER_Q>(sh.desc[warp][s], Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
+                stage_issue<PER_Q>(sh.desc[warp][s].w, Uin, Vin, Qh, my_stage + s * WarpBuf<PER_Q, true>::stage,
                                    &sh.mbar[warp][s]);
             }
             __syncwarp();
@@ -1339,13 +1342,13 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(pf));
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(pf + sizeof(WorkItem) - 1));
                 }
-                const WorkItem W = STAGED ? sh.desc[warp][s] : items[i];
+                const WorkItem W = STAGED ? sh.desc[warp][s].w : items[i];
                 const WorkItemPL *plw = (GEN && S.pl != nullptr) ? S.pl + i : nullptr;
                 if (STAGED) {
                     // the next item's descriptor comes in while this one is
                     // pushed; its copies start halfway through this item
                     if (nxt >= 0 && lane == 0)
-                        desc_fetch(&sh.desc[warp][s ^ 1], items + nxt);
+                        desc_fetch(&sh.desc[warp][s ^ 1].w, items + nxt);
                     const bool ok = mbar_wait_bounded(&sh.mbar[warp][s], (phase >> s) & 1u);
                     phase ^= 1u << s;
                     if (!__all_sync(0xffffffffu, ok)) {
@@ -1358,7 +1361,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     auto mid = [&]() {
                         if (nxt >= 0 && lane == 0) {
                             desc_wait();
-                            stage_issue<PER_Q>(sh.desc[warp][s ^ 1], Uin, Vin, Qh,
+                            stage_issue<PER_Q>(sh.desc[warp][s ^ 1].w, Uin, Vin, Qh,
                                                my_stage + (s ^ 1) * WarpBuf<PER_Q, true>::stage, &sh.mbar[warp][s ^ 1]);
                         }
                     };

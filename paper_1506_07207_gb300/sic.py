@@ -126,7 +126,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_step_batch_static": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_moments": ([simp, ctypes.c_int32, dp, dp], ctypes.c_int),
-        "sic_batch_autotune": ([vp, ctypes.c_int32, ip, ip], ctypes.c_int),
+        "sic_batch_autotune": ([vp, ctypes.c_int32, ip, ip, ip], ctypes.c_int),
         "sic_refine": ([simp, ctypes.c_double, lp], ctypes.c_int),
         "sic_sheet_counts": ([simp, ip], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
@@ -371,6 +371,7 @@ def sic_step_batch(sims, n_steps):
 
 
 SIC_STATIC_MAX_SIMS = 64
+SIC_AUTOTUNE_CANDIDATES = 8
 SIC_DEPOSIT_BOX, SIC_DEPOSIT_LINEAR, SIC_DEPOSIT_PIC_NGP, SIC_DEPOSIT_PIC_CIC = 0, 1, 2, 3
 
 
@@ -400,12 +401,12 @@ class Batch:
 
     def sic_batch_autotune(self, steps_each=3):
         """Time the schedule candidates on real steps and keep the fastest;
-        advances every member by 5 (steps_each + 1) steps.  Returns
-        (claim divisor, staging)."""
-        d, st = ctypes.c_int32(), ctypes.c_int32()
-        _check(_lib.sic_batch_autotune(self._h, int(steps_each), ctypes.byref(d), ctypes.byref(st)),
-               "sic_batch_autotune")
-        return d.value, st.value
+        advances every member by SIC_AUTOTUNE_CANDIDATES (steps_each + 1)
+        steps.  Returns (claim divisor, staging, smallest claim)."""
+        d, st, mn = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.sic_batch_autotune(self._h, int(steps_each), ctypes.byref(d), ctypes.byref(st),
+                                       ctypes.byref(mn)), "sic_batch_autotune")
+        return d.value, st.value, mn.value
 
     def sic_batch_segments(self):
         return int(_lib.sic_batch_segments(self._h))

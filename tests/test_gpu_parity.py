@@ -352,14 +352,15 @@ def test_autotuned_batch_equals_plain_batch(sic):
     b = [sic.Sim.from_problem(p, history_len=8) for p in probs]
     try:
         ba, bb = sic.Batch(a), sic.Batch(b)
-        d, st = ba.sic_batch_autotune(2)
-        assert d in (2, 4, 8) and st in (0, 1, 2)
-        ba.sic_batch_step(9)                 # 5 * (2 + 1) + 9 = 24 steps in all
-        bb.sic_batch_step(24)
+        d, st, mn = ba.sic_batch_autotune(2)
+        assert d in (2, 4, 8) and st in (0, 1, 2) and mn in (1, 2, 4)
+        n_tuned = sic.SIC_AUTOTUNE_CANDIDATES * (2 + 1)
+        ba.sic_batch_step(30 - n_tuned)
+        bb.sic_batch_step(30)
         ba.sic_batch_destroy()
         bb.sic_batch_destroy()
         for s, t in zip(a, b):
-            assert s.sic_diagnostics()["step"] == t.sic_diagnostics()["step"] == 24
+            assert s.sic_diagnostics()["step"] == t.sic_diagnostics()["step"] == 30
             for u, w in zip(s.sic_get_state(), t.sic_get_state()):
                 np.testing.assert_array_equal(u, w)
     finally:
