@@ -332,7 +332,7 @@ def main():
         batch.sic_batch_step(1)
     schedule = None
     if args.autotune:
-        d, st, mn = batch.sic_batch_autotune(3)   # untimed: 32 more warm-up steps
+        d, st, mn = batch.sic_batch_autotune(3)   # untimed: 40 more warm-up steps
         schedule = {"claim_divisor": d, "staging": ["auto", "off", "on"][st], "claim_min": mn}
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]

@@ -211,7 +211,7 @@ int sic_batch_create(sic_sim *const *sims, int32_t n_sims, sic_batch **out);
 int sic_batch_step(sic_batch *batch, int32_t n_steps);
 /*
  * Autotuning of the batch's launch schedule: each of SIC_AUTOTUNE_CANDIDATES
- * candidates (claim divisor D = 2, 4 or 8 for the guided claims of work
+ * candidates (claim divisor D = 1, 2, 4 or 8 for the guided claims of work
  * items, a warp claiming about 1 / (D x warps) of what is left; the smallest
  * claim, 1, 2 or 4 items; staging of the items through shared memory
  * automatic, off, or on whenever it fits) is timed with CUDA events on
@@ -222,7 +222,7 @@ int sic_batch_step(sic_batch *batch, int32_t n_steps);
  * (steps_each + 1) steps.  *claim_div, *staging and *claim_min (nullable)
  * get the choice (staging: 0 automatic, 1 off, 2 on).  steps_each >= 1.
  */
-#define SIC_AUTOTUNE_CANDIDATES 8
+#define SIC_AUTOTUNE_CANDIDATES 10
 int sic_batch_autotune(sic_batch *batch, int32_t steps_each, int32_t *claim_div, int32_t *staging,
                        int32_t *claim_min);
 

@@ -1065,8 +1065,8 @@ int sic_batch_autotune(sic_batch *b, int32_t steps_each, int32_t *claim_div, int
         return SIC_EINVAL;
     sic_sim *sim = b->sims[0];
     // (claim divisor, staging, smallest claim): the default first
-    const int cand[SIC_AUTOTUNE_CANDIDATES][3] = {{4, 0, 1}, {2, 0, 1}, {8, 0, 1}, {4, 1, 1},
-                                                  {4, 2, 1}, {2, 0, 2}, {4, 0, 2}, {2, 0, 4}};
+    const int cand[SIC_AUTOTUNE_CANDIDATES][3] = {{4, 0, 1}, {2, 0, 1}, {8, 0, 1}, {4, 1, 1}, {4, 2, 1},
+                                                  {2, 0, 2}, {4, 0, 2}, {2, 0, 4}, {1, 0, 4}, {1, 0, 2}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
     if (b->gexec) {  // captured with the old arguments
         cudaGraphExecDestroy(b->gexec);

@@ -1109,16 +1109,18 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
 
         // cross-cell segments: compact them into a task list and let every
         // lane take one in turn; a lane's slot is the count before it, summed
-        // from one ballot per bit of the per-lane counts (0..R)
+        // from one ballot per bit of the per-lane counts (0..R) when there are any
         const int cnt = __popc(cross);
         unsigned lt;
         asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-        int excl = 0, total = 0;
+        const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);  // tasks of the warp
+        int excl = 0;
+        if (total) {
 #pragma unroll
-        for (int bit = 0; (1 << bit) <= R; ++bit) {
-            const unsigned bb = __ballot_sync(0xffffffffu, (cnt >> bit) & 1);
-            excl += __popc(bb & lt) << bit;
-            total += __popc(bb) << bit;
+            for (int bit = 0; (1 << bit) <= R; ++bit) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (cnt >> bit) & 1);
+                excl += __popc(bb & lt) << bit;
+            }
         }
         if (total) {
             int pos = excl;

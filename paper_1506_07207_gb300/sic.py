@@ -371,7 +371,7 @@ def sic_step_batch(sims, n_steps):
 
 
 SIC_STATIC_MAX_SIMS = 64
-SIC_AUTOTUNE_CANDIDATES = 8
+SIC_AUTOTUNE_CANDIDATES = 10
 SIC_DEPOSIT_BOX, SIC_DEPOSIT_LINEAR, SIC_DEPOSIT_PIC_NGP, SIC_DEPOSIT_PIC_CIC = 0, 1, 2, 3
 
 
