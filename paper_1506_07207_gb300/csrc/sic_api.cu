@@ -146,11 +146,12 @@ void plan_items(sic_sim *sim)
         const int n = sim->counts[s];
         for (int k = 0; k * item < n; ++k) {
             WorkItem w{};
-            w.sim = 0;
-            w.local = (int)sim->items.size();
             w.t0 = sim->sheet_off[s] + (int64_t)k * item;
             w.count = std::min(item, n - k * item);
             w.qh = sim->per_q ? 0 : sim->sheet_qh[s];
+            const float qq = sim->per_q ? 1.0f : (float)w.qh;  // rounded as the kernel did
+            w.ke_mult = std::ldexp(qq, sim->h.ke_u);
+            w.p_mult = std::ldexp(qq, sim->h.p_u);
             const bool last = (k + 1) * item >= n;
             if (!last) {
                 w.halo = w.t0 + w.count;
@@ -278,6 +279,23 @@ int setup(sic_sim *sim, const sic_config *cfg)
     } else {
         CK(cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking));
         sim->own_stream = true;
+    }
+    // fixed-point units of the lanes' KE and P sums: an item's term (R tracers,
+    // old and new velocity, at most the largest half charge, velocities up to
+    // 4 times the largest at creation) comes to about 2^44 units, so a lane's
+    // 64-bit sum has room for 2^19 items before it spills into the block's
+    // 128-bit sum; the unit is never finer than 2^-32
+    {
+        SimDev &h = sim->h;
+        const double qh_max = std::max(1.0, sim->w_max * sim->sigma * 0.5);
+        const double vb = 4.0 * sim->v_max;
+        auto unit_exp = [](double bound) {
+            if (!(bound > 0.0))
+                return 32;
+            return std::max(-40, std::min(32, (int)std::floor(44.0 - std::log2(bound))));
+        };
+        h.ke_u = unit_exp(qh_max * 2.0 * SIC_K1_R * vb * vb);
+        h.p_u = unit_exp(qh_max * 2.0 * SIC_K1_R * vb);
     }
     plan_items(sim);
     const int n_items = (int)sim->items.size();
@@ -485,7 +503,7 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
     int64_t n = 0;
     for (int s = 0; s < cfg->n_sheets; ++s)
         n += cfg->tracers_per_sheet[s];
-    double max_w = 0;
+    double max_w = 0, max_v = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (!is_finite(x_host[i]) || !is_finite(v_host[i]) || !is_finite(w_host[i]) || w_host[i] <= 0)
             return SIC_EINVAL;
@@ -494,10 +512,13 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
         if (std::fabs(v_host[i] * cfg->dt / dx) >= (double)(1 << 20))
             return SIC_EINVAL;
         max_w = std::max(max_w, w_host[i]);
+        max_v = std::max(max_v, std::fabs(v_host[i] * cfg->dt / dx));
     }
     sic_sim *sim = new (std::nothrow) sic_sim;
     if (!sim)
         return SIC_ENOMEM;
+    sim->v_max = max_v;
+    sim->w_max = max_w;
     sim->M = cfg->n_sheets;
     sim->counts.assign(cfg->tracers_per_sheet, cfg->tracers_per_sheet + sim->M);
     sim->closed.assign(cfg->sheet_closed, cfg->sheet_closed + sim->M);
@@ -592,17 +613,20 @@ int sic_create_horizontal(const sic_config *cfg, int32_t n_template, const doubl
         if (std::fabs(x_template_host[i] / dx) >= (double)(1 << 29))
             return SIC_ERANGE;
     }
-    double max_w = 0;
+    double max_w = 0, max_v = 0;
     for (int s = 0; s < cfg->n_sheets; ++s) {
         if (!is_finite(v_sheet_host[s]) || !is_finite(w_sheet_host[s]) || w_sheet_host[s] <= 0)
             return SIC_EINVAL;
         if (std::fabs(v_sheet_host[s] * cfg->dt / dx) >= (double)(1 << 20))
             return SIC_EINVAL;
         max_w = std::max(max_w, w_sheet_host[s]);
+        max_v = std::max(max_v, std::fabs(v_sheet_host[s] * cfg->dt / dx));
     }
     sic_sim *sim = new (std::nothrow) sic_sim;
     if (!sim)
         return SIC_ENOMEM;
+    sim->v_max = max_v;
+    sim->w_max = max_w;
     sim->M = cfg->n_sheets;
     sim->counts.assign(sim->M, n_template);
     sim->closed.assign(sim->M, 1);

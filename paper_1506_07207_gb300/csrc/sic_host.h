@@ -47,6 +47,8 @@ struct sic_sim {
     std::vector<int32_t> sheet_qh;
     int64_t n_tracers = 0, n_alloc = 0;
     double sigma = 1.0;
+    double v_max = 0.0;               // largest |v| at creation, cells per step
+    double w_max = 0.0;               // largest weight at creation
     std::vector<WorkItem> items;
     int deposit = SIC_DEPOSIT_BOX;    // SIC_DEPOSIT_*
     bool seg_q = false;               // refined: Qh holds per-particle charges

@@ -62,8 +62,8 @@ struct NxDiv {
 
 // One work item, the task of one warp: up to 32 R consecutive tracers of one sheet.
 struct WorkItem {
-    int32_t sim;        // slot in the launch's simulation table
-    int32_t local;      // index of the item inside its simulation
+    float ke_mult;      // the item's KE and P terms are multiplied by these:
+    float p_mult;       // the sheet half charge (1 with a Qh array) x 2^ke_u, 2^p_u
     int64_t t0;         // first tracer (aligned to SIC_ALIGN_TRACERS)
     int32_t count;      // tracers, 1..SIC_K1_WARP_TRACERS
     int32_t qh;         // sheet half charge when the simulation has no Qh array
@@ -85,12 +85,13 @@ struct WorkItemPL {
 };
 
 // Per-step sums every block adds into and the epilogue reads: the kinetic
-// energy and momentum terms as 128-bit fixed-point integers (2^-32 units,
-// each item's FP32 partial converted exactly), so the totals do not depend
-// on the order of the additions; the longest segment by atomicMax.
+// energy and momentum terms as 128-bit fixed-point integers (units of
+// 2^-ke_u and 2^-p_u set per simulation, each item's FP32 partial truncated
+// to them), so the totals do not depend on the order of the additions; the
+// longest segment by atomicMax.
 struct SimAccum {
-    unsigned long long ke[2];   // sum Qh (v_old^2 + v_new^2)  ((cells/step)^2), lo/hi
-    unsigned long long p[2];    // sum Qh (v_old + v_new)                      , lo/hi
+    unsigned long long ke[2];   // sum Qh (v_old^2 + v_new^2)  ((cells/step)^2 2^-ke_u), lo/hi
+    unsigned long long p[2];    // sum Qh (v_old + v_new)  (cells/step 2^-p_u)     , lo/hi
     unsigned long long maxseg;  // longest segment crossing a cell edge, 2^-16 cells
     unsigned long long pad[3];
 };
@@ -130,8 +131,9 @@ struct SimDev {
     double we_scale;            // W_E = we_scale * sum (K_j 2^-60)^2
     float ek_mant;              // e_scale = ek_mant * 2^ek_exp
     int32_t ek_exp;
-    double ke_scale;            // KE = ke_scale * sum ke
-    double p_scale;             // P  = p_scale * sum p
+    double ke_scale;            // KE = ke_scale * sum ke 2^-ke_u
+    double p_scale;             // P  = p_scale * sum p 2^-p_u
+    int32_t ke_u, p_u;          // the sums count units of 2^-ke_u and 2^-p_u
     int32_t strict;
     int32_t pow2;               // nx is a power of two
 };

@@ -353,48 +353,11 @@ __device__ __forceinline__ void emit_linear_warp(long long ua, int ja, long long
     }
 }
 
-// A 128-bit fixed-point sum (2^-32 units) held in registers; adding the
-// same FP32 values in any order gives the same bits.
+// A 128-bit integer as two words (the warp's and block's fixed-point sums).
 struct Acc128 {
     unsigned long long lo;
     long long hi;
 };
-
-__device__ __noinline__ Acc128 acc_add_f32_wide(Acc128 a, float x)
-{
-    const unsigned b = __float_as_uint(x);
-    const int e = (int)((b >> 23) & 0xffu);
-    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
-    const int sh = e - 118;
-    const __int128 t = sh > 100 ? ((__int128)1 << 124) : ((__int128)m << sh);
-    const unsigned long long lo = (unsigned long long)t;
-    const long long hi = (long long)(t >> 64);
-    if (b >> 31) {
-        const unsigned long long nlo = a.lo - lo;
-        a.hi = a.hi - hi - (a.lo < lo ? 1 : 0);
-        a.lo = nlo;
-    } else {
-        const unsigned long long nlo = a.lo + lo;
-        a.hi = a.hi + hi + (nlo < lo ? 1 : 0);
-        a.lo = nlo;
-    }
-    return a;
-}
-
-// Add x * 2^32, truncated to an integer, to the 128-bit sum: branch-free
-// for |x| < 2^31 (the common case), a call for larger values.
-__device__ __forceinline__ void acc_add_f32(Acc128 &a, float x)
-{
-    if (__builtin_expect(fabsf(x) < 2147483648.0f, 1)) {
-        // x * 2^32 is exact in FP32 and below 2^63: one truncating conversion
-        const long long v = __float2ll_rz(__fmul_rn(x, 4294967296.0f));
-        const unsigned long long nlo = a.lo + (unsigned long long)v;
-        a.hi += (v < 0 ? -1ll : 0ll) + (nlo < (unsigned long long)v ? 1 : 0);
-        a.lo = nlo;
-    } else {
-        a = acc_add_f32_wide(a, x);
-    }
-}
 
 __device__ __forceinline__ void acc_add(Acc128 &a, const Acc128 &b)
 {
@@ -426,6 +389,47 @@ __device__ __forceinline__ void atomic_add_i128(unsigned long long *lohi, __int1
     const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
     if (hi + carry)
         atomicAdd(lohi + 1, hi + carry);
+}
+
+struct Spill {
+    long long a;
+    unsigned err;
+};
+
+// The rare path of sum_add: the lane's sum goes into the block's 128-bit sum
+// (shared memory), and so does the term y unless it fits a fresh 64-bit sum.
+// y is integer-valued when it is 2^63 or more (below 2^124; inf, NaN or
+// larger set bit 31 of the error word instead).
+__device__ __noinline__ Spill acc_spill(long long a, float y, unsigned long long *blk)
+{
+    atomic_add_i128(blk, (__int128)a);
+    if (fabsf(y) < 9223372036854775808.0f)
+        return Spill{__float2ll_rz(y), 0u};
+    const unsigned b = __float_as_uint(y);
+    const int sh = (int)((b >> 23) & 0xffu) - 150;  // y = m 2^sh, sh >= 40 here
+    if (sh > 100)
+        return Spill{0, 0x80000000u};
+    const __int128 m = (__int128)((b & 0x7fffffu) | 0x800000u) << sh;
+    atomic_add_i128(blk, (b >> 31) ? -m : m);
+    return Spill{0, 0u};
+}
+
+// Add y (a term already in the sum's fixed-point unit), truncated to an
+// integer, to a lane's 64-bit sum.  A term of 2^62 or more, or one that
+// would overflow the sum, takes the rare path, which moves the lane's sum
+// into the block's 128-bit sum: the total stays exact, so it does not
+// depend on the order of the additions.
+__device__ __forceinline__ void sum_add(long long &a, float y, unsigned long long *blk, unsigned &err)
+{
+    const long long v = __float2ll_rz(y);
+    const long long s = (long long)((unsigned long long)a + (unsigned long long)v);
+    if (__builtin_expect(!(fabsf(y) < 4611686018427387904.0f) || ((a ^ s) & (v ^ s)) < 0, 0)) {
+        const Spill r = acc_spill(a, y, blk);
+        a = r.a;
+        err |= r.err;
+    } else {
+        a = s;
+    }
 }
 
 __device__ __forceinline__ double i128_words_to_double(unsigned long long lo, unsigned long long hi)
@@ -696,8 +700,8 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         for (int i = 0; i < NW; ++i)
             w += sh.da[i];
         SimAccum *ac = S.acc;
-        const double kk = i128_words_to_double(__ldcg(&ac->ke[0]), __ldcg(&ac->ke[1])) * 2.3283064365386963e-10;
-        const double pp = i128_words_to_double(__ldcg(&ac->p[0]), __ldcg(&ac->p[1])) * 2.3283064365386963e-10;
+        const double kk = ldexp(i128_words_to_double(__ldcg(&ac->ke[0]), __ldcg(&ac->ke[1])), -S.ke_u);
+        const double pp = ldexp(i128_words_to_double(__ldcg(&ac->p[0]), __ldcg(&ac->p[1])), -S.p_u);
         const long long mm = (long long)__ldcg(&ac->maxseg);
         ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
         SimScalars *sc = S.sc;
@@ -757,7 +761,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
                                         const float *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
-                                        char *st, unsigned short *tasks, Acc128 &ake, Acc128 &ap, unsigned &mseg,
+                                        char *st, unsigned short *tasks, long long &ake, long long &ap, unsigned &mseg,
                                         const WorkItemPL *pw, int dep, int segq, const MID &mid)
 {
     const long long *stU = reinterpret_cast<const long long *>(st);
@@ -1188,16 +1192,13 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         __syncwarp();  // pts and tasks are rewritten by the next item
     }
 
-    // this lane's kinetic-energy and momentum terms, added exactly into its
-    // 128-bit registers (summed over the warp when the run ends)
+    // this lane's kinetic-energy and momentum terms (times the sheet's half
+    // charge, unless the tracers carry their own, and in the sums' fixed-point
+    // units), added exactly to its running sums (summed over the warp when it
+    // leaves the simulation)
     if (PUSH) {
-        if (!PER_Q) {
-            const float qq = __int2float_rn(W.qh);
-            acc_a = __fmul_rn(acc_a, qq);
-            acc_b = __fmul_rn(acc_b, qq);
-        }
-        acc_add_f32(ake, acc_a);
-        acc_add_f32(ap, acc_b);
+        sum_add(ake, __fmul_rn(acc_a, W.ke_mult), sh.ke, rerr);
+        sum_add(ap, __fmul_rn(acc_b, W.p_mult), sh.p, rerr);
     }
 }
 
@@ -1246,7 +1247,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         cur = lo;
     }
     unsigned rerr = 0, mseg = 0;
-    Acc128 ake{0ull, 0ll}, ap{0ull, 0ll};
+    long long ake = 0, ap = 0;  // this lane's KE and P sums (units 2^-ke_u, 2^-p_u)
 
     while (cur >= 0) {
         // ---- enter simulation cur
@@ -1403,13 +1404,14 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         // ---- leave: fold the block's mesh and sums into the simulation's,
         // take an item ticket, run the field epilogue if it completes it
         if (PUSH) {
-            const Acc128 k2 = acc_warp_sum(ake), p2 = acc_warp_sum(ap);
+            const Acc128 k2 = acc_warp_sum(Acc128{(unsigned long long)ake, ake >> 63});
+            const Acc128 p2 = acc_warp_sum(Acc128{(unsigned long long)ap, ap >> 63});
             if (lane == 0) {
                 atomic_add_i128(sh.ke, (__int128)(((unsigned __int128)(unsigned long long)k2.hi << 64) | k2.lo));
                 atomic_add_i128(sh.p, (__int128)(((unsigned __int128)(unsigned long long)p2.hi << 64) | p2.lo));
             }
-            ake = Acc128{0ull, 0ll};
-            ap = Acc128{0ull, 0ll};
+            ake = 0;
+            ap = 0;
         }
         if (DEPOSIT) {
 #pragma unroll

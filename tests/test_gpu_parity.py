@@ -156,6 +156,22 @@ def test_langmuir_trajectory(sic):
     assert np.abs(Et - Etr).max() <= 1e-3 * Etr.max()
 
 
+def test_energy_sums_through_all_accumulation_paths(sic):
+    """A cold plasma (v = 0 at creation, so the finest sum unit, 2^-32) driven
+    to several cells per step: an item's KE term soon exceeds what a lane's
+    64-bit sum holds (the term goes to the block's 128-bit sum whole) and
+    smaller terms overflow it on the way (the lane's sum spills into the
+    block's). KE and momentum must still follow the oracle's histories."""
+    p = inputs.langmuir(n_tracers=1 << 20, nx=256, amp=1.5, dt=0.1, n_steps=16)
+    h, x, v, d = _run_gpu(sic, p, p.n_steps)
+    r = oracle.run_problem(p)
+    K, Kr = h[:, 1], r["hist"][:-1, 1]
+    assert np.abs(v).max() * p.dt / (p.L / p.nx) > 2.0        # several cells per step
+    assert np.abs(K - Kr).max() <= 1e-3 * Kr.max()
+    P, Pr = h[:, 2], r["hist"][:-1, 2]
+    assert np.abs(P - Pr).max() <= 1e-3 * np.sqrt(2.0 * Kr.max() * p.L) + 1e-9
+
+
 def test_landau_damping_matches_oracle(sic):
     p = inputs.landau_linear()
     h, x, v, d = _run_gpu(sic, p, p.n_steps)
