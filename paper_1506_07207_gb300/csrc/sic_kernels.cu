@@ -20,8 +20,9 @@
 //      simulation with the most unclaimed items, until none has any.
 //
 // Deposit arithmetic: a segment [a, b] of q units in 32.32 fixed-point cell
-// coordinates gives its first cell F = round(q (e_1 - a) / (b - a)) (FP32),
-// every whole cell inside P = floor(q 2^32 / (b - a)) (exact integer), and the
+// coordinates gives its first cell F = round(q (e_1 - a) / (b - a)) (FP32,
+// with an approximate reciprocal, clamped to [0, q]), every whole cell inside
+// P = floor(q 2^32 / (b - a)) (exact integer), and the
 // last cell the rest, q - F - (cells inside) P.  The pieces always sum to q
 // exactly and never go negative; the integer mesh does not depend on the
 // order of the atomic adds, so results are bit-identical however the work is
