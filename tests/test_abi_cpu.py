@@ -34,6 +34,23 @@ def test_header_symbols_are_exported(sic):
     assert sorted(sic.EXPORTS) == names
 
 
+def test_header_constants_match_the_binding(sic):
+    """Every integer constant the header defines has the same value in the
+    binding wherever the binding names it (error codes, limits, deposit
+    schemes, the autotuner's candidate count)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {}
+    for name, val in re.findall(r"#define\s+(SIC_[A-Z0-9_]+)\s+(\(?-?\d+\)?)", text):
+        consts[name] = int(val.strip("()"))
+    assert {"SIC_OK", "SIC_NX_MAX", "SIC_AUTOTUNE_CANDIDATES", "SIC_DEPOSIT_PIC_CIC"} <= set(consts)
+    checked = 0
+    for name, val in consts.items():
+        if hasattr(sic, name):
+            assert getattr(sic, name) == val, name
+            checked += 1
+    assert checked >= 12
+
+
 def test_library_is_built_for_sm103a(sic):
     # the fatbinary names its target; no other architecture is embedded
     blob = open(sic.LIB_PATH, "rb").read()
