@@ -40,7 +40,7 @@ def test_header_constants_match_the_binding(sic):
     schemes, the autotuner's candidate count)."""
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     consts = {}
-    for name, val in re.findall(r"#define\s+(SIC_[A-Z0-9_]+)\s+(\(?-?\d+\)?)", text):
+    for name, val in re.findall(r"^#define\s+(SIC_[A-Z0-9_]+)\s+(\(?-?\d+\)?)\s*$", text, flags=re.M):
         consts[name] = int(val.strip("()"))
     assert {"SIC_OK", "SIC_NX_MAX", "SIC_AUTOTUNE_CANDIDATES", "SIC_DEPOSIT_PIC_CIC"} <= set(consts)
     checked = 0
