@@ -278,6 +278,8 @@ def main():
                     help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC")
     ap.add_argument("--autotune", type=int, default=1, help="tune the batch schedule before timing (0: default)")
     ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--presteps", type=int, default=0,
+                    help="advance the resident batch this many steps before the warm-up (evolved, filamented states)")
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
     ap.add_argument("--overload", type=float, default=2.0,
                     help="a second replay at this load (0: none): requests queue up")
@@ -328,6 +330,9 @@ def main():
     sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream, order=args.deposit) for p in probs]
     batch = Batch(sims)
     S = batch.sic_batch_segments()
+    if args.presteps > 0:
+        batch.sic_batch_step(args.presteps)   # untimed
+        config["presteps"] = args.presteps
     for _ in range(args.warmup):
         batch.sic_batch_step(1)
     schedule = None
