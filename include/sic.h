@@ -145,7 +145,14 @@ int sic_create_horizontal(const sic_config *cfg, int32_t n_template,
  */
 int sic_deposit(sic_sim *sim, int64_t *mesh_fixed_host, double *rho_host);
 
-/* The node field E_j (host, nx entries) of the latest deposit. */
+/*
+ * The node field E_j (host, nx entries) solved from the latest deposit: the
+ * Poisson equation of Sec. 2.1 with C = 1 against the neutralising
+ * background (the mean density), "solve" of the PIC cycle in Sec. 2.3.  E is
+ * the exact integral of rho from node to node, shifted to zero mean (periodic
+ * potential): E_0' = 0, E_{j+1}' = E_j' + dx rho_j, E_j = E_j' - mean(E').
+ * E_host is caller-owned; SIC_EINVAL for a null pointer.
+ */
 int sic_field(sic_sim *sim, double *E_host);
 
 /*
@@ -186,13 +193,28 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added);
 /* Tracers per sheet now (they grow with sic_refine), into counts_host[M]. */
 int sic_sheet_counts(sic_sim *sim, int32_t *counts_host);
 
-/* Gather, kick and drift every tracer with the current field; no deposit. */
+/*
+ * Gather, kick and drift every tracer with the current field, no deposit:
+ * the "gather" and "move" of the PIC cycle, which Sec. 2.3 keeps unchanged
+ * for SIC (forces gathered at the tracers by linear weighting between the
+ * two nodes around each).  The integrator is the leapfrog kick-drift the
+ * paper leaves open: v += dt qm E(x), then x += dt v.  The field is not
+ * re-solved, so a second sic_push kicks with the same field; sic_deposit
+ * re-solves it.  Asynchronous on the simulation's stream; device-side
+ * errors show at the next synchronising call.
+ */
 int sic_push(sic_sim *sim);
 
-/* n_steps full steps; each is one kernel launch: fused gather-kick-drift-deposit
- * over every segment, then the field solve by the block that finishes last.
- * Asynchronous on the simulation's stream: errors found on the device are
- * returned by the next synchronising call (sic_sync, sic_diagnostics, ...). */
+/*
+ * n_steps full SIC steps (Sec. 2.3: the PIC cycle with the scatter replaced
+ * by the sheet deposit of Eq. overlap and Eq. rho_sum): gather and push with
+ * the current field, deposit every particle of the new positions, solve the
+ * field (Sec. 2.1).  Each step is one kernel launch, the field solved by the
+ * block that finishes last; runs of 8 steps replay a captured CUDA graph.
+ * n_steps >= 0.  Asynchronous on the simulation's stream: errors found on
+ * the device are returned by the next synchronising call (sic_sync,
+ * sic_diagnostics, ...).
+ */
 int sic_step(sic_sim *sim, int32_t n_steps);
 
 /* Advance several simulations together, n_steps[i] steps each; the work of
@@ -237,8 +259,13 @@ int sic_diagnostics(sic_sim *sim, sic_diag *out);
  * (room for max_rows rows, max_rows >= 1); the row count goes to *rows. */
 int sic_history(sic_sim *sim, double *hist_host, int32_t max_rows, int32_t *rows);
 
-/* Copy the tracers back: unwrapped positions and current velocities
- * (v^{n-1/2} after n steps), host, sum(tracers_per_sheet) entries each. */
+/*
+ * Copy the tracers back (the sheets of ordered tracers of Sec. 2.2, in the
+ * order they were given): positions and current velocities (v^{n-1/2} after
+ * n steps), into caller-owned host arrays of sum(tracers_per_sheet) entries
+ * each (either may be NULL).  Positions are unwrapped along each sheet (see
+ * SIC position format above).
+ */
 int sic_get_state(sic_sim *sim, double *x_host, double *v_host);
 
 /* Device addresses of the state for zero-copy consumers:

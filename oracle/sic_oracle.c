@@ -159,8 +159,10 @@ int orc_deposit_seg(int nx, double L, int n_sheets, const int32_t *counts,
  * On a closed sheet the closing particle (x_{n-1}, x_0 + winding L) is the
  * neighbour of the first and the last ones; its centroid is shifted by one
  * winding when it is compared with theirs.  A particle at least one box
- * length long also stays a box (the paper stops a run at such a particle,
- * Sec. 3.2; keeping it a box bounds the per-particle work).
+ * length long also stays a box: Sec. 3.2 notes that a run cannot go on
+ * once a particle outgrows the box (it no longer describes the phase-space
+ * sheet), and a linear profile about the centroid of such a particle would
+ * overlap its own periodic image, so the uniform density of Sec. 2.3 is kept.
  *
  * The charge of the piece [lo, hi] of a particle inside a cell is the integral
  * of its density: rho0 (hi - lo) + g ((hi - c)^2 - (lo - c)^2) / 2, summed over

@@ -39,18 +39,26 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
+def compile_command(src: str) -> list:
+    """The nvcc command line that compiles one translation unit."""
+    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    return [_nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+
+
+def link_command(out: str) -> list:
+    """The nvcc command line that links the objects into the library."""
+    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
+    return [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", out, *objs]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link ``libsic.so`` if any source is newer; return its path."""
     if not force and not stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    nvcc = _nvcc()
     procs = []
-    objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = compile_command(src)
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -62,8 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-    subprocess.check_call(cmd)
+    subprocess.check_call(link_command(tmp))
     os.replace(tmp, LIB)
     return LIB
 

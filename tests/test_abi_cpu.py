@@ -51,10 +51,15 @@ def test_header_constants_match_the_binding(sic):
     assert checked >= 12
 
 
-def test_library_is_built_for_sm103a(sic):
-    # the fatbinary names its target; no other architecture is embedded
-    blob = open(sic.LIB_PATH, "rb").read()
-    assert b"sm_103a" in blob
+def test_library_is_built_for_sm103a_only(sic):
+    """Every compile and the link name one target, sm_103a (real code for
+    that architecture, no PTX for others)."""
+    from paper_1506_07207_gb300 import build
+    cmds = [build.compile_command(s) for s in build.SOURCES] + [build.link_command(build.LIB)]
+    for cmd in cmds:
+        gencodes = [cmd[i + 1] for i, a in enumerate(cmd) if a == "-gencode"]
+        assert gencodes == ["arch=compute_103a,code=sm_103a"], cmd
+        assert not any(a.startswith(("-arch", "--gpu-architecture")) for a in cmd), cmd
 
 
 def test_strerror(sic):

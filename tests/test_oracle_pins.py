@@ -160,19 +160,30 @@ def test_gather_linear_weighting():
 
 
 def test_one_leapfrog_step_by_hand():
+    """One kick-drift step and its diagnostics row, by hand.  Unequal tracer
+    weights make the net force on the tracers non-zero, so the time-centred
+    momentum differs from one taken with either velocity alone."""
     nx, n, k = 16, 64, 1.0
     L = 2 * np.pi / k
     q = np.arange(n) * (L / n)
     x0 = q + 0.2 * np.sin(k * q)
-    v0 = 0.1 * np.cos(k * q)
-    w = np.full(n, L / n)
+    v0 = 0.1 * np.cos(k * q) + 0.05
+    w = (L / n) * (1.0 + 0.5 * np.sin(k * q + 1.0))
     dt, qm = 0.3, 1.7
-    # field at t=0 from the inverse-map closed form (see the test above)
-    xe = np.concatenate([x0 - L, x0, x0 + L, [x0[0] + 2 * L]])
-    le = np.concatenate([q - L, q, q + L, [2 * L]])
-    charge = np.diff(np.interp(np.arange(nx + 1) * (L / nx), xe, le))
-    Ep = np.concatenate([[0.0], np.cumsum(charge - L / nx)])[:nx]
-    E0 = Ep - Ep.mean()
+
+    def field_by_hand(x):
+        # the sheet's cumulative charge is linear between tracers (each particle
+        # a box, charge (w_i + w_{i+1}) / 2), extended periodically
+        qs = 0.5 * (w + np.roll(w, -1))
+        c = np.concatenate([[0.0], np.cumsum(qs)[:-1]])
+        Q = qs.sum()
+        xe = np.concatenate([x - L, x, x + L, [x[0] + 2 * L]])
+        le = np.concatenate([c - Q, c, c + Q, [2 * Q]])
+        charge = np.diff(np.interp(np.arange(nx + 1) * (L / nx), xe, le))
+        Ep = np.concatenate([[0.0], np.cumsum(charge - Q / nx)])[:nx]
+        return Ep - Ep.mean()
+
+    E0 = field_by_hand(x0)
     nodes = np.arange(nx + 1) * (L / nx)
     Ex = np.interp(np.mod(x0, L), nodes, np.append(E0, E0[0]))
     v1 = v0 + dt * qm * Ex
@@ -180,6 +191,26 @@ def test_one_leapfrog_step_by_hand():
     r = oracle.run(nx, L, dt, [n], [1], [1], x0, v0, w, 1, qm=qm, half_step_init=False)
     np.testing.assert_allclose(r["v"], v1, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(r["x"], x1, rtol=1e-12, atol=1e-14)
+    # the diagnostics row of the step, time-centred on it (reading A-4):
+    # W_E of E^0, KE = 1/2 sum m (v0^2 + v1^2) / 2, P = sum m (v0 + v1) / 2 with
+    # m = w / qm, and the total charge; the last row has W_E of E^1
+    m = w / qm
+    h = r["hist"]
+    assert math.isclose(h[0, 0], 0.5 * (L / nx) * np.sum(E0 * E0), rel_tol=1e-12)
+    assert math.isclose(h[0, 1], 0.5 * np.sum(m * 0.5 * (v0 * v0 + v1 * v1)), rel_tol=1e-12)
+    P = np.sum(m * 0.5 * (v0 + v1))
+    assert math.isclose(h[0, 2], P, rel_tol=1e-12)
+    assert math.isclose(h[0, 3], w.sum(), rel_tol=1e-14)
+    # a momentum or energy taken from one velocity alone misses the row by far
+    # more than the 1e-12 it is held to (the self-force nearly cancels, so the
+    # momentum margin is about 2e-6 relative)
+    for vv in (v0, v1):
+        assert abs(np.sum(m * vv) - P) > 1e-7 * abs(P)
+        assert abs(0.5 * np.sum(m * vv * vv) - h[0, 1]) > 1e-4 * h[0, 1]
+    E1 = field_by_hand(x1)
+    np.testing.assert_allclose(r["E"], E1, atol=1e-12)
+    assert math.isclose(h[1, 0], 0.5 * (L / nx) * np.sum(E1 * E1), rel_tol=1e-10)
+    assert np.isnan(h[1, 1]) and np.isnan(h[1, 2])
     # the half step back at start-up: v^{-1/2} = v^0 - dt/2 qm E^0(x^0)
     r = oracle.run(nx, L, dt, [n], [1], [1], x0, v0, w, 0, qm=qm, half_step_init=True)
     np.testing.assert_allclose(r["v"], v0 - 0.5 * dt * qm * Ex, rtol=1e-12, atol=1e-14)
@@ -416,6 +447,35 @@ def test_zero_order_moments_agree_with_the_deposit():
     np.testing.assert_allclose(j, u * n, rtol=1e-13, atol=1e-15)
 
 
+def test_segment_velocity_is_mass_weighted():
+    """Sec. 2.3: a particle moves with the mass-weighted mean velocity of its
+    two tracers, (m_i v_i + m_j v_j) / (m_i + m_j).  Worked by hand: tracers of
+    weights 1 and 3 at velocities 2 and -1 give (2 - 3) / 4 = -1/4 (the plain
+    mean would be +1/2); the particle carries (1 + 3) / 2 = 2."""
+    nx, L = 4, 4.0                                    # dx = 1
+    w, v = [1.0, 3.0], [2.0, -1.0]
+    # inside cell 0
+    n, j = oracle.moments(nx, L, [2], [0], [0], [0.125, 0.375], v, w, weighting=0)
+    np.testing.assert_array_equal(n, [2.0, 0, 0, 0])
+    np.testing.assert_array_equal(j, [-0.5, 0, 0, 0])
+    # across the edge at x = 1, half in each cell, and reversed in x
+    n, j = oracle.moments(nx, L, [2], [0], [0], [1.5, 0.5], v, w, weighting=0)
+    np.testing.assert_array_equal(n, [1.0, 1.0, 0, 0])
+    np.testing.assert_array_equal(j, [-0.25, -0.25, 0, 0])
+    # a zero-length particle is a point charge with the same velocity, and its
+    # first-order weights are the hats of its point: 3/4 at node 2, 1/4 at 3
+    n, j = oracle.moments(nx, L, [2], [0], [0], [2.25, 2.25], v, w, weighting=1)
+    np.testing.assert_allclose(n, [0, 0, 1.5, 0.5], rtol=1e-15)
+    np.testing.assert_allclose(j, [0, 0, -0.375, -0.125], rtol=1e-15)
+
+
+def test_particle_charges_by_hand():
+    """q_s = (w_i + w_{i+1}) / 2 (reading A-5); a closed sheet's last entry is
+    the closing particle, an open sheet's is 0."""
+    q = oracle.particle_charges([3, 2], [1, 0], [1.0, 2.0, 4.0, 8.0, 16.0])
+    np.testing.assert_array_equal(q, [1.5, 3.0, 2.5, 12.0, 0.0])
+
+
 def test_first_order_moments_of_a_cosine_density():
     """CIC weighting of a density 1 + A cos(kx) on the nodes is
     1 + A cos(k X_j) sinc^2(k dx / 2) (the hat's Fourier transform); the
@@ -559,3 +619,84 @@ def test_repeated_refinement_bounds_every_particle():
         ends = np.r_[xs[1:], xs[0] + wd * L] if c else xs[1:]
         assert np.abs(ends - xs[:len(ends)]).max() <= l_ref
         base += n
+
+
+def test_run_refined_without_refinement_is_the_leapfrog_run():
+    """run_refined with no particle longer than l_ref carries the charge on the
+    particles but is otherwise the leapfrog loop of orc_run: positions,
+    velocities and the field-energy row agree bit for bit."""
+    p = inputs.tiny_problem(5, n_sheets=4, max_tracers=60, nx=24, L=2.0, dt=0.05)
+    steps = 12
+    r = oracle.run(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w, steps,
+                   half_step_init=False)
+    q = oracle.particle_charges(p.counts, p.closed, p.w)
+    rr = oracle.run_refined(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, q, steps,
+                            l_ref=np.inf, every=1)
+    np.testing.assert_array_equal(rr["counts"], p.counts)
+    np.testing.assert_array_equal(rr["x"], r["x"])
+    np.testing.assert_array_equal(rr["v"], r["v"])
+    np.testing.assert_array_equal(rr["W"], r["hist"][:-1, 0])
+
+
+def test_run_refined_splits_without_changing_the_field():
+    """With refinement after every 3 steps, the refinement at step 3 leaves the
+    deposit unchanged (the halves of a box particle cut at its centre), so the
+    field energies of steps 0..3 are those of the unrefined run (to rounding);
+    afterwards the new tracers move on their own and the runs part."""
+    p = inputs.tiny_problem(8, n_sheets=3, max_tracers=40, nx=32, L=1.0, dt=0.05, spread=0.8)
+    q = oracle.particle_charges(p.counts, p.closed, p.w)
+    every = 3
+    r = oracle.run(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w, 8,
+                   half_step_init=False)
+    rr = oracle.run_refined(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, q, 8,
+                            l_ref=0.02, every=every)
+    assert rr["counts"].sum() > p.counts.sum()
+    assert math.isclose(rr["qseg"].sum(), q.sum(), rel_tol=1e-14)
+    W, Wr = rr["W"], r["hist"][:-1, 0]
+    np.testing.assert_allclose(W[:every + 1], Wr[:every + 1], rtol=1e-11)
+    assert np.abs(W[every + 1:] - Wr[every + 1:]).max() > 1e-9 * Wr.max()
+
+
+def test_linear_particle_a_box_length_long_stays_a_box():
+    """Reading A-19: a piecewise-linear particle at least one box length long
+    keeps the uniform density of Sec. 2.3 (once a particle outgrows the box the
+    run has left the regime the method describes, Sec. 3.2, and a linear
+    profile about its centroid would overlap its own periodic image).  Open
+    sheet of three particles of lengths 0.1, l, 0.2 on a box of length 1: the
+    two end particles have no neighbour on one side and stay boxes; the middle
+    one has ordered centroids and unequal neighbour densities, so it gets a
+    gradient while l < 1 and none at l = 1."""
+    nx, L = 8, 1.0
+    w = [0.25, 0.25, 0.25, 0.25]
+    for ell, linear in ((0.875, True), (1.0, False), (1.25, False)):
+        x = [0.0, 0.125, 0.125 + ell, 0.375 + ell]
+        box = oracle.deposit(nx, L, [4], [0], [0], x, w)
+        lin = oracle.deposit(nx, L, [4], [0], [0], x, w, order=1)
+        if linear:
+            assert np.abs(lin - box).max() > 1e-3
+        else:
+            np.testing.assert_array_equal(lin, box)
+        assert math.isclose(lin.sum(), 0.75, rel_tol=1e-15)
+
+
+# ------------------------------------------------------------------ fits ----
+
+def test_fit_helpers_on_closed_forms():
+    """The rate and frequency fits on signals with known answers."""
+    t = np.arange(0, 40, 0.05)
+    # damping: W = exp(2 gamma t) cos^2(omega t) peaks decay at 2 gamma
+    g, w = -0.1533, 1.4157
+    W = np.exp(2 * g * t) * np.cos(w * t) ** 2
+    assert abs(fits.damping_rate(t, W, 2.0, 30.0) / g - 1) < 1e-3
+    # growth: |E| = exp(gamma t)
+    assert abs(fits.growth_rate(t, 3.0 * np.exp(0.33488 * t), 5.0, 30.0) - 0.33488) < 1e-12
+    # oscillation: cos(omega t + phase)
+    assert abs(fits.oscillation_omega(t, np.cos(1.000417 * t + 0.3)) - 1.000417) < 1e-5
+    # local maxima of a sampled parabola: refined to the vertex
+    tt = np.arange(10.0)
+    pt, py = fits.local_maxima(tt, -(tt - 4.3) ** 2 + 2.0)
+    assert np.allclose(pt, [4.3]) and np.allclose(py, [2.0])
+    # mode: the Fourier coefficient of cos(2 pi m j / nx) is 1/2
+    nx = 16
+    E = np.cos(2 * np.pi * 3 * np.arange(nx) / nx)[None, :]
+    assert abs(fits.mode(E, 3)[0] - 0.5) < 1e-15
