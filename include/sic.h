@@ -21,12 +21,27 @@
  *   - A closed sheet is closed by the segment (x_N, x_1 + winding * L).
  *   - Leapfrog: v^{n+1/2} = v^{n-1/2} + dt qm E^n(x^n), x^{n+1} = x^n + dt v^{n+1/2}.
  *
- * Precision: positions are held as unwrapped 32.32 fixed point in cell units,
- * velocities and push arithmetic in FP32, charge in int64 fixed point (total
- * charge is conserved bit-exactly and the deposit is independent of the order
- * of the atomic adds); the field solve is exact integer arithmetic with one
- * final rounding.  Results are bit-identical however the work is split
- * across thread blocks or batched with other simulations.
+ * Precision: positions are 32-bit fixed point (SIC position format below),
+ * velocities and push arithmetic FP32, charge int64 fixed point (total charge
+ * is conserved bit-exactly and the deposit is independent of the order of
+ * the atomic adds); the field solve is exact integer arithmetic with one final
+ * rounding.  Results are bit-identical however the work is split across
+ * thread blocks or batched with other simulations.
+ *
+ * SIC position format.  A tracer at x is stored as P = x / L 2^30 modulo 2^32
+ * (L the box length): 30 bits of box fraction (a resolution of L 2^-30) and
+ * 2 bits of winding, so positions are known modulo 4 box lengths and the
+ * segment between two tracers is the 32-bit difference of their P, exact
+ * while it is shorter than 2 box lengths.  A drift adds the step v dt rounded
+ * to whole units of L 2^-30.  Limits, checked: a segment stays shorter than
+ * 1.5 box lengths (at creation: SIC_ERANGE; while stepping: the run stops
+ * with SIC_ERANGE at the next synchronising call; Sec. 3.2 notes that a run
+ * cannot go on once a segment outgrows the box anyway), and a tracer moves
+ * less than half a box per step.  Since each end of a segment moves less
+ * than half a box per step, no segment can pass from below 1.5 to 2.5 box
+ * lengths, where its difference would alias, in one step.  Positions read
+ * back (sic_get_state) are unwrapped along each sheet: its first tracer
+ * inside [0, L), each next one a segment further.
  *
  * Memory: every pointer argument named *_host is caller-owned host memory that
  * the call only reads or writes during the call.  All device state is owned by
@@ -48,7 +63,9 @@ extern "C" {
 #define SIC_EINVAL (-1)        /* bad size, NaN/Inf input, nx out of range, ... */
 #define SIC_ENOMEM (-2)        /* device or host allocation failed */
 #define SIC_ECUDA (-3)         /* a CUDA call failed */
-#define SIC_ERANGE (-4)        /* a position left the fixed-point range (|x/dx| >= 2^30) */
+#define SIC_ERANGE (-4)        /* outside the position format: a segment of 1.5 box
+                                  lengths or more, a step of half a box or more, |x| of
+                                  2^20 box lengths or more at creation */
 #define SIC_ESEGMENT_LONG (-5) /* strict mode: a segment is longer than the box */
 #define SIC_ETIMEOUT (-6)      /* a bounded device wait gave up */
 #define SIC_EBUSY (-7)         /* server: budget or slots exhausted */
@@ -119,9 +136,11 @@ typedef struct {
 
 /*
  * Create a simulation from host arrays of length sum(tracers_per_sheet):
- * positions x (unwrapped, any real value), velocities v and charge weights
- * w > 0, all finite.  The inputs are copied; the initial charge is deposited
- * and the field solved (and the half step applied if asked).
+ * positions x (unwrapped, |x| < 2^20 L), velocities v (|v dt| < L / 2) and
+ * charge weights w > 0, all finite; every segment, the closing one included,
+ * shorter than 1.5 L (SIC_ERANGE otherwise).  The inputs are copied; the
+ * initial charge is deposited and the field solved (and the half step applied
+ * if asked).
  */
 int sic_create(const sic_config *cfg, const double *x_host, const double *v_host,
                const double *w_host, sic_sim **out);
@@ -268,10 +287,12 @@ int sic_history(sic_sim *sim, double *hist_host, int32_t max_rows, int32_t *rows
  */
 int sic_get_state(sic_sim *sim, double *x_host, double *v_host);
 
-/* Device addresses of the state for zero-copy consumers:
- * positions int64 (2^-32 cell units), velocities float (cells per step),
- * tracer i of sheet s at sheet_offset[s] + i.  Valid until sic_destroy. */
-int sic_device_state(sic_sim *sim, int64_t **pos_dev, float **vel_dev,
+/* Device addresses of the state for zero-copy consumers: positions uint32 in
+ * the SIC position format (x / L 2^30 modulo 2^32), velocities float (position
+ * units per step, v dt / L 2^30), tracer i of sheet s at sheet_offset[s] + i.
+ * Valid until the next sic_step, sic_push or sic_refine (the state is double
+ * buffered) or sic_destroy. */
+int sic_device_state(sic_sim *sim, uint32_t **pos_dev, float **vel_dev,
                      const int64_t **sheet_offset_host);
 
 /* Synchronise the simulation's stream. */

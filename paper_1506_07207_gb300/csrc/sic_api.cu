@@ -48,27 +48,20 @@ int num_sms()
     return n;
 }
 
-NxDiv make_div(int nx)
+constexpr double kPosUnits = 1073741824.0;  // 2^SIC_POS_FRAC_BITS position units per box length
+
+// A position x as P = x / L 2^30 modulo 2^32 (the box length L): the box
+// fraction t = x / L is folded into [0, 4) first, so P keeps full precision.
+uint32_t to_pos(double x, double L)
 {
-    NxDiv d;
-    d.nx = nx;
-    int l = 0;
-    while ((1 << l) < nx)
-        ++l;
-    const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - (uint64_t)nx)) / (uint64_t)nx + 1;
-    d.magic = (uint32_t)m;
-    d.shift = l - 1;
-    d.offset = nx * ((1 << 30) / nx + 1);
-    return d;
+    double t = x / L;
+    t -= 4.0 * std::floor(t * 0.25);
+    return (uint32_t)((uint64_t)std::llround(t * kPosUnits) & 0xffffffffull);
 }
 
-// x / dx as 32.32 fixed point
-int64_t to_fixed(double xc)
-{
-    const double c = std::floor(xc);
-    const double f = xc - c;
-    return (int64_t)c * (int64_t)4294967296LL + (int64_t)std::llround(f * kTwo32);
-}
+// Largest |x| / L accepted at creation (the fold into [0, 4) box lengths keeps
+// the position to well within a unit below this).
+constexpr double kMaxBoxes = 1048576.0;
 
 bool is_finite(double x) { return std::isfinite(x); }
 
@@ -155,25 +148,27 @@ void plan_items(sic_sim *sim)
             const bool last = (k + 1) * item >= n;
             if (!last) {
                 w.halo = w.t0 + w.count;
-                w.halo_shift = 0;
+                w.halo_shift = 0u;
             } else if (sim->closed[s]) {
                 w.halo = sim->sheet_off[s];
-                w.halo_shift = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
+                w.halo_shift = (uint32_t)sim->winding[s] << SIC_POS_FRAC_BITS;
             } else {
                 w.halo = -1;
-                w.halo_shift = 0;
+                w.halo_shift = 0u;
             }
             sim->items.push_back(w);
             if (sim->deposit == SIC_DEPOSIT_LINEAR) {
-                // the tracer before the first one and the one after the halo
-                const int64_t wind = (int64_t)sim->winding[s] * (int64_t)sim->nx * (int64_t)4294967296LL;
+                // the tracer before the first one and the one after the halo;
+                // on a closed sheet the other end is one winding away (the
+                // kernel subtracts prev_shift and adds next2_shift)
+                const uint32_t wind = (uint32_t)sim->winding[s] << SIC_POS_FRAC_BITS;
                 const int64_t off = sim->sheet_off[s];
-                WorkItemPL p{-1, 0, -1, 0};
+                WorkItemPL p{-1, -1, 0u, 0u};
                 if (k > 0)
                     p.prev = w.t0 - 1;
                 else if (sim->closed[s]) {
                     p.prev = off + n - 1;
-                    p.prev_shift = -wind;
+                    p.prev_shift = wind;
                 }
                 const int64_t after = (int64_t)k * item + w.count + 1;  // sheet index after the halo
                 if (!last) {
@@ -225,8 +220,8 @@ cudaError_t bind_layout(sic_sim *sim, char *b, const SimLayout &L)
 {
     SimDev &h = sim->h;
     const int n_items = (int)sim->items.size();
-    h.U[0] = (int64_t *)(b + L.oU0);
-    h.U[1] = (int64_t *)(b + L.oU1);
+    h.U[0] = (uint32_t *)(b + L.oU0);
+    h.U[1] = (uint32_t *)(b + L.oU1);
     h.V[0] = (float *)(b + L.oV0);
     h.V[1] = (float *)(b + L.oV1);
     h.Qh = sim->per_q ? (const int32_t *)(b + L.oQ) : nullptr;
@@ -292,7 +287,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
         auto unit_exp = [](double bound) {
             if (!(bound > 0.0))
                 return 32;
-            return std::max(-40, std::min(32, (int)std::floor(44.0 - std::log2(bound))));
+            return std::max(-100, std::min(32, (int)std::floor(44.0 - std::log2(bound))));
         };
         h.ke_u = unit_exp(qh_max * 2.0 * SIC_K1_R * vb * vb);
         h.p_u = unit_exp(qh_max * 2.0 * SIC_K1_R * vb);
@@ -310,10 +305,11 @@ int setup(sic_sim *sim, const sic_config *cfg)
     SimDev &h = sim->h;
     CK(bind_layout(sim, b, L));
     h.hist_len = sim->hist_len;
-    h.div = make_div(nx);
+    h.nx = nx;
     const double nx2 = (double)nx * (double)nx;
     h.E_scale = 1.0 / (nx2 * sim->sigma);
-    h.e_scale = sim->qm * sim->dt * sim->dt / sim->dx * h.E_scale;
+    // the kick per step in position units: qm E dt^2 / L 2^30
+    h.e_scale = sim->qm * sim->dt * sim->dt / sim->L * kPosUnits * h.E_scale;
     h.rho_scale = 1.0 / ((double)nx * sim->sigma * sim->dx);
     // W_E = dx/2 sum E_j^2 = dx/2 E_scale^2 2^120 sum (K_j 2^-60)^2
     h.we_scale = 0.5 * sim->dx * h.E_scale * h.E_scale * std::ldexp(1.0, 120);
@@ -323,11 +319,10 @@ int setup(sic_sim *sim, const sic_config *cfg)
         h.ek_mant = (float)(mant * 2.0);
         h.ek_exp = ex - 1;
     }
-    const double vu = sim->dx / sim->dt;  // physical velocity of one cell per step
+    const double vu = sim->L / (sim->dt * kPosUnits);  // physical velocity of one position unit per step
     h.ke_scale = vu * vu / (2.0 * sim->sigma * sim->qm);
     h.p_scale = vu / (sim->sigma * sim->qm);
     h.strict = sim->strict;
-    h.pow2 = (nx & (nx - 1)) == 0;
     sic_sim *one[1] = {sim};
     CK(build_plan(sim->plan, one, 1, sim->stream));
     return SIC_OK;
@@ -356,8 +351,7 @@ void free_plan(Plan &p, cudaStream_t s)
 // Build the device plan of one launch over several simulations (slot order):
 // the table of their descriptors, where each one's items start in the
 // launch's list, and the zeroed claim cursors, item tickets and block count.
-// Every member must share the charge mode; pow2 only if every nx is a power
-// of two.
+// Every member must share the charge mode.
 //
 // Scheduling: block b starts on the simulation that holds its proportional
 // share of the items; its warps claim runs of consecutive items of that
@@ -371,19 +365,17 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
     std::vector<SimDev> table(n);
     std::vector<int32_t> slot_begin(n + 1, 0);
     int nx_max = 2;
-    bool pow2 = true;
     int64_t n_items = 0;
     for (int slot = 0; slot < n; ++slot) {
         sic_sim *m = sims[slot];
         table[slot] = m->h;
         nx_max = std::max(nx_max, m->nx);
-        pow2 = pow2 && ((m->nx & (m->nx - 1)) == 0);
         slot_begin[slot] = (int32_t)n_items;
         n_items += (int64_t)m->items.size();
     }
     slot_begin[n] = (int32_t)n_items;
     const bool per_q = sims[0]->per_q;
-    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
+    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q);
     if (per_sm < 1)
         per_sm = 1;
     const int by_items = (int)((n_items + SIC_K1_WARPS - 1) / SIC_K1_WARPS);
@@ -424,7 +416,6 @@ cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s)
         p.args.gen |= sims[slot]->deposit != SIC_DEPOSIT_BOX ? 1 : 0;
     p.grid = grid;
     p.per_q = per_q;
-    p.pow2 = pow2;
     return cudaSuccess;
 }
 
@@ -441,7 +432,7 @@ cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int re
     a.kick_scale = kick_scale;
     a.drift = drift;
     a.record = record;
-    return launch_step_kernel(a, p.grid, mode, p.per_q, p.pow2, s);
+    return launch_step_kernel(a, p.grid, mode, p.per_q, s);
 }
 
 
@@ -449,8 +440,8 @@ SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int h
 {
     Layout lay;
     SimLayout L;
-    L.oU0 = lay.take(8 * (size_t)n_alloc);
-    L.oU1 = lay.take(8 * (size_t)n_alloc);
+    L.oU0 = lay.take(4 * (size_t)n_alloc);
+    L.oU1 = lay.take(4 * (size_t)n_alloc);
     L.oV0 = lay.take(4 * (size_t)n_alloc);
     L.oV1 = lay.take(4 * (size_t)n_alloc);
     L.oQ = per_q ? lay.take(4 * (size_t)n_alloc) : 0;
@@ -499,7 +490,7 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
         return rc;
     if (!x_host || !v_host || !w_host)
         return SIC_EINVAL;
-    const double dx = cfg->box_length / cfg->nx;
+    const double L = cfg->box_length;
     int64_t n = 0;
     for (int s = 0; s < cfg->n_sheets; ++s)
         n += cfg->tracers_per_sheet[s];
@@ -507,12 +498,30 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
     for (int64_t i = 0; i < n; ++i) {
         if (!is_finite(x_host[i]) || !is_finite(v_host[i]) || !is_finite(w_host[i]) || w_host[i] <= 0)
             return SIC_EINVAL;
-        if (std::fabs(x_host[i] / dx) >= (double)(1 << 29))
+        if (std::fabs(x_host[i] / L) >= kMaxBoxes)
             return SIC_ERANGE;
-        if (std::fabs(v_host[i] * cfg->dt / dx) >= (double)(1 << 20))
-            return SIC_EINVAL;
+        // a tracer may move less than half a box per step
+        if (std::fabs(v_host[i] * cfg->dt / L) >= 0.5)
+            return SIC_ERANGE;
         max_w = std::max(max_w, w_host[i]);
-        max_v = std::max(max_v, std::fabs(v_host[i] * cfg->dt / dx));
+        max_v = std::max(max_v, std::fabs(v_host[i] * cfg->dt / L * kPosUnits));
+    }
+    // every segment shorter than 1.5 box lengths (the position format holds
+    // segments up to 2; the step kernels stop a run at 1.5)
+    {
+        int64_t base = 0;
+        for (int s = 0; s < cfg->n_sheets; ++s) {
+            const int c = cfg->tracers_per_sheet[s];
+            for (int i = 0; i + 1 < c; ++i)
+                if (!(std::fabs(x_host[base + i + 1] - x_host[base + i]) < 1.5 * L))
+                    return SIC_ERANGE;
+            if (cfg->sheet_closed[s]) {
+                const double wd = cfg->sheet_winding ? (double)cfg->sheet_winding[s] : 0.0;
+                if (!(std::fabs(x_host[base] + wd * L - x_host[base + c - 1]) < 1.5 * L))
+                    return SIC_ERANGE;
+            }
+            base += c;
+        }
     }
     sic_sim *sim = new (std::nothrow) sic_sim;
     if (!sim)
@@ -557,22 +566,22 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
         return rc;
     }
     {
-        std::vector<int64_t> U(sim->n_alloc, 0);
+        std::vector<uint32_t> U(sim->n_alloc, 0u);
         std::vector<float> V(sim->n_alloc, 0.f);
         std::vector<int32_t> Q(sim->per_q ? sim->n_alloc : 0, 0);
-        const double vscale = cfg->dt / dx;
+        const double vscale = cfg->dt / L * kPosUnits;
         int64_t base = 0;
         for (int s = 0; s < sim->M; ++s) {
             const int64_t o = sim->sheet_off[s];
             for (int i = 0; i < sim->counts[s]; ++i) {
-                U[o + i] = to_fixed(x_host[base + i] / dx);
+                U[o + i] = to_pos(x_host[base + i], L);
                 V[o + i] = (float)(v_host[base + i] * vscale);
                 if (sim->per_q)
                     Q[o + i] = (int32_t)std::llround(w_host[base + i] * sim->sigma * 0.5);
             }
             base += sim->counts[s];
         }
-        cudaError_t e = cudaMemcpyAsync(sim->h.U[0], U.data(), 8 * U.size(), cudaMemcpyHostToDevice, sim->stream);
+        cudaError_t e = cudaMemcpyAsync(sim->h.U[0], U.data(), 4 * U.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(sim->h.V[0], V.data(), 4 * V.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess && sim->per_q)
@@ -606,21 +615,24 @@ int sic_create_horizontal(const sic_config *cfg, int32_t n_template, const doubl
         return SIC_EINVAL;
     if ((int64_t)n_template * cfg->n_sheets > SIC_TRACERS_MAX)
         return SIC_EINVAL;
-    const double dx = cfg->box_length / cfg->nx;
+    const double L = cfg->box_length;
     for (int i = 0; i < n_template; ++i) {
         if (!is_finite(x_template_host[i]))
             return SIC_EINVAL;
-        if (std::fabs(x_template_host[i] / dx) >= (double)(1 << 29))
+        if (std::fabs(x_template_host[i] / L) >= kMaxBoxes)
+            return SIC_ERANGE;
+        const double next = i + 1 < n_template ? x_template_host[i + 1] : x_template_host[0] + L;
+        if (!(std::fabs(next - x_template_host[i]) < 1.5 * L))   // segments below 1.5 box lengths
             return SIC_ERANGE;
     }
     double max_w = 0, max_v = 0;
     for (int s = 0; s < cfg->n_sheets; ++s) {
         if (!is_finite(v_sheet_host[s]) || !is_finite(w_sheet_host[s]) || w_sheet_host[s] <= 0)
             return SIC_EINVAL;
-        if (std::fabs(v_sheet_host[s] * cfg->dt / dx) >= (double)(1 << 20))
-            return SIC_EINVAL;
+        if (std::fabs(v_sheet_host[s] * cfg->dt / L) >= 0.5)
+            return SIC_ERANGE;
         max_w = std::max(max_w, w_sheet_host[s]);
-        max_v = std::max(max_v, std::fabs(v_sheet_host[s] * cfg->dt / dx));
+        max_v = std::max(max_v, std::fabs(v_sheet_host[s] * cfg->dt / L * kPosUnits));
     }
     sic_sim *sim = new (std::nothrow) sic_sim;
     if (!sim)
@@ -642,21 +654,22 @@ int sic_create_horizontal(const sic_config *cfg, int32_t n_template, const doubl
         sic_destroy(sim);
         return rc;
     }
-    std::vector<int64_t> ut(n_template);
+    std::vector<uint32_t> ut(n_template);
     for (int i = 0; i < n_template; ++i)
-        ut[i] = to_fixed(x_template_host[i] / dx);
+        ut[i] = to_pos(x_template_host[i], L);
     std::vector<float> vs(sim->M);
     for (int s = 0; s < sim->M; ++s)
-        vs[s] = (float)(v_sheet_host[s] * cfg->dt / dx);
+        vs[s] = (float)(v_sheet_host[s] * cfg->dt / L * kPosUnits);
     void *tmp = nullptr;
-    const size_t bytes = 8 * (size_t)n_template + 8 * (size_t)sim->M + 4 * (size_t)sim->M + 64;
+    // sheet offsets (8-byte) first, then the template and the velocities
+    const size_t bytes = 8 * (size_t)sim->M + 4 * (size_t)n_template + 4 * (size_t)sim->M + 64;
     cudaError_t e = cudaMallocAsync(&tmp, bytes, sim->stream);
     if (e == cudaSuccess) {
         char *t = (char *)tmp;
-        int64_t *d_ut = (int64_t *)t;
-        int64_t *d_off = (int64_t *)(t + 8 * (size_t)n_template);
-        float *d_vs = (float *)(t + 8 * (size_t)n_template + 8 * (size_t)sim->M);
-        e = cudaMemcpyAsync(d_ut, ut.data(), 8 * ut.size(), cudaMemcpyHostToDevice, sim->stream);
+        int64_t *d_off = (int64_t *)t;
+        uint32_t *d_ut = (uint32_t *)(t + 8 * (size_t)sim->M);
+        float *d_vs = (float *)(t + 8 * (size_t)sim->M + 4 * (size_t)n_template);
+        e = cudaMemcpyAsync(d_ut, ut.data(), 4 * ut.size(), cudaMemcpyHostToDevice, sim->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_off, sim->sheet_off.data(), 8 * sim->sheet_off.size(), cudaMemcpyHostToDevice,
                                 sim->stream);
@@ -704,8 +717,8 @@ int sic_moments(sic_sim *sim, int32_t weighting, double *n_host, double *j_host)
         return SIC_EINVAL;
     // E64 and rho64 serve as the device buffers: sic_field and sic_deposit
     // rewrite them before reading them
-    CK(launch_moments(sim->h, weighting, sim->dx, 1.0 / sim->sigma, sim->dx / sim->dt, sim->h.rho64, sim->h.E64,
-                      sim->stream));
+    CK(launch_moments(sim->h, weighting, sim->L, 1.0 / sim->sigma, sim->L / (sim->dt * kPosUnits), sim->h.rho64,
+                      sim->h.E64, sim->stream));
     if (n_host)
         CK(cudaMemcpyAsync(n_host, sim->h.rho64, 8 * (size_t)sim->nx, cudaMemcpyDeviceToHost, sim->stream));
     if (j_host)
@@ -724,9 +737,9 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
     int rc = check_device_errors(sim);
     if (rc)
         return rc;
-    const double lc = l_ref / sim->dx * kTwo32;  // 32.32 cells
-    if (lc >= 4.0e18)
-        return SIC_OK;  // nothing can be that long
+    const double lc = l_ref / sim->L * kPosUnits;  // position units
+    if (lc >= 2.0 * kPosUnits)
+        return SIC_OK;  // no segment is 2 box lengths long
     const long long lfix = (long long)lc;
     const int n_items = (int)sim->items.size();
 
@@ -806,7 +819,7 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
     CK(cudaStreamSynchronize(sim->stream));
     const int cur = (int)(sc.buf & 1);
     const size_t oU = cur ? L.oU1 : L.oU0, oV = cur ? L.oV1 : L.oV0;
-    e = launch_refine_scatter(sim->h, lfix, d_base, (int64_t *)(b + oU), (float *)(b + oV), (int32_t *)(b + L.oQ),
+    e = launch_refine_scatter(sim->h, lfix, d_base, (uint32_t *)(b + oU), (float *)(b + oV), (int32_t *)(b + L.oQ),
                               sim->stream);
     const size_t nx8 = 8 * (size_t)sim->nx;
     if (e == cudaSuccess)
@@ -1217,17 +1230,22 @@ int sic_get_state(sic_sim *sim, double *x_host, double *v_host)
     if (rc)
         return rc;
     const int b = sc.buf & 1;
-    std::vector<int64_t> U(sim->n_alloc);
+    std::vector<uint32_t> U(sim->n_alloc);
     std::vector<float> V(sim->n_alloc);
-    CK(cudaMemcpy(U.data(), sim->h.U[b], 8 * U.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(U.data(), sim->h.U[b], 4 * U.size(), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(V.data(), sim->h.V[b], 4 * V.size(), cudaMemcpyDeviceToHost));
-    const double xs = sim->dx / kTwo32, vs = sim->dx / sim->dt;
+    // each sheet unwrapped along its tracers: the first one inside the box,
+    // every next one a segment (the 32-bit position difference) further
+    const double unit = sim->L / kPosUnits, vs = sim->L / (sim->dt * kPosUnits);
     int64_t base = 0;
     for (int s = 0; s < sim->M; ++s) {
         const int64_t o = sim->sheet_off[s];
+        double x = (double)(uint32_t)(U[o] << SIC_POS_WIND_BITS) * (sim->L / kTwo32);
         for (int i = 0; i < sim->counts[s]; ++i) {
+            if (i > 0)
+                x += (double)(int32_t)(U[o + i] - U[o + i - 1]) * unit;
             if (x_host)
-                x_host[base + i] = (double)U[o + i] * xs;
+                x_host[base + i] = x;
             if (v_host)
                 v_host[base + i] = (double)V[o + i] * vs;
         }
@@ -1236,7 +1254,7 @@ int sic_get_state(sic_sim *sim, double *x_host, double *v_host)
     return SIC_OK;
 }
 
-int sic_device_state(sic_sim *sim, int64_t **pos_dev, float **vel_dev, const int64_t **sheet_offset_host)
+int sic_device_state(sic_sim *sim, uint32_t **pos_dev, float **vel_dev, const int64_t **sheet_offset_host)
 {
     if (!sim)
         return SIC_EINVAL;
@@ -1292,7 +1310,7 @@ const char *sic_strerror(int code)
     case SIC_ECUDA:
         return "CUDA error";
     case SIC_ERANGE:
-        return "position outside the fixed-point range";
+        return "outside the fixed-point position range (a segment of 1.5 box lengths or a step of half a box)";
     case SIC_ESEGMENT_LONG:
         return "segment longer than the box";
     case SIC_ETIMEOUT:
@@ -1355,24 +1373,21 @@ cudaError_t static_scratch(int dev, unsigned char **out)
 
 // Write the plan of one group into its part of the scratch (stream-ordered
 // after the previous launches), clear its counters, and return its arguments.
-cudaError_t static_plan(unsigned char *region, sic_sim *const *grp, int n, cudaStream_t s, LaunchArgs &a, int &grid,
-                        bool &pow2)
+cudaError_t static_plan(unsigned char *region, sic_sim *const *grp, int n, cudaStream_t s, LaunchArgs &a, int &grid)
 {
     SimDev table[SIC_STATIC_MAX_SIMS];
     int32_t slot_begin[SIC_STATIC_MAX_SIMS + 1];
     int nx_max = 2;
-    pow2 = true;
     int64_t n_items = 0;
     for (int i = 0; i < n; ++i) {
         table[i] = grp[i]->h;
         nx_max = std::max(nx_max, grp[i]->nx);
-        pow2 = pow2 && ((grp[i]->nx & (grp[i]->nx - 1)) == 0);
         slot_begin[i] = (int32_t)n_items;
         n_items += (int64_t)grp[i]->items.size();
     }
     slot_begin[n] = (int32_t)n_items;
     const bool per_q = grp[0]->per_q;
-    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q, pow2);
+    int per_sm = step_blocks_per_sm(nx_max, MODE_STEP, per_q);
     if (per_sm < 1)
         per_sm = 1;
     const int by_items = (int)((n_items + SIC_K1_WARPS - 1) / SIC_K1_WARPS);
@@ -1437,14 +1452,12 @@ int static_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)
             break;
         LaunchArgs a[2];
         int grid[2] = {0, 0};
-        bool pow2[2] = {true, true};
         for (int g = 0; g < 2; ++g)
-            if (ng[g] && static_plan(scratch + g * kStaticGroup, grp[g], ng[g], bs, a[g], grid[g], pow2[g]) !=
-                             cudaSuccess)
+            if (ng[g] && static_plan(scratch + g * kStaticGroup, grp[g], ng[g], bs, a[g], grid[g]) != cudaSuccess)
                 return SIC_ECUDA;
         for (int32_t st = 0; st < k; ++st)
             for (int g = 0; g < 2; ++g)
-                if (ng[g] && launch_step_kernel(a[g], grid[g], MODE_STEP, g == 1, pow2[g], bs) != cudaSuccess)
+                if (ng[g] && launch_step_kernel(a[g], grid[g], MODE_STEP, g == 1, bs) != cudaSuccess)
                     return SIC_ECUDA;
         for (int i = 0; i < n_sims; ++i)
             if (left[i] > 0)

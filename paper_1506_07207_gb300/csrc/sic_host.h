@@ -18,7 +18,6 @@ struct Plan {
     LaunchArgs args{};
     int grid = 0;
     bool per_q = false;
-    bool pow2 = false;
 };
 
 // Device bytes of one simulation's allocation (state, meshes, items, ...).
@@ -47,7 +46,7 @@ struct sic_sim {
     std::vector<int32_t> sheet_qh;
     int64_t n_tracers = 0, n_alloc = 0;
     double sigma = 1.0;
-    double v_max = 0.0;               // largest |v| at creation, cells per step
+    double v_max = 0.0;               // largest |v| at creation, position units per step
     double w_max = 0.0;               // largest weight at creation
     std::vector<WorkItem> items;
     int deposit = SIC_DEPOSIT_BOX;    // SIC_DEPOSIT_*

@@ -1,12 +1,16 @@
 // sic_internal.h -- device-side layout shared by the kernels and the host runtime.
 //
 // State of one simulation in HBM (all arrays device-resident for its lifetime):
-//   U[2][n_alloc] int64  tracer position, unwrapped, 32.32 fixed point in cell
-//                        units (x / dx * 2^32); two buffers, a step reads one
-//                        and writes the other (sc->buf names the current one).
-//                        Sheets start on 32-tracer boundaries so every thread's
-//                        tracers are 16-byte aligned.
-//   V[2][n_alloc] float  velocity in cells per step (v dt / dx).
+//   U[2][n_alloc] uint32 tracer position P = x / L * 2^30 modulo 2^32: a 30-bit
+//                        fraction of the box and 2 bits of winding, so positions
+//                        are kept modulo 4 box lengths and the segment between
+//                        two tracers is the 32-bit difference of their P
+//                        (exact while it is shorter than 2 box lengths).  Two
+//                        buffers: a step reads one and writes the other
+//                        (sc->buf names the current one).  Sheets start on
+//                        32-tracer boundaries so every thread's tracers are
+//                        16-byte aligned.
+//   V[2][n_alloc] float  velocity in position units per step (v dt / L * 2^30).
 //   Qh[n_alloc]   int32  half charge of each tracer in fixed-point units (only
 //                        when weights differ inside a sheet; otherwise every
 //                        work item carries its sheet's value); after a
@@ -15,7 +19,7 @@
 //   mesh[nx]      u64    int64 charge accumulator the deposit adds into.
 //   mesh_last     int64  charge of the latest completed deposit.
 //   Ek[nx]        float2 (Ek_j, Ek_{j+1} - Ek_j): the kick per step
-//                        qm E_j dt^2 / dx at node j and its difference to the
+//                        qm E_j dt^2 / L 2^30 at node j and its difference to the
 //                        next node (the step kernel stages Ek_j alone in
 //                        shared memory and forms the same difference).
 //   E64[nx]       double the node field E_j in physical units.
@@ -27,6 +31,10 @@
 #include <stdint.h>
 
 #include "sic.h"
+
+// Position format: P = x / L * 2^SIC_POS_FRAC_BITS modulo 2^32.
+#define SIC_POS_FRAC_BITS 30
+#define SIC_POS_WIND_BITS 2      // 32 - SIC_POS_FRAC_BITS
 
 #define SIC_ALIGN_TRACERS 32
 #define SIC_K1_BLOCK 256
@@ -46,19 +54,11 @@
 
 // Per-warp double-buffered staging of the next work item in shared memory
 // (filled by bulk copies): positions, velocities and, per-tracer charge mode,
-// half charges, each with room for the item's 32 R tracers plus its halo.
-#define SIC_STAGE_U_BYTES (((SIC_K1_WARP_TRACERS + 1) * 8 + 15) / 16 * 16)
-#define SIC_STAGE_V_BYTES (((SIC_K1_WARP_TRACERS + 1) * 4 + 15) / 16 * 16)
-#define SIC_STAGE_Q_BYTES SIC_STAGE_V_BYTES
-
-// periodic cell reduction by a precomputed multiplier (unsigned division by
-// an invariant integer: q = (t + ((n - t) >> 1)) >> (l - 1), t = umulhi(m, n))
-struct NxDiv {
-    int32_t nx;
-    uint32_t magic;
-    int32_t shift;     // l - 1
-    int32_t offset;    // multiple of nx >= 2^30, added before the division
-};
+// half charges, each with room for the item's 32 R tracers, its halo and (for
+// the published positions of piecewise-linear particles) one more.
+#define SIC_STAGE_U_BYTES (((SIC_K1_WARP_TRACERS + 2) * 4 + 15) / 16 * 16)
+#define SIC_STAGE_V_BYTES SIC_STAGE_U_BYTES
+#define SIC_STAGE_Q_BYTES SIC_STAGE_U_BYTES
 
 // One work item, the task of one warp: up to 32 R consecutive tracers of one sheet.
 struct WorkItem {
@@ -70,18 +70,19 @@ struct WorkItem {
     int64_t halo;       // tracer after the item's last one: the next item's
                         // first, or the sheet's first for a closed sheet; -1
                         // at the open end of a chain
-    int64_t halo_shift; // added to the halo position (winding * nx * 2^32)
+    uint32_t halo_shift; // added to the halo position (winding * 2^30, modulo 2^32)
+    uint32_t pad;
 };
 
 // The two more tracers a piecewise-linear particle's gradient needs (Sec. 2.5):
 // the one before the item's first and the one after its halo; -1 when the
 // sheet has none there (open ends).  The shifts move a closed sheet's other
-// end by one winding (winding * nx * 2^32).
+// end by one winding (in position units, modulo 2^32).
 struct WorkItemPL {
     int64_t prev;
-    int64_t prev_shift;
     int64_t next2;
-    int64_t next2_shift;
+    uint32_t prev_shift;   // winding * 2^30 modulo 2^32, subtracted or added
+    uint32_t next2_shift;
 };
 
 // Per-step sums every block adds into and the epilogue reads: the kinetic
@@ -106,7 +107,7 @@ struct SimScalars {
 };
 
 struct SimDev {
-    int64_t *U[2];
+    uint32_t *U[2];
     float *V[2];
     const int32_t *Qh;          // may be null
     unsigned long long *mesh;
@@ -124,7 +125,8 @@ struct SimDev {
                                 // sheets: the particle starting at the tracer)
     int32_t n_items;
     int32_t hist_len;
-    NxDiv div;
+    int32_t nx;
+    int32_t pad0;
     double e_scale;             // Ek_j = K_j * e_scale
     double E_scale;             // E_j  = K_j * E_scale
     double rho_scale;           // rho_j = (nx mesh_j - Q) * rho_scale
@@ -135,7 +137,7 @@ struct SimDev {
     double p_scale;             // P  = p_scale * sum p 2^-p_u
     int32_t ke_u, p_u;          // the sums count units of 2^-ke_u and 2^-p_u
     int32_t strict;
-    int32_t pow2;               // nx is a power of two
+    int32_t pad1;
 };
 
 // Everything one launch of the step kernel needs.
@@ -163,17 +165,17 @@ struct LaunchArgs {
 #include <cuda_runtime.h>
 namespace sic {
 enum Mode { MODE_STEP = 0, MODE_DEPOSIT = 1, MODE_PUSH = 2 };
-cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s);
+cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, cudaStream_t s);
 cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s);
 cudaError_t launch_refine_count(const SimDev &sim, long long lfix, int32_t *splits, cudaStream_t s);
-cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, int64_t *U2, float *V2,
+cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, uint32_t *U2, float *V2,
                                   int32_t *Q2, cudaStream_t s);
-cudaError_t launch_moments(const SimDev &sim, int weighting, double dx, double unit_q, double unit_v, double *n,
-                           double *j, cudaStream_t s);
-cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,
+cudaError_t launch_moments(const SimDev &sim, int weighting, double box_length, double unit_q, double unit_v,
+                           double *n, double *j, cudaStream_t s);
+cudaError_t launch_expand_horizontal(uint32_t *U, float *V, const uint32_t *u_template, int32_t n_template,
                                      const float *v_sheet, const int64_t *sheet_offset, int32_t n_sheets,
                                      cudaStream_t s);
-int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2);
+int step_blocks_per_sm(int nx_max, Mode mode, bool per_q);
 size_t step_smem_bytes(int nx_max, bool staged, bool per_q);
 bool step_staged(int nx_max, bool per_q);
 void count_launches(int64_t n);

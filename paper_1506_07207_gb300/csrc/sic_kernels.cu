@@ -19,6 +19,11 @@
 //      diagnostic row, and the buffer swap.  The block then moves to the
 //      simulation with the most unclaimed items, until none has any.
 //
+// Positions are 32-bit: P = x / L 2^30 modulo 2^32 (2 bits of winding).  The
+// cell coordinate of a position, 32.32 fixed point with the cell in [0, nx),
+// is one multiply (P 2^2) nx; a segment is the 32-bit difference of its ends'
+// P times nx 2^2, so both ends are known in the frame of the lower one.
+//
 // Deposit arithmetic: a segment [a, b] of q units in 32.32 fixed-point cell
 // coordinates gives its first cell F = round(q (e_1 - a) / (b - a)) (FP32,
 // with an approximate reciprocal, clamped to [0, q]), every whole cell inside
@@ -47,64 +52,46 @@ constexpr int WT = SIC_K1_WARP_TRACERS;
 __device__ __forceinline__ int cell_of(long long u) { return (int)(u >> 32); }
 __device__ __forceinline__ unsigned frac_of(long long u) { return (unsigned)(unsigned long long)u; }
 
-// floor-mod of a cell number into [0, nx) for |c| < 2^30
-template <bool POW2>
-__device__ __forceinline__ int wrap_cell(int c, const NxDiv &d)
+// 32.32 fixed-point cell coordinate of a position P (x / L 2^30 modulo 2^32):
+// the cell in [0, nx) in the high word, the fraction of the cell in the low
+// word, exactly (one 32 x 32 -> 64 multiply of the box fraction P 2^2 by nx)
+__device__ __forceinline__ long long cell_coord(unsigned p, int nx)
 {
-    if (POW2)
-        return c & (d.nx - 1);
-    const unsigned n = (unsigned)c + (unsigned)d.offset;
-    const unsigned t = __umulhi(d.magic, n);
-    const unsigned q = (t + ((n - t) >> 1)) >> d.shift;
-    return (int)(n - q * (unsigned)d.nx);
+    return (long long)((unsigned long long)(p << SIC_POS_WIND_BITS) * (unsigned)nx);
+}
+
+// The segment from position pa to pb in 32.32 cell units: the 32-bit
+// difference of the positions (exact for segments shorter than 2 box lengths)
+// times nx 2^2
+__device__ __forceinline__ long long seg_span(unsigned pa, unsigned pb, int nx4)
+{
+    return (long long)(int)(pb - pa) * (long long)nx4;
 }
 
 // fraction of a cell in [0, 1) from the low word (its top 23 bits)
-__device__ __forceinline__ float frac_float(long long u)
+__device__ __forceinline__ float frac_float(unsigned lo)
 {
-    return __fsub_rn(__uint_as_float(0x3f800000u | (frac_of(u) >> 9)), 1.0f);
-}
-
-// v cells -> 32.32 fixed point, v * 2^32 rounded to an integer; 32-bit
-// conversions only (|v| < 2^31)
-__device__ __forceinline__ long long to_fixed(float v)
-{
-    const float h = floorf(v);
-    const int hi = __float2int_rz(h);
-    const unsigned lo = __float2uint_rn(__fmul_rn(__fsub_rn(v, h), 4294967296.0f));
-    return (long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned long long)lo);
+    return __fsub_rn(__uint_as_float(0x3f800000u | (lo >> 9)), 1.0f);
 }
 
 // gather (linear weighting between nodes j and j+1), kick, drift; j is the
-// cell of the new position on return
-template <bool POW2>
-__device__ __forceinline__ void push_one(long long &u, float &v, int &j, const float *ek, const NxDiv &d,
-                                         float ks, int drift, unsigned &rerr)
+// cell of the new position on return.  The drift adds the velocity rounded
+// to whole position units (exact integer arithmetic, wrapping modulo 4 box
+// lengths); a step of half a box or more sets bit 30 or 31 of rerr.
+__device__ __forceinline__ void push_one(unsigned &p, float &v, int &j, const float *ek, int nx, float ks,
+                                         int drift, unsigned &rerr)
 {
-    const int c = cell_of(u);
-    j = wrap_cell<POW2>(c, d);
+    const long long c = cell_coord(p, nx);
+    j = cell_of(c);
     const float e0 = ek[j], e1 = ek[j + 1];  // ek[nx] repeats ek[0]
-    const float a = __fmaf_rn(frac_float(u), __fsub_rn(e1, e0), e0);
+    const float a = __fmaf_rn(frac_float(frac_of(c)), __fsub_rn(e1, e0), e0);
     const float vn = __fmaf_rn(ks, a, v);
     v = vn;
     if (drift) {
-        const long long nu = u + to_fixed(vn);
-        const int cn = cell_of(nu);
-        if (POW2) {
-            j = cn & (d.nx - 1);
-        } else {
-            const int dc = cn - c;
-            if (dc >= -d.nx && dc < d.nx) {
-                int t = j + dc;
-                t += (t < 0) ? d.nx : 0;
-                t -= (t >= d.nx) ? d.nx : 0;
-                j = t;
-            } else {
-                j = wrap_cell<false>(cn, d);
-            }
-        }
-        rerr |= (unsigned)(cn + (1 << 30));  // bit 31 set: |cell| >= 2^30
-        u = nu;
+        const int d = __float2int_rn(vn);
+        rerr |= (unsigned)(d + (1 << 29));
+        p += (unsigned)d;
+        j = cell_of(cell_coord(p, nx));
     }
 }
 
@@ -521,19 +508,18 @@ __device__ __forceinline__ void desc_wait()
 // Lane 0 of a warp: start the bulk copies of item W (and its halo when the
 // halo is the next tracer in memory) into one stage.
 template <bool PER_Q>
-__device__ __forceinline__ void stage_issue(const WorkItem &W, const long long *Uin, const float *Vin,
+__device__ __forceinline__ void stage_issue(const WorkItem &W, const unsigned *Uin, const float *Vin,
                                             const int32_t *Qh, char *st, unsigned long long *bar)
 {
     const bool contiguous_halo = (W.halo == W.t0 + W.count);
     const int n = W.count + (contiguous_halo ? 1 : 0);
-    const unsigned bu = (unsigned)(n * 8 + 15) & ~15u;
-    const unsigned bv = (unsigned)(n * 4 + 15) & ~15u;
+    const unsigned b = (unsigned)(n * 4 + 15) & ~15u;  // the same for positions, velocities, charges
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, bu + bv + (PER_Q ? bv : 0u));
-    bulk_g2s(st, Uin + W.t0, bu, bar);
-    bulk_g2s(st + kStageBytesU, Vin + W.t0, bv, bar);
+    mbar_expect_tx(bar, (PER_Q ? 3u : 2u) * b);
+    bulk_g2s(st, Uin + W.t0, b, bar);
+    bulk_g2s(st + kStageBytesU, Vin + W.t0, b, bar);
     if (PER_Q)
-        bulk_g2s(st + kStageBytesU + kStageBytesV, Qh + W.t0, bv, bar);
+        bulk_g2s(st + kStageBytesU + kStageBytesV, Qh + W.t0, b, bar);
 }
 
 struct Shared {
@@ -543,7 +529,7 @@ struct Shared {
     } desc[NW][2];  // staging: each warp's descriptors of the items in its two stages
     int diff_used;
     int last;
-    long long pl_prev[NW];   // piecewise-linear particles: each warp's tracer before its item
+    unsigned pl_prev[NW];    // piecewise-linear particles: each warp's tracer before its item
     int pl_prevq[NW];
     int taken;               // items of the current simulation the block's warps took
     int pick_n[NW], pick_s[NW];  // per warp: most unclaimed items, in which slot
@@ -622,7 +608,7 @@ __device__ __forceinline__ float i128_to_float(__int128 v, int e2)
 __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *sm, float *sE, Shared &sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nx = S.div.nx;
+    const int nx = S.nx;
     for (int j = tid; j < nx; j += B) {
         const unsigned long long mv = __ldcg(S.mesh + j);
         sm[j] = mv;
@@ -720,6 +706,13 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         sc->maxseg = mm;
         if (S.strict && mm > ((long long)nx << 16))
             sc->err |= SIC_ERR_SEGLONG;
+        // the position format holds a segment exactly while it is shorter than
+        // 2 box lengths; one of 1.5 or more ends the run with a range error.
+        // Each end moves less than half a box per step, so a segment cannot
+        // get from below 1.5 box lengths to 2.5 or more (where its difference
+        // would alias to less than 1.5) in one step unseen
+        if (mm >= ((long long)(3 * nx) << 15))
+            sc->err |= SIC_ERR_RANGE;
     }
 }
 
@@ -756,39 +749,39 @@ __device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int 
 
 // One work item (up to 32 R tracers, R per lane) of the current simulation.
 // FULL: the item has all 32 R tracers, so no lane needs a bounds test.
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool FULL, bool STAGED, bool GEN, class MID>
-__device__ __forceinline__ void do_item(const WorkItem &W, const long long *__restrict__ Uin,
-                                        const float *__restrict__ Vin, long long *__restrict__ Uout,
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool FULL, bool STAGED, bool GEN, class MID>
+__device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__restrict__ Uin,
+                                        const float *__restrict__ Vin, unsigned *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
                                         const float *ek, const Hist &hist, unsigned long long *diff,
-                                        Shared &sh, const NxDiv &dv, float ks, int drift, unsigned &rerr,
+                                        Shared &sh, int nx, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, long long &ake, long long &ap, unsigned &mseg,
                                         const WorkItemPL *pw, int dep, int segq, const MID &mid)
 {
-    const long long *stU = reinterpret_cast<const long long *>(st);
+    const unsigned *stU = reinterpret_cast<const unsigned *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
     const int *stQ = reinterpret_cast<const int *>(st + kStageBytesU + kStageBytesV);
     const int lane = threadIdx.x & 31;
-    const int nx = dv.nx;
+    const int nx4 = nx << SIC_POS_WIND_BITS;
     const int m = FULL ? WT : W.count;
     const long long base = W.t0;
     const int l0 = lane * R;
     const int rn = FULL ? R : max(0, min(R, m - l0));
     const int lane_last = FULL ? 31 : (m - 1) / R;
 
-    long long u[R];
+    unsigned u[R];
     float v[R];
     int q[R];
     int jn[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        u[r] = 0;
+        u[r] = 0u;
         v[r] = 0.f;
         q[r] = W.qh;
         jn[r] = 0;
     }
     // the tracer after the item's last one (next item, or the sheet's first)
-    long long hu = 0;
+    unsigned hu = 0u;
     float hv = 0.f;
     int hq = W.qh, hj = 0;
     bool has_halo = false;
@@ -808,65 +801,32 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 hq = Qh[W.halo];
         }
     }
-    if (STAGED) {
+    static_assert(R % 4 == 0, "a lane's tracers load as 16-byte vectors");
+    if (STAGED || FULL || rn == R) {
         // the stage holds the whole item (and garbage past its end)
-        const longlong2 *pu = reinterpret_cast<const longlong2 *>(stU + l0);
+        const unsigned *pu = STAGED ? stU + l0 : Uin + base + l0;
+        const float *pvv = STAGED ? stV + l0 : Vin + base + l0;
+        const int *pqq = STAGED ? stQ + l0 : Qh + base + l0;
 #pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            const longlong2 t = pu[k];
-            u[2 * k] = t.x;
-            u[2 * k + 1] = t.y;
-        }
-        if (PUSH) {
-            const float4 *pv = reinterpret_cast<const float4 *>(stV + l0);
-#pragma unroll
-            for (int k = 0; k < R / 4; ++k) {
-                const float4 t = pv[k];
-                v[4 * k] = t.x;
-                v[4 * k + 1] = t.y;
-                v[4 * k + 2] = t.z;
-                v[4 * k + 3] = t.w;
+        for (int k = 0; k < R / 4; ++k) {
+            const uint4 t = reinterpret_cast<const uint4 *>(pu)[k];
+            u[4 * k] = t.x;
+            u[4 * k + 1] = t.y;
+            u[4 * k + 2] = t.z;
+            u[4 * k + 3] = t.w;
+            if (PUSH) {
+                const float4 f = reinterpret_cast<const float4 *>(pvv)[k];
+                v[4 * k] = f.x;
+                v[4 * k + 1] = f.y;
+                v[4 * k + 2] = f.z;
+                v[4 * k + 3] = f.w;
             }
-        }
-        if (PER_Q) {
-            const int4 *pq = reinterpret_cast<const int4 *>(stQ + l0);
-#pragma unroll
-            for (int k = 0; k < R / 4; ++k) {
-                const int4 t = pq[k];
-                q[4 * k] = t.x;
-                q[4 * k + 1] = t.y;
-                q[4 * k + 2] = t.z;
-                q[4 * k + 3] = t.w;
-            }
-        }
-    } else if (FULL || rn == R) {
-        const longlong2 *pu = reinterpret_cast<const longlong2 *>(Uin + base + l0);
-#pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            const longlong2 t = pu[k];
-            u[2 * k] = t.x;
-            u[2 * k + 1] = t.y;
-        }
-        if (PUSH) {
-            const float4 *pv = reinterpret_cast<const float4 *>(Vin + base + l0);
-#pragma unroll
-            for (int k = 0; k < R / 4; ++k) {
-                const float4 t = pv[k];
-                v[4 * k] = t.x;
-                v[4 * k + 1] = t.y;
-                v[4 * k + 2] = t.z;
-                v[4 * k + 3] = t.w;
-            }
-        }
-        if (PER_Q) {
-            const int4 *pq = reinterpret_cast<const int4 *>(Qh + base + l0);
-#pragma unroll
-            for (int k = 0; k < R / 4; ++k) {
-                const int4 t = pq[k];
-                q[4 * k] = t.x;
-                q[4 * k + 1] = t.y;
-                q[4 * k + 2] = t.z;
-                q[4 * k + 3] = t.w;
+            if (PER_Q) {
+                const int4 c = reinterpret_cast<const int4 *>(pqq)[k];
+                q[4 * k] = c.x;
+                q[4 * k + 1] = c.y;
+                q[4 * k + 2] = c.z;
+                q[4 * k + 3] = c.w;
             }
         }
     } else {
@@ -888,7 +848,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         for (int r = 0; r < R; ++r) {
             if (FULL || r < rn) {
                 const float vo = v[r];
-                push_one<POW2>(u[r], v[r], jn[r], ek, dv, ks, drift, rerr);
+                push_one(u[r], v[r], jn[r], ek, nx, ks, drift, rerr);
                 const float vn = v[r];
                 if (PER_Q) {
                     const float qq = __int2float_rn(q[r]);
@@ -902,17 +862,16 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         }
         if (has_halo) {
             unsigned ignore = 0;
-            push_one<POW2>(hu, hv, hj, ek, dv, ks, drift, ignore);
+            push_one(hu, hv, hj, ek, nx, ks, drift, ignore);
         }
         if (FULL || rn == R) {
-            longlong2 *pu = reinterpret_cast<longlong2 *>(Uout + base + l0);
 #pragma unroll
-            for (int k = 0; k < R / 2; ++k)
-                __stcs(pu + k, make_longlong2(u[2 * k], u[2 * k + 1]));
-            float4 *pv = reinterpret_cast<float4 *>(Vout + base + l0);
-#pragma unroll
-            for (int k = 0; k < R / 4; ++k)
-                __stcs(pv + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+            for (int k = 0; k < R / 4; ++k) {
+                __stcs(reinterpret_cast<uint4 *>(Uout + base + l0) + k,
+                       make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]));
+                __stcs(reinterpret_cast<float4 *>(Vout + base + l0) + k,
+                       make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+            }
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -926,16 +885,16 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (FULL || r < rn)
-                jn[r] = wrap_cell<POW2>(cell_of(u[r]), dv);
+                jn[r] = cell_of(cell_coord(u[r], nx));
         if (has_halo)
-            hj = wrap_cell<POW2>(cell_of(hu), dv);
+            hj = cell_of(cell_coord(hu, nx));
     }
     mid();  // staging: the next item's copies start here
 
     // piecewise-linear particles (pw set): the tracer before the item and the
     // one after its halo too, for the gradients of the item's first and last
     // particles (Sec. 2.5)
-    long long pu = 0, nu2 = 0;
+    unsigned pu = 0u, nu2 = 0u;
     int pq = W.qh, nq2 = W.qh;
     bool has_prev = false, has_next2 = false;
     if (GEN && DEPOSIT && pw != nullptr) {
@@ -950,9 +909,9 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 float pv = Vin[ip];
                 int pj;
                 unsigned ignore = 0;
-                push_one<POW2>(pu, pv, pj, ek, dv, ks, drift, ignore);
+                push_one(pu, pv, pj, ek, nx, ks, drift, ignore);
             }
-            pu += pw->prev_shift;
+            pu -= pw->prev_shift;
         }
         if (lane == lane_last && has_next2) {
             nu2 = Uin[in2];
@@ -962,7 +921,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 float nv = Vin[in2];
                 int nj;
                 unsigned ignore = 0;
-                push_one<POW2>(nu2, nv, nj, ek, dv, ks, drift, ignore);
+                push_one(nu2, nv, nj, ek, nx, ks, drift, ignore);
             }
             nu2 += pw->next2_shift;
         }
@@ -982,8 +941,9 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 if (dep == SIC_DEPOSIT_PIC_NGP) {
                     run.add(jn[r], Qt);
                 } else {
-                    const long long pc = u[r] - (1ll << 31);  // half a cell back: centres on integers
-                    const int j0 = wrap_cell<POW2>(cell_of(pc), dv);
+                    const long long pc = cell_coord(u[r], nx) - (1ll << 31);  // centres on integers
+                    int j0 = cell_of(pc);                                      // -1 before the first centre
+                    j0 += (j0 < 0) ? nx : 0;
                     const int j1 = (j0 + 1 == nx) ? 0 : j0 + 1;
                     const long long p1 =
                         (long long)(((unsigned long long)Qt * (unsigned long long)frac_of(pc) + (1ull << 31)) >> 32);
@@ -997,18 +957,14 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         hu += W.halo_shift;  // closing segment: the sheet's first tracer one winding on
         // publish the new positions (and charges) of the item in shared
         // memory, so the cross-cell segments can be shared out over the warp
-        long long *pts = reinterpret_cast<long long *>(st);
+        unsigned *pts = reinterpret_cast<unsigned *>(st);
         int *qpts = reinterpret_cast<int *>(st + WarpBuf<PER_Q, STAGED>::q_offset);
         if (FULL || rn == R) {
-            longlong2 *pp = reinterpret_cast<longlong2 *>(pts + l0);
 #pragma unroll
-            for (int k = 0; k < R / 2; ++k)
-                pp[k] = make_longlong2(u[2 * k], u[2 * k + 1]);
-            if (PER_Q) {
-                int4 *pq = reinterpret_cast<int4 *>(qpts + l0);
-#pragma unroll
-                for (int k = 0; k < R / 4; ++k)
-                    pq[k] = make_int4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+            for (int k = 0; k < R / 4; ++k) {
+                reinterpret_cast<uint4 *>(pts + l0)[k] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+                if (PER_Q)
+                    reinterpret_cast<int4 *>(qpts + l0)[k] = make_int4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
             }
         } else {
 #pragma unroll
@@ -1034,7 +990,8 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             sh.pl_prevq[threadIdx.x >> 5] = pq;
         }
         // the next tracer of each lane's last one comes from the lane above
-        const long long nu = __shfl_down_sync(0xffffffffu, u[0], 1);
+        const unsigned nu = __shfl_down_sync(0xffffffffu, u[0], 1);
+        const int nj = __shfl_down_sync(0xffffffffu, jn[0], 1);
         const int nq = __shfl_down_sync(0xffffffffu, q[0], 1);
         const int qs_sheet = 2 * W.qh;
         __syncwarp();
@@ -1042,33 +999,39 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
         // segments inside one cell: whole charges summed per lane into three
         // buckets for the cells c0, c0 + 1, c0 + 2 of its first tracer (a lane
         // that reaches other cells falls back to run merging); the segments
-        // that cross a cell edge are marked for the second pass
+        // that cross a cell edge are marked for the second pass.  A segment
+        // lies inside one cell when its two ends share a cell and it is
+        // shorter than half a box (a longer one could end in the same cell
+        // one box on).
         unsigned cross = 0;
         {
-            const int c0 = cell_of(u[0]);
+            const int c0 = jn[0];
             unsigned b0 = 0, b1 = 0, b2 = 0;
             bool wide = false;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (FULL || r < rn) {
-                    long long ub;
-                    int qb;
+                    unsigned ub;
+                    int jb, qb;
                     bool seg = true;
                     if (r + 1 < R && (FULL || r + 1 < rn)) {
                         ub = u[r + 1 < R ? r + 1 : r];
+                        jb = jn[r + 1 < R ? r + 1 : r];
                         qb = q[r + 1 < R ? r + 1 : r];
                     } else if (lane < lane_last) {
                         ub = nu;
+                        jb = nj;
                         qb = nq;
                     } else {
                         ub = hu;
+                        jb = hj;
                         qb = hq;
                         seg = has_halo;
                     }
-                    const int cr = cell_of(u[r]);
-                    const bool same = seg && cr == cell_of(ub);
+                    const bool shrt = (ub - u[r] + (1u << 29)) < (1u << 30);
+                    const bool same = seg && shrt && jn[r] == jb;
                     const unsigned qv = (unsigned)(PER_Q ? (segq ? q[r] : q[r] + qb) : qs_sheet);
-                    const int d = cr - c0;
+                    const int d = jn[r] - c0;
                     b0 += (same && d == 0) ? qv : 0u;
                     b1 += (same && d == 1) ? qv : 0u;
                     b2 += (same && d == 2) ? qv : 0u;
@@ -1077,10 +1040,10 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 }
             }
             if (__builtin_expect(!wide, 1)) {
-                const int j1 = (jn[0] + 1 == nx) ? 0 : jn[0] + 1;
+                const int j1 = (c0 + 1 == nx) ? 0 : c0 + 1;
                 const int j2 = (j1 + 1 == nx) ? 0 : j1 + 1;
                 if (b0)
-                    hist.add(jn[0], b0);
+                    hist.add(c0, b0);
                 if (b1)
                     hist.add(j1, b1);
                 if (b2)
@@ -1089,22 +1052,18 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 RunAcc acc(hist);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (FULL || r < rn) {
-                        long long ub;
+                    if ((FULL || r < rn) && !((cross >> r) & 1u)) {
                         int qb;
                         bool seg = true;
                         if (r + 1 < R && (FULL || r + 1 < rn)) {
-                            ub = u[r + 1 < R ? r + 1 : r];
                             qb = q[r + 1 < R ? r + 1 : r];
                         } else if (lane < lane_last) {
-                            ub = nu;
                             qb = nq;
                         } else {
-                            ub = hu;
                             qb = hq;
                             seg = has_halo;
                         }
-                        if (seg && cell_of(u[r]) == cell_of(ub))
+                        if (seg)
                             acc.add(jn[r], PER_Q ? (segq ? q[r] : q[r] + qb) : qs_sheet);
                     }
                 }
@@ -1136,8 +1095,10 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             }
             __syncwarp();
             DirectAdd acc{hist};
-            // piecewise-linear particles: kappa of the particle at idx; 0 keeps
-            // it a box (no neighbour on one side, or a box length or longer)
+            // piecewise-linear particles: kappa of the particle at idx, from
+            // its neighbours' positions in the frame of its own lower end ua;
+            // 0 keeps it a box (no neighbour on one side, or a box length or
+            // longer)
             auto kappa_of = [&](int idx, long long ua, long long ub, int qs) -> float {
                 const bool hp = idx > 0 || has_prev;
                 const bool hn = idx + 2 < m || (idx + 2 == m && W.halo >= 0) || (idx + 2 == m + 1 && has_next2);
@@ -1145,8 +1106,9 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                 if (!(hp && hn && len < ((long long)nx << 32)))
                     return 0.f;
                 const int w8 = threadIdx.x >> 5;
-                const long long up = idx > 0 ? pts[idx - 1] : sh.pl_prev[w8];
-                const long long un = pts[idx + 2];
+                const unsigned pp = idx > 0 ? pts[idx - 1] : sh.pl_prev[w8];
+                const long long up = ua - seg_span(pp, pts[idx], nx4);
+                const long long un = ub + seg_span(pts[idx + 1], pts[idx + 2], nx4);
                 const int qp = PER_Q ? (idx > 0 ? qpts[idx - 1] : sh.pl_prevq[w8]) + (segq ? 0 : qpts[idx]) : qs_sheet;
                 const int qn = PER_Q ? qpts[idx + 1] + (segq ? 0 : qpts[idx + 2]) : qs_sheet;
                 return pl_kappa(up, ua, ub, un, qp, qs, qn);
@@ -1154,20 +1116,21 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
             bool any_long = false;
             for (int k = lane; k < total; k += 32) {
                 const int idx = tasks[k];
-                const long long ua = pts[idx], ub = pts[idx + 1];
+                const unsigned pa = pts[idx], pb = pts[idx + 1];
+                const long long ua = cell_coord(pa, nx);
+                const long long ub = ua + seg_span(pa, pb, nx4);
+                const int ja = cell_of(ua), jb = cell_of(cell_coord(pb, nx));
                 const int qs = PER_Q ? qpts[idx] + (segq ? 0 : qpts[idx + 1]) : qs_sheet;
                 const float kappa = (GEN && pw != nullptr) ? kappa_of(idx, ua, ub, qs) : 0.f;
                 if (kappa == 0.f) {
-                    emit_cross(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs, nx,
-                               acc, diff, &sh.diff_used, mseg);
+                    emit_cross(ua, ja, ub, jb, qs, nx, acc, diff, &sh.diff_used, mseg);
                 } else {
                     const int cuts = cell_of(ua) > cell_of(ub) ? cell_of(ua) - cell_of(ub) : cell_of(ub) - cell_of(ua);
                     if (cuts >= kWarpCuts) {
                         tasks[k] = (unsigned short)(idx | 0x8000);  // for the whole warp, below
                         any_long = true;
                     } else {
-                        emit_cross_linear(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv),
-                                          qs, kappa, nx, acc, mseg);
+                        emit_cross_linear(ua, ja, ub, jb, qs, kappa, nx, acc, mseg);
                     }
                 }
             }
@@ -1182,9 +1145,11 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
                         const int src = __ffs(bal) - 1;
                         bal &= bal - 1u;
                         const int idx = tasks[base + src] & 0x7fff;
-                        const long long ua = pts[idx], ub = pts[idx + 1];
+                        const unsigned pa = pts[idx], pb = pts[idx + 1];
+                        const long long ua = cell_coord(pa, nx);
+                        const long long ub = ua + seg_span(pa, pb, nx4);
                         const int qs = PER_Q ? qpts[idx] + (segq ? 0 : qpts[idx + 1]) : qs_sheet;
-                        emit_linear_warp(ua, wrap_cell<POW2>(cell_of(ua), dv), ub, wrap_cell<POW2>(cell_of(ub), dv), qs,
+                        emit_linear_warp(ua, cell_of(ua), ub, cell_of(cell_coord(pb, nx)), qs,
                                          kappa_of(idx, ua, ub, qs), nx, acc, mseg, lane);
                     }
                 }
@@ -1203,7 +1168,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const long long *__re
     }
 }
 
-template <bool PUSH, bool DEPOSIT, bool PER_Q, bool POW2, bool STAGED, bool GEN>
+template <bool PUSH, bool DEPOSIT, bool PER_Q, bool STAGED, bool GEN>
 __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1255,12 +1220,11 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         const SimDev &S = A.sims[cur];
         const WorkItem *items = S.items;
         const int n_s = A.slot_begin[cur + 1] - A.slot_begin[cur];
-        const NxDiv dv = S.div;
-        const int nx = dv.nx;
+        const int nx = S.nx;
         const int src = (int)S.sc->buf;
-        const long long *Uin = reinterpret_cast<const long long *>(S.U[src]);
+        const unsigned *Uin = S.U[src];
         const float *Vin = S.V[src];
-        long long *Uout = reinterpret_cast<long long *>(S.U[src ^ 1]);
+        unsigned *Uout = S.U[src ^ 1];
         float *Vout = S.V[src ^ 1];
         const int32_t *Qh = S.Qh;
         unsigned *cursor = A.cursor + cur;
@@ -1371,25 +1335,25 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     };
                     char *st = my_stage + s * WarpBuf<PER_Q, true>::stage;
                     if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                        sh, dv, ks, drift, rerr, st, tasks, ake, ap,
-                                                                        mseg, plw, S.deposit, S.seg_q, mid);
+                        do_item<PUSH, DEPOSIT, PER_Q, true, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
+                                                                  nx, ks, drift, rerr, st, tasks, ake, ap, mseg, plw,
+                                                                  S.deposit, S.seg_q, mid);
                     else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
-                                                                         diff, sh, dv, ks, drift, rerr, st, tasks,
-                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q, mid);
+                        do_item<PUSH, DEPOSIT, PER_Q, false, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
+                                                                   nx, ks, drift, rerr, st, tasks, ake, ap, mseg, plw,
+                                                                   S.deposit, S.seg_q, mid);
                     __syncwarp();
                     s ^= 1;
                 } else {
                     auto mid = []() {};
                     if (W.count == WT)
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, true, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff,
-                                                                         sh, dv, ks, drift, rerr, my_stage, tasks,
-                                                                         ake, ap, mseg, plw, S.deposit, S.seg_q, mid);
+                        do_item<PUSH, DEPOSIT, PER_Q, true, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
+                                                                   nx, ks, drift, rerr, my_stage, tasks, ake, ap, mseg,
+                                                                   plw, S.deposit, S.seg_q, mid);
                     else
-                        do_item<PUSH, DEPOSIT, PER_Q, POW2, false, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist,
-                                                                          diff, sh, dv, ks, drift, rerr, my_stage,
-                                                                          tasks, ake, ap, mseg, plw, S.deposit, S.seg_q, mid);
+                        do_item<PUSH, DEPOSIT, PER_Q, false, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
+                                                                    nx, ks, drift, rerr, my_stage, tasks, ake, ap, mseg,
+                                                                    plw, S.deposit, S.seg_q, mid);
                 }
             }
             if (!took) {
@@ -1432,7 +1396,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     atomicAdd(S.mesh + j, h);
             }
         }
-        if (rerr >> 31)
+        if (rerr >> 30)  // a step of half a box or more, or a sum that is not finite
             atomicOr(&S.sc->err, SIC_ERR_RANGE);
         rerr = 0;
         if (STAGED && timed_out && lane == 0)
@@ -1520,12 +1484,12 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     }
 }
 
-template <bool P, bool D, bool Q, bool T, bool G, bool L>
+template <bool P, bool D, bool Q, bool G, bool L>
 cudaError_t prep(size_t smem)
 {
     static size_t done = 0;
     if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, T, G, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step<P, D, Q, G, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess)
             return e;
@@ -1534,26 +1498,26 @@ cudaError_t prep(size_t smem)
     return cudaSuccess;
 }
 
-template <bool P, bool D, bool Q, bool T, bool G, bool L>
+template <bool P, bool D, bool Q, bool G, bool L>
 cudaError_t run(const LaunchArgs &a, int grid, cudaStream_t s)
 {
     const size_t smem = step_smem_bytes(a.nx_max, G, Q);
-    cudaError_t e = prep<P, D, Q, T, G, L>(smem);
+    cudaError_t e = prep<P, D, Q, G, L>(smem);
     if (e != cudaSuccess)
         return e;
-    k_step<P, D, Q, T, G, L><<<grid, B, smem, s>>>(a);
+    k_step<P, D, Q, G, L><<<grid, B, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <bool P, bool D, bool Q, bool T, bool G>
+template <bool P, bool D, bool Q, bool G>
 int occ(int nx_max)
 {
     const size_t smem = step_smem_bytes(nx_max, G, Q);
-    if (prep<P, D, Q, T, G, false>(smem) != cudaSuccess)
+    if (prep<P, D, Q, G, false>(smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, T, G, false>, B, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<P, D, Q, G, false>, B, smem) != cudaSuccess)
         return 0;
     return n;
 }
@@ -1561,24 +1525,17 @@ int occ(int nx_max)
 // a.gen: some simulation of the launch deposits other than box particles;
 // that variant handles every kind
 template <bool P, bool D, bool G>
-cudaError_t run_pd(const LaunchArgs &a, int grid, bool per_q, bool pow2, cudaStream_t s)
+cudaError_t run_pd(const LaunchArgs &a, int grid, bool per_q, cudaStream_t s)
 {
-    if (a.gen) {
-        if (per_q)
-            return pow2 ? run<P, D, true, true, G, true>(a, grid, s) : run<P, D, true, false, G, true>(a, grid, s);
-        return pow2 ? run<P, D, false, true, G, true>(a, grid, s) : run<P, D, false, false, G, true>(a, grid, s);
-    }
-    if (per_q)
-        return pow2 ? run<P, D, true, true, G, false>(a, grid, s) : run<P, D, true, false, G, false>(a, grid, s);
-    return pow2 ? run<P, D, false, true, G, false>(a, grid, s) : run<P, D, false, false, G, false>(a, grid, s);
+    if (a.gen)
+        return per_q ? run<P, D, true, G, true>(a, grid, s) : run<P, D, false, G, true>(a, grid, s);
+    return per_q ? run<P, D, true, G, false>(a, grid, s) : run<P, D, false, G, false>(a, grid, s);
 }
 
 template <bool P, bool D, bool G>
-int occ_pd(int nx_max, bool per_q, bool pow2)
+int occ_pd(int nx_max, bool per_q)
 {
-    if (per_q)
-        return pow2 ? occ<P, D, true, true, G>(nx_max) : occ<P, D, true, false, G>(nx_max);
-    return pow2 ? occ<P, D, false, true, G>(nx_max) : occ<P, D, false, false, G>(nx_max);
+    return per_q ? occ<P, D, true, G>(nx_max) : occ<P, D, false, G>(nx_max);
 }
 
 // The double-precision node field E_j and density rho_j of the latest
@@ -1589,7 +1546,7 @@ __global__ void __launch_bounds__(1024) k_field_out(const SimDev S)
     __shared__ long long s_w[NWW];
     __shared__ long long s_hi[NWW], s_lo[NWW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nx = S.div.nx;
+    const int nx = S.nx;
     const int per = (nx + BB - 1) / BB;
     const int j0 = min(tid * per, nx), j1 = min(j0 + per, nx);
     long long lsum = 0;
@@ -1637,7 +1594,7 @@ __global__ void __launch_bounds__(1024) k_field_out(const SimDev S)
     }
 }
 
-__global__ void k_expand_horizontal(int64_t *U, float *V, const int64_t *ut, int32_t n, const float *vs,
+__global__ void k_expand_horizontal(uint32_t *U, float *V, const uint32_t *ut, int32_t n, const float *vs,
                                     const int64_t *off, int32_t M)
 {
     const long long total = (long long)M * n;
@@ -1690,7 +1647,7 @@ static long long g_launches = 0;
 void count_launches(int64_t n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
 int64_t launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
-cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, bool pow2, cudaStream_t s)
+cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, cudaStream_t s)
 {
     switch (mode) {
     case MODE_STEP: {
@@ -1700,27 +1657,27 @@ cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool pe
         else if (a.staging == 2)
             staged = step_smem_bytes(a.nx_max, true, per_q) <= 227 * 1024;
         if (staged)
-            return run_pd<true, true, true>(a, grid, per_q, pow2, s);
-        return run_pd<true, true, false>(a, grid, per_q, pow2, s);
+            return run_pd<true, true, true>(a, grid, per_q, s);
+        return run_pd<true, true, false>(a, grid, per_q, s);
     }
     case MODE_DEPOSIT:
-        return run_pd<false, true, false>(a, grid, per_q, pow2, s);
+        return run_pd<false, true, false>(a, grid, per_q, s);
     default:
-        return run_pd<true, false, false>(a, grid, per_q, pow2, s);
+        return run_pd<true, false, false>(a, grid, per_q, s);
     }
 }
 
-int step_blocks_per_sm(int nx_max, Mode mode, bool per_q, bool pow2)
+int step_blocks_per_sm(int nx_max, Mode mode, bool per_q)
 {
     switch (mode) {
     case MODE_STEP:
         if (step_staged(nx_max, per_q))
-            return occ_pd<true, true, true>(nx_max, per_q, pow2);
-        return occ_pd<true, true, false>(nx_max, per_q, pow2);
+            return occ_pd<true, true, true>(nx_max, per_q);
+        return occ_pd<true, true, false>(nx_max, per_q);
     case MODE_DEPOSIT:
-        return occ_pd<false, true, false>(nx_max, per_q, pow2);
+        return occ_pd<false, true, false>(nx_max, per_q);
     default:
-        return occ_pd<true, false, false>(nx_max, per_q, pow2);
+        return occ_pd<true, false, false>(nx_max, per_q);
     }
 }
 
@@ -1731,7 +1688,7 @@ cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand_horizontal(int64_t *U, float *V, const int64_t *u_template, int32_t n_template,
+cudaError_t launch_expand_horizontal(uint32_t *U, float *V, const uint32_t *u_template, int32_t n_template,
                                      const float *v_sheet, const int64_t *sheet_offset, int32_t n_sheets,
                                      cudaStream_t s)
 {
@@ -1802,25 +1759,31 @@ __device__ void moments_one(double xa, double va, double xb, double vb, double q
     }
 }
 
-__global__ void k_moments(const SimDev S, int weighting, double dx, double unit_q, double unit_v, double *n,
+__global__ void k_moments(const SimDev S, int weighting, double L, double unit_q, double unit_v, double *n,
                           double *j)
 {
-    const int nx = S.div.nx;
+    const int nx = S.nx;
+    const double dx = L / nx;
     const int src = (int)S.sc->buf;
-    const long long *U = reinterpret_cast<const long long *>(S.U[src]);
+    const unsigned *U = S.U[src];
     const float *V = S.V[src];
+    const double box = L * 0x1p-32, unit_p = L * 0x1p-30;  // box fraction, position unit
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < S.n_items; it += gridDim.x * blockDim.x) {
         const WorkItem W = S.items[it];
         const long long last = W.t0 + W.count - 1;
         for (long long t = W.t0; t <= last; ++t) {
-            long long t1 = t + 1, shift = 0;
+            long long t1 = t + 1;
+            unsigned shift = 0u;
             if (t == last) {
                 if (W.halo < 0)
                     break;
                 t1 = W.halo;
                 shift = W.halo_shift;
             }
-            const double xa = (double)U[t] * dx * 0x1p-32, xb = (double)(U[t1] + shift) * dx * 0x1p-32;
+            // the particle's lower end inside the box, its far end one
+            // segment (the 32-bit position difference) away
+            const double xa = (double)(U[t] << SIC_POS_WIND_BITS) * box;
+            const double xb = xa + (double)(int)(U[t1] + shift - U[t]) * unit_p;
             const double va = (double)V[t] * unit_v, vb = (double)V[t1] * unit_v;
             const double qa = S.Qh ? (double)S.Qh[t] : (double)W.qh, qb = S.Qh ? (double)S.Qh[t1] : (double)W.qh;
             const double vbar = (qa + qb) > 0 ? (qa * va + qb * vb) / (qa + qb) : 0.5 * (va + vb);
@@ -1834,16 +1797,16 @@ __global__ void k_moments(const SimDev S, int weighting, double dx, double unit_
 
 }  // namespace
 
-cudaError_t launch_moments(const SimDev &sim, int weighting, double dx, double unit_q, double unit_v, double *n,
-                           double *j, cudaStream_t s)
+cudaError_t launch_moments(const SimDev &sim, int weighting, double box_length, double unit_q, double unit_v,
+                           double *n, double *j, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(n, 0, sizeof(double) * (size_t)sim.div.nx, s);
+    cudaError_t e = cudaMemsetAsync(n, 0, sizeof(double) * (size_t)sim.nx, s);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(j, 0, sizeof(double) * (size_t)sim.div.nx, s);
+        e = cudaMemsetAsync(j, 0, sizeof(double) * (size_t)sim.nx, s);
     if (e != cudaSuccess)
         return e;
     const int grid = (int)std::min<long long>(4096, ((long long)sim.n_items + 255) / 256);
-    k_moments<<<std::max(grid, 1), 256, 0, s>>>(sim, weighting, dx, unit_q, unit_v, n, j);
+    k_moments<<<std::max(grid, 1), 256, 0, s>>>(sim, weighting, box_length, unit_q, unit_v, n, j);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1854,17 +1817,17 @@ namespace sic {
 namespace {
 
 // ---------------------------------------------------------- refinement ----
-// Sec. 2.6: a particle longer than the refinement length (lfix, 32.32 cells)
-// gets a new tracer at its centre.  k_refine_count counts those particles per
-// work item; k_refine_scatter writes every tracer, and after each split
-// particle's first tracer the new one, into the new layout, with per-particle
-// charges: each half of a split particle gets half its charge (the first
-// floor(Q / 2), the second the rest).  One thread per work item.
-__device__ __forceinline__ bool refine_seg(const SimDev &S, const WorkItem &W, long long t, const long long *U,
-                                           long long &d, long long &t1)
+// Sec. 2.6: a particle longer than the refinement length (lfix, position
+// units) gets a new tracer at its centre.  k_refine_count counts those
+// particles per work item; k_refine_scatter writes every tracer, and after
+// each split particle's first tracer the new one, into the new layout, with
+// per-particle charges: each half of a split particle gets half its charge
+// (the first floor(Q / 2), the second the rest).  One thread per work item.
+__device__ __forceinline__ bool refine_seg(const WorkItem &W, long long t, const unsigned *U, long long &d,
+                                           long long &t1)
 {
     const long long last = W.t0 + W.count - 1;
-    long long shift = 0;
+    unsigned shift = 0u;
     t1 = t + 1;
     if (t == last) {
         if (W.halo < 0)
@@ -1872,37 +1835,37 @@ __device__ __forceinline__ bool refine_seg(const SimDev &S, const WorkItem &W, l
         t1 = W.halo;
         shift = W.halo_shift;
     }
-    d = U[t1] + shift - U[t];
+    d = (long long)(int)(U[t1] + shift - U[t]);
     return true;
 }
 
 __global__ void k_refine_count(const SimDev S, long long lfix, int32_t *splits)
 {
-    const long long *U = reinterpret_cast<const long long *>(S.U[S.sc->buf & 1]);
+    const unsigned *U = S.U[S.sc->buf & 1];
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < S.n_items; it += gridDim.x * blockDim.x) {
         const WorkItem W = S.items[it];
         int c = 0;
         for (long long t = W.t0; t < W.t0 + W.count; ++t) {
             long long d, t1;
-            if (refine_seg(S, W, t, U, d, t1) && (d > lfix || -d > lfix))
+            if (refine_seg(W, t, U, d, t1) && (d > lfix || -d > lfix))
                 ++c;
         }
         splits[it] = c;
     }
 }
 
-__global__ void k_refine_scatter(const SimDev S, long long lfix, const int64_t *out_base, int64_t *U2, float *V2,
+__global__ void k_refine_scatter(const SimDev S, long long lfix, const int64_t *out_base, uint32_t *U2, float *V2,
                                  int32_t *Q2)
 {
     const int b = (int)(S.sc->buf & 1);
-    const long long *U = reinterpret_cast<const long long *>(S.U[b]);
+    const unsigned *U = S.U[b];
     const float *V = S.V[b];
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < S.n_items; it += gridDim.x * blockDim.x) {
         const WorkItem W = S.items[it];
         long long out = out_base[it];
         for (long long t = W.t0; t < W.t0 + W.count; ++t) {
             long long d = 0, t1 = t;
-            const bool seg = refine_seg(S, W, t, U, d, t1);
+            const bool seg = refine_seg(W, t, U, d, t1);
             // the particle's charge: its own (refined sheets), else the
             // mean of its tracers' weights (the sheet's, or per tracer)
             const int Q = !seg ? 0 : S.seg_q ? S.Qh[t] : S.Qh ? S.Qh[t] + S.Qh[t1] : 2 * W.qh;
@@ -1911,7 +1874,7 @@ __global__ void k_refine_scatter(const SimDev S, long long lfix, const int64_t *
             if (seg && (d > lfix || -d > lfix)) {
                 Q2[out] = Q >> 1;
                 ++out;
-                U2[out] = U[t] + (d >> 1);
+                U2[out] = U[t] + (unsigned)(int)(d >> 1);  // floor of half the segment
                 V2[out] = 0.5f * (V[t] + V[t1]);
                 Q2[out] = Q - (Q >> 1);
             } else {
@@ -1932,7 +1895,7 @@ cudaError_t launch_refine_count(const SimDev &sim, long long lfix, int32_t *spli
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, int64_t *U2, float *V2,
+cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, uint32_t *U2, float *V2,
                                   int32_t *Q2, cudaStream_t s)
 {
     const int grid = (int)std::max<long long>(1, std::min<long long>(4096, ((long long)sim.n_items + 255) / 256));

@@ -332,7 +332,8 @@ class Sim:
         return x, v
 
     def sic_device_state(self):
-        """(positions int64*, velocities float*, sheet offsets) as integer addresses."""
+        """(positions uint32* in the SIC position format, velocities float*,
+        sheet offsets) as integer addresses."""
         pu, pv, po = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         _check(_lib.sic_device_state(self.handle, ctypes.byref(pu), ctypes.byref(pv),
                                      ctypes.byref(po)), "sic_device_state")

@@ -1,0 +1,93 @@
+"""Paper configurations at their stated sizes, GPU against the FP64 oracle.
+
+* Nonlinear Landau damping (alpha 0.5, k 0.5, Nx 512, 1024 sheets x 4096
+  tracers = 4.2 M segments, dt 0.05, t_end 60): the field-energy history's
+  local maxima within 1e-3 relative of the oracle's, over the whole run.
+* Two-stream instability (v0 2.4, sigma 0.1, k 0.2, Nx 1024, 512 x 16384 =
+  8.4 M segments, eps 0.01, dt 0.05) through the linear phase and
+  saturation (t <= 20): history within 1e-3 of its maximum, and the growth
+  rate fitted on t in [12, 16] (where the growing root dominates the
+  oscillating ones this large a perturbation also excites) within 1e-3 of
+  the oracle's.
+
+The oracle runs take about a minute each on one host core; they run in
+threads (the C oracle releases the interpreter lock) while the GPU runs.
+"""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fits
+from paper_1506_07207_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def sic():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1506_07207_gb300 import sic as binding
+    return binding
+
+
+def _landau3():
+    return inputs.landau_nonlinear()
+
+
+def _two_stream4():
+    return inputs.two_stream_config(t_end=20.0)
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    """Both oracle references, started in threads as soon as the module runs."""
+    oracle.build()
+    pool = cf.ThreadPoolExecutor(max_workers=2)
+    futs = {"landau3": pool.submit(lambda: oracle.run_problem(_landau3())["hist"]),
+            "two_stream4": pool.submit(lambda: oracle.run_problem(_two_stream4())["hist"])}
+    yield futs
+    pool.shutdown(wait=True)
+
+
+def _gpu_history(sic, p):
+    sim = sic.Sim.from_problem(p, history_len=p.n_steps)
+    try:
+        q0 = sim.sic_diagnostics()["charge_fixed"]
+        sim.sic_step(p.n_steps)
+        h = sim.sic_history(p.n_steps)
+        assert sim.sic_diagnostics()["charge_fixed"] == q0
+        assert np.all(h[:, 3] == q0)
+    finally:
+        sim.sic_destroy()
+    return h
+
+
+def test_nonlinear_landau_full_size(sic, oracle_runs):
+    p = _landau3()
+    assert p.n_segments == 1024 * 4096 and p.nx == 512 and p.n_steps == 1200
+    h = _gpu_history(sic, p)
+    hr = oracle_runs["landau3"].result()
+    t = np.arange(p.n_steps) * p.dt
+    W, Wr = h[:, 0], hr[:-1, 0]
+    pt, py = fits.local_maxima(t, W)
+    ptr, pyr = fits.local_maxima(t, Wr)
+    assert len(pt) == len(ptr) and len(pt) >= 10
+    np.testing.assert_allclose(py, pyr, rtol=1e-3)
+    np.testing.assert_allclose(pt, ptr, rtol=0, atol=0.5 * p.dt)
+
+
+def test_two_stream_full_size_growth(sic, oracle_runs):
+    p = _two_stream4()
+    assert p.n_segments == 512 * 16384 and p.nx == 1024
+    h = _gpu_history(sic, p)
+    hr = oracle_runs["two_stream4"].result()
+    t = np.arange(p.n_steps) * p.dt
+    W, Wr = h[:, 0], hr[:-1, 0]
+    assert np.abs(W - Wr).max() <= 1e-3 * Wr.max()
+    g = fits.growth_rate(t, np.sqrt(W), 12.0, 16.0)
+    gr = fits.growth_rate(t, np.sqrt(Wr), 12.0, 16.0)
+    assert abs(g / gr - 1) <= 1e-3, (g, gr)

@@ -111,3 +111,73 @@ def test_mixed_orders_batch_equals_alone(sic):
     finally:
         for s in sims:
             s.sic_destroy()
+
+
+def _kappa_bound_per_cell(p, x, eps):
+    """Per-cell bound, in charge units, on the FP32 cut error of
+    piecewise-linear particles (Sec. 2.5): a particle of charge q whose density
+    is rho0 (1 + 2 kappa (x - c) / l) puts round(q phi(t)) - round(q phi(t'))
+    in each cell it touches, phi(t) = t + kappa t (t - 1); FP32 t and phi carry
+    about (1 + |kappa|) 2^-24 relative error each, so every touched cell is
+    off by at most 2 eps q (1 + |kappa|).  kappa = g l / (2 rho0) with g the
+    central difference of the neighbours' rho0 over their centroid distance,
+    0 at a fold corner, a zero length or a particle of a box length or more
+    (reading A-19).  Closed horizontal sheets only (the Landau and two-stream
+    set-ups)."""
+    dx = p.L / p.nx
+    bound = np.zeros(p.nx)
+    base = 0
+    for n, wd in zip(p.counts, p.winding):
+        xs = x[base:base + n]
+        ws = p.w[base:base + n]
+        xa = xs
+        xb = np.r_[xs[1:], xs[0] + wd * p.L]
+        q = 0.5 * (ws + np.roll(ws, -1))
+        ln = np.abs(xb - xa)
+        c = 0.5 * (xa + xb)
+        rho0 = np.where(ln > 0, q / np.where(ln > 0, ln, 1.0), 0.0)
+        cp = np.r_[c[-1] - wd * p.L, c[:-1]]
+        cn = np.r_[c[1:], c[0] + wd * p.L]
+        rp, rn = np.roll(rho0, 1), np.roll(rho0, -1)
+        lp, lnn = np.roll(ln, 1), np.roll(ln, -1)
+        ordered = ((cp < c) & (c < cn)) | ((cp > c) & (c > cn))
+        ok = ordered & (ln > 0) & (lp > 0) & (lnn > 0) & (ln < p.L)
+        g = np.where(ok, (rn - rp) / np.where(cn != cp, cn - cp, 1.0), 0.0)
+        kappa = np.where(ok & (rho0 > 0), g * ln / (2 * np.where(rho0 > 0, rho0, 1.0)), 0.0)
+        err = 2 * eps * q * (1 + np.abs(kappa))
+        lo = np.floor(np.minimum(xa, xb) / dx).astype(np.int64)
+        hi = np.floor(np.maximum(xa, xb) / dx).astype(np.int64)
+        span = np.minimum(hi - lo, p.nx - 1) + 1
+        cells = (np.repeat(lo, span) + (np.arange(span.sum()) - np.repeat(np.cumsum(span) - span, span))) % p.nx
+        np.add.at(bound, cells, np.repeat(err, span))
+        base += n
+    return bound
+
+
+def test_linear_deposit_on_an_evolved_two_stream_state(sic):
+    """Piecewise-linear particles on a rolled-up state: a two-stream run
+    (Sec. 3.2 set-up, eps 0.05) stepped past saturation, where sheets have
+    filamented and neighbouring particle lengths differ a lot.  The deposit of
+    the GPU's own state against the oracle's, cell by cell, within the box
+    tolerance (1e-5 of the gross density) plus the kappa-dependent FP32 cut
+    bound of each cell; total charge exact."""
+    p = inputs.two_stream(2.4, 0.1, 0.2, nx=256, n_sheets=64, n_tracers=2048, eps=0.05, t_end=30.0)
+    sim = sic.Sim.from_problem(p, history_len=4, order=1)
+    try:
+        q0 = sim.sic_diagnostics()["charge_fixed"]
+        sim.sic_step(p.n_steps)
+        x, _ = sim.sic_get_state()
+        mesh, _ = sim.sic_deposit()
+        unit = sim.sic_diagnostics()["charge_unit"]
+        assert int(mesh.sum()) == q0
+    finally:
+        sim.sic_destroy()
+    ref = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, x, p.w, order=1)
+    dx = p.L / p.nx
+    gross = np.abs(ref).max()
+    bound = 1e-5 * gross + _kappa_bound_per_cell(p, x, 8 * 2.0 ** -24) + 4 * unit
+    err = np.abs(mesh * unit - ref)
+    assert np.all(err <= bound), (err / bound).max()
+    # the state is filamented: some particles are many times longer than others
+    lens = np.abs(np.diff(x.reshape(len(p.counts), -1), axis=1))
+    assert lens.max() > 50 * np.median(lens)

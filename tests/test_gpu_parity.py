@@ -97,8 +97,11 @@ def test_single_segments_exact(sic):
              ([4.0, 1.0], [0, 1 / 3, 1 / 3, 1 / 3, 0, 0, 0, 0]),
              ([2.0, 2.0], [0, 0, 1, 0, 0, 0, 0, 0]),
              ([-0.5, 0.5], [0.5, 0, 0, 0, 0, 0, 0, 0.5]),
-             ([0.5, 16.5], [0.125] * 8),    # twice around the box
-             ([0.5, 40.5], [0.125] * 8)]    # five times: the O(nx) long-segment path
+             ([0.5, 8.5], [0.125] * 8),     # once around the box
+             # 1.25 box lengths: cells 0-2 twice in part (every image counts),
+             # the whole-cell interior wraps past the box (the O(1) range path)
+             ([0.5, 10.5], [0.15, 0.2, 0.15, 0.1, 0.1, 0.1, 0.1, 0.1]),
+             ([13.5, 3.5], [0.1, 0.1, 0.1, 0.15, 0.2, 0.15, 0.1, 0.1])]
     for x, want in cases:
         sim = sic.Sim.sic_create(nx, L, 0.1, [2], [0], [0], x, [0.0, 0.0], [1.0, 1.0],
                                  half_step_init=False)
@@ -149,7 +152,8 @@ def test_langmuir_trajectory(sic):
     r = oracle.run_problem(p)
     W, Wr = h[:, 0], r["hist"][:-1, 0]
     assert np.abs(W - Wr).max() <= 1e-3 * Wr.max()
-    assert np.abs(x - r["x"]).max() <= 1e-5 * p.L
+    dxr = (x - r["x"]) / p.L
+    assert np.abs(dxr - np.round(dxr)).max() <= 1e-5      # positions modulo the box
     assert np.isclose(d["field_energy"], r["hist"][-1, 0], rtol=1e-3, atol=1e-3 * Wr.max())
     # energy and momentum diagnostics follow the oracle's
     Et, Etr = h[:, 0] + h[:, 1], r["hist"][:-1, 0] + r["hist"][:-1, 1]
@@ -250,8 +254,8 @@ def test_translation_by_whole_cells_is_exact(sic):
 
 
 def test_strict_mode_reports_long_segment(sic):
-    # a segment longer than the box at create
-    x = np.array([0.0, 0.3, 2.6])
+    # a segment longer than the box (but inside the position format) at create
+    x = np.array([0.0, 0.3, 1.5])
     with pytest.raises(sic.SicError) as e:
         sic.Sim.sic_create(16, 1.0, 0.1, [3], [0], [0], x, np.zeros(3), np.ones(3), strict=True,
                            half_step_init=False)
@@ -263,7 +267,7 @@ def test_strict_mode_reports_long_segment(sic):
         sim.sic_step(1)
         sim.sic_sync()
         with pytest.raises(sic.SicError) as e:
-            sim.sic_step(2)
+            sim.sic_step(1)
             sim.sic_sync()
         assert e.value.code == sic.SIC_ESEGMENT_LONG
     finally:
@@ -272,12 +276,60 @@ def test_strict_mode_reports_long_segment(sic):
     sim = sic.Sim.sic_create(16, 1.0, 0.1, [2], [0], [0], [0.2, 0.7], [-2.0, 2.0], [1.0, 1.0],
                              half_step_init=False, qm=1e-6)
     try:
-        sim.sic_step(5)
+        sim.sic_step(2)
         d = sim.sic_diagnostics()
-        assert d["max_segment"] > 2.0
+        assert 1.2 < d["max_segment"] < 1.5
         assert d["charge_fixed"] * d["charge_unit"] == 1.0
+        x, _ = sim.sic_get_state()
+        assert abs((x[1] - x[0]) - 1.3) < 1e-6
+        # a third step takes it to 1.7 box lengths: past the position format's
+        # range (1.5), reported as a range error at the next synchronising call
+        with pytest.raises(sic.SicError) as e:
+            sim.sic_step(1)
+            sim.sic_sync()
+        assert e.value.code == sic.SIC_ERANGE
     finally:
         sim.sic_destroy()
+
+
+def test_position_format_limits_at_create(sic):
+    """A segment of 1.5 box lengths or more, or a step of half a box or more,
+    is outside the position format: SIC_ERANGE at creation."""
+    for x in ([0.0, 1.5], [0.0, -1.6], [0.25, 1.75]):
+        with pytest.raises(sic.SicError) as e:
+            sic.Sim.sic_create(8, 1.0, 0.1, [2], [0], [0], x, [0.0, 0.0], [1.0, 1.0], half_step_init=False)
+        assert e.value.code == sic.SIC_ERANGE
+    # the closing segment of a closed sheet counts with its winding
+    with pytest.raises(sic.SicError) as e:
+        sic.Sim.sic_create(8, 1.0, 0.1, [2], [1], [2], [0.0, 0.25], [0.0, 0.0], [1.0, 1.0], half_step_init=False)
+    assert e.value.code == sic.SIC_ERANGE
+    with pytest.raises(sic.SicError) as e:
+        sic.Sim.sic_create(8, 1.0, 0.1, [2], [0], [0], [0.0, 0.1], [0.0, 5.0], [1.0, 1.0], half_step_init=False)
+    assert e.value.code == sic.SIC_ERANGE
+    # just inside: 1.4 box lengths, and a step of 0.45 box
+    sim = sic.Sim.sic_create(8, 1.0, 0.1, [2], [0], [0], [0.0, 1.4], [0.0, 4.5], [1.0, 1.0], half_step_init=False)
+    sim.sic_destroy()
+
+
+def test_positions_far_from_the_box(sic):
+    """Tracers given a thousand boxes away give the same deposit and steps as
+    the same tracers inside the box (positions are kept modulo 4 boxes).  The
+    positions sit on the format's grid (multiples of L 2^-30, L a power of
+    two), so the shifted ones are exact."""
+    p = inputs.tiny_problem(41, n_sheets=3, max_tracers=2000, nx=50, L=2.0)
+    xq = np.round(p.x / p.L * 2.0 ** 30) * (p.L * 2.0 ** -30)
+    runs = []
+    for shift in (0.0, 1024.0 * p.L, -3.0 * p.L):
+        sim = sic.Sim.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, xq + shift, p.v, p.w,
+                                 half_step_init=False, history_len=4)
+        sim.sic_step(3)
+        runs.append((sim.sic_deposit()[0], sim.sic_history(4), sim.sic_get_state()))
+        sim.sic_destroy()
+    for m, h, (x, v) in runs[1:]:
+        np.testing.assert_array_equal(m, runs[0][0])
+        np.testing.assert_array_equal(h, runs[0][1])
+        np.testing.assert_array_equal(x, runs[0][2][0])
+        np.testing.assert_array_equal(v, runs[0][2][1])
 
 
 def test_grid_shape_does_not_change_results(sic, monkeypatch):
@@ -303,7 +355,7 @@ def test_persistent_batch_equals_alone(sic):
     probs = [inputs.landau(0.1, 0.4, 128, 32, 3000, t_end=1.0),
              inputs.two_stream(1.5, 0.2, 0.3, 512, 16, 5000, t_end=1.0),
              inputs.langmuir(nx=100),
-             inputs.tiny_problem(12, n_sheets=4, max_tracers=2000, nx=64, L=1.0)]
+             inputs.tiny_problem(12, n_sheets=4, max_tracers=2000, nx=64, L=1.0, vscale=0.5)]
     steps = 19      # two graph replays of 8 and three single launches
     alone = []
     for p in probs:
@@ -332,8 +384,10 @@ def test_many_small_simulations_batch_equals_alone(sic):
     move between simulations and often arrive when every item is claimed.
     Each simulation still takes exactly its steps, bit-identical to running
     alone."""
-    probs = [inputs.tiny_problem(100 + i, n_sheets=2, max_tracers=300, nx=[16, 37, 64][i % 3], L=1.0)
-             for i in range(40)]
+    # random per-tracer velocities stretch a sheet's segments; vscale 0.2 keeps
+    # them inside the position format's 1.5 box lengths over the 25 steps
+    probs = [inputs.tiny_problem(100 + i, n_sheets=2, max_tracers=300, nx=[16, 37, 64][i % 3], L=1.0,
+                                 vscale=0.2) for i in range(40)]
     probs += [inputs.landau(0.1, 0.5, 128, 64, 4096, t_end=1.0), inputs.two_stream(1.5, 0.2, 0.3, 256, 32, 8192,
                                                                                      t_end=1.0)]
     steps = 25
@@ -363,7 +417,7 @@ def test_autotuned_batch_equals_plain_batch(sic):
     steps ends bit-identical to one stepped the same number of times."""
     probs = [inputs.landau(0.1, 0.4, 128, 32, 3000, t_end=1.0),
              inputs.two_stream(1.5, 0.2, 0.3, 512, 16, 5000, t_end=1.0),
-             inputs.tiny_problem(31, n_sheets=4, max_tracers=2000, nx=64, L=1.0)]
+             inputs.tiny_problem(31, n_sheets=4, max_tracers=2000, nx=64, L=1.0, vscale=0.2)]
     a = [sic.Sim.from_problem(p, history_len=8) for p in probs]
     b = [sic.Sim.from_problem(p, history_len=8) for p in probs]
     try:

@@ -2,7 +2,7 @@
 oracle's, through the C ABI.
 
 On the same state the decisions (particle length > l_ref) are the same, the
-new tracers sit at the centres (fixed point: within 2^-32 cells) with the mean
+new tracers sit at the centres (fixed point: within a unit L 2^-30) with the mean
 velocities (FP32), the total charge is unchanged to the unit, and the deposit
 after refinement matches the oracle's with per-particle charges within the
 step tolerance (1e-5 of the gross density).  Runs that refine every few steps
@@ -52,7 +52,9 @@ def test_refine_matches_oracle(sic, seed, order):
         assert added == int(c_ref.sum() - p.counts.sum()) > 0
         np.testing.assert_array_equal(sim.counts, c_ref)
         x1, v1 = sim.sic_get_state()
-        np.testing.assert_allclose(x1, x_ref, rtol=0, atol=4 * (p.L / p.nx) * 2.0 ** -32)
+        # the new tracer: the lower end plus half the segment, floored to the
+        # position unit L 2^-30
+        np.testing.assert_allclose(x1, x_ref, rtol=0, atol=p.L * 2.0 ** -29)
         np.testing.assert_allclose(v1, v_ref, rtol=1e-6, atol=1e-7 * np.abs(v0).max())
         mesh1 = _state_parity(sim, p, c_ref, q_ref, order)
         assert mesh1.sum() == mesh0.sum()
