@@ -305,7 +305,10 @@ def main():
     ap.add_argument("--deposit", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC")
     ap.add_argument("--autotune", type=int, default=1, help="tune the batch schedule before timing (0: default)")
-    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=512,
+                    help="leading requests of the seeded 4096-request mix to serve (and hold resident for value)")
+    ap.add_argument("--budget-gib", type=float, default=4.0, help="server device-memory budget")
+    ap.add_argument("--max-active", type=int, default=32, help="server slots")
     ap.add_argument("--presteps", type=int, default=0,
                     help="advance the resident batch this many steps before the warm-up (evolved, filamented states)")
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
@@ -338,6 +341,8 @@ def main():
     from paper_1506_07207_gb300 import inputs, ranks, serving
     from paper_1506_07207_gb300.sic import Batch, Sim, sic_launch_count
 
+    legs = {}
+    t_leg = time.perf_counter()
     serving_mode = args.workload == "serving"
     if serving_mode:
         reqs = sample_requests(args.requests)
@@ -356,11 +361,14 @@ def main():
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         flush.fill_(1.0)
     sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream, order=args.deposit) for p in probs]
+    if args.presteps > 0:
+        # untimed: each simulation advanced on its own, refining where its
+        # particles pass the refinement length (Sec. 2.6)
+        for sim, p in zip(sims, probs):
+            sim.sic_run(min(args.presteps, p.n_steps))
+        config["presteps"] = args.presteps
     batch = Batch(sims)
     S = batch.sic_batch_segments()
-    if args.presteps > 0:
-        batch.sic_batch_step(args.presteps)   # untimed
-        config["presteps"] = args.presteps
     for _ in range(args.warmup):
         batch.sic_batch_step(1)
     schedule = None
@@ -379,6 +387,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = sic_launch_count()
+    steps0 = [s.sic_diagnostics()["step"] for s in sims]
     with Clocks(uuid) as clk:
         t_wall = time.perf_counter()
         for a, b in evs:
@@ -395,7 +404,13 @@ def main():
         torch.cuda.synchronize()
     launches = sic_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms, value = ranks.combine(sum(step_ms), S * args.steps, world, dist, torch.device("cuda", local))
+    # the work done: each simulation's own steps (one that holds for
+    # refinement, or for an error, takes fewer), at its segments
+    seg_each = [int(s.n_tracers - sum(1 for c in p.closed if not c)) for s, p in zip(sims, probs)]
+    done_steps = [s.sic_diagnostics()["step"] - k for s, k in zip(sims, steps0)]
+    work = sum(n * d for n, d in zip(seg_each, done_steps))
+    held = sum(1 for d in done_steps if d < args.steps)
+    total_ms, value = ranks.combine(sum(step_ms), work, world, dist, torch.device("cuda", local))
     batch.sic_batch_destroy()
     for s in sims:
         s.sic_destroy()
@@ -411,7 +426,7 @@ def main():
     }
     peak, peak_src = peaks()
     avg_s = statistics.mean(step_ms) / 1e3
-    abytes = algo_bytes(probs)
+    abytes = algo_bytes(probs) * work / max(1, S * args.steps)   # per launch, of the work done
     achieved = abytes / avg_s / 1e9
     traffic = kernel_traffic(S)
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -424,10 +439,12 @@ def main():
                         "avg_launch_ms": avg_s * 1e3, "peak_source": peak_src}
     line["clocks"] = clocks
     line["gpu_launches"] = int(launches)
+    line["held_during_timing"] = held
+    legs["value"] = time.perf_counter() - t_leg
     line["wall_s_timed_region"] = t_wall
 
+    budget = int(args.budget_gib * (1 << 30))
     if rank == 0 and serving_mode and not args.no_serving:
-        import numpy as np
         works = [p.n_segments * p.n_steps for p in probs]
 
         def replay(load):
@@ -440,34 +457,57 @@ def main():
                 arrivals.append(t)
             out = {}
             for mode in ("batched", "plain"):
-                r = serving.run_trace(probs, arrivals, plain=(mode == "plain"), max_active=64, chunk_steps=32)
+                r = serving.run_trace(probs, arrivals, plain=(mode == "plain"), hbm_budget=budget,
+                                      max_active=args.max_active, chunk_steps=32)
                 out[mode] = {"throughput": r["throughput"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                              "makespan_s": r["makespan_s"], "segment_updates": r["segment_updates"],
-                             "peak_device_bytes": r["bytes_peak"], "device_busy_s": r["busy_s"]}
+                             "peak_device_bytes": r["bytes_peak"], "device_busy_s": r["busy_s"],
+                             "admission_waits_slots": r["waits_slots"],
+                             "admission_waits_memory": r["waits_memory"], "refinements": r["refinements"],
+                             "failed_requests": r["failed"]}
             out["arrival_rate_per_s"] = rate
             out["load"] = load
+            out["requests"] = len(probs)
+            out["hbm_budget_bytes"] = budget
+            out["max_active"] = args.max_active
             return out
 
+        t_leg = time.perf_counter()
         line["serving"] = replay(args.load)
+        legs["serving"] = time.perf_counter() - t_leg
         if args.overload > 0:
+            t_leg = time.perf_counter()
             line["serving"]["overload"] = replay(args.overload)
+            legs["overload"] = time.perf_counter() - t_leg
+    t_leg = time.perf_counter()
     if rank == 0 and not args.no_e2e:
         if serving_mode:
             arrivals0 = [0.0] * len(probs)
-            r = serving.run_trace(probs, arrivals0, plain=False, max_active=64, chunk_steps=32)
+            r = serving.run_trace(probs, arrivals0, plain=False, hbm_budget=budget, max_active=args.max_active,
+                                  chunk_steps=32, history=True)
             steps_total = sum(p.n_steps for p in probs)
             h2d = sum(8 * (p.x_template.size + 2 * p.n_sheets) for p in probs)
-            line["e2e"] = {"value": r["throughput"], "unit": UNIT,
+            d2h = sum(32 * p.n_steps + 96 for p in probs)
+            bad = [(i, res["status"]) for i, res in enumerate(r["results"]) if res["status"] != 0]
+            hist_ok = sum(1 for res, p in zip(r["results"], probs)
+                          if "history" in res and res["history"].shape == (p.n_steps, 4))
+            line["e2e"] = {"value": r["throughput"], "unit": UNIT, "failed_requests": bad[:16],
+                           "histories_read": hist_ok,
                            "h2d_bytes_per_step": h2d / steps_total,
-                           "d2h_bytes_per_step": 96 * len(probs) / steps_total,
+                           "d2h_bytes_per_step": d2h / steps_total,
                            "note": "request server fed from host arrays (position template, per-sheet "
-                                   "velocity and weight), all requests at t = 0, results read back; "
-                                   "per-step bytes averaged over all requests' steps",
+                                   "velocity and weight), all requests at t = 0, each request's result and "
+                                   "its per-step [W_E, KE, P, Q] history read back; per-step bytes averaged "
+                                   "over all requests' steps",
                            "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "makespan_s": r["makespan_s"]}
         else:
             line["e2e"] = e2e_single(torch, Sim, probs[0])
+    legs["e2e"] = time.perf_counter() - t_leg
+    t_leg = time.perf_counter()
     if rank == 0 and serving_mode and not args.no_single:
         line["single_sim"] = single_sim(torch, Sim, args.steps, args.warmup)
+    legs["single_sim"] = time.perf_counter() - t_leg
+    t_leg = time.perf_counter()
     if rank == 0 and not args.no_cpu_baseline:
         v, upd, el = oracle_rate(probs)
         va, upa, wall, cores, nreq = oracle_rate_all_cores(reqs, probs) if serving_mode else (v, upd, el, 1, 0)
@@ -479,6 +519,8 @@ def main():
             "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"4 steps each of the sampled problems of at most 2^24 segments, in order, until 12 s "
                       f"({upd} segment-updates in {el:.1f} s), FP64 C oracle, single thread"}
+    legs["cpu_baseline"] = time.perf_counter() - t_leg
+    line["leg_wall_s"] = {k: round(v, 1) for k, v in legs.items()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -118,6 +118,18 @@ typedef struct {
     void *stream;                      /* cudaStream_t the simulation runs on, NULL = its own */
     int32_t deposit;                   /* SIC_DEPOSIT_*: what carries the charge onto the mesh;
                                           other values SIC_EINVAL */
+    double refine_length;              /* refinement length of Sec. 2.6 (same unit as box_length):
+                                          0 = never refine; else >= box_length / nx / 1024, box
+                                          and piecewise-linear deposits only.  After a step whose
+                                          longest particle exceeds it the simulation holds: later
+                                          steps leave it as it is until it is refined (sic_run
+                                          and the server do this themselves; sic_refine clears
+                                          the hold).  It holds at the same step alone or in any
+                                          batch. */
+    double refine_split;               /* when a hold for refinement is resolved, every particle
+                                          longer than this is split (passes until none is): 0 =
+                                          refine_length, else 0 < refine_split <= refine_length.
+                                          A shorter one splits ahead, so holds come less often */
 } sic_config;
 
 /* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum
@@ -213,6 +225,17 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added);
 int sic_sheet_counts(sic_sim *sim, int32_t *counts_host);
 
 /*
+ * n_steps full steps, synchronously, refining as Sec. 2.6 describes: whenever
+ * a step leaves a particle longer than cfg->refine_length the run holds, the
+ * particles longer than cfg->refine_split are split (sic_refine passes until
+ * none is), and the run goes on, until n_steps steps are done (a hold after
+ * the last of them is resolved by the next call).  Without a refinement length
+ * it is sic_step followed by sic_sync.  *n_added (nullable) gets the tracers
+ * added.  Errors as for sic_sync (the run stops at the step that raised one).
+ */
+int sic_run(sic_sim *sim, int32_t n_steps, int64_t *n_added);
+
+/*
  * Gather, kick and drift every tracer with the current field, no deposit:
  * the "gather" and "move" of the PIC cycle, which Sec. 2.3 keeps unchanged
  * for SIC (forces gathered at the tracers by linear weighting between the
@@ -232,7 +255,9 @@ int sic_push(sic_sim *sim);
  * block that finishes last; runs of 8 steps replay a captured CUDA graph.
  * n_steps >= 0.  Asynchronous on the simulation's stream: errors found on
  * the device are returned by the next synchronising call (sic_sync,
- * sic_diagnostics, ...).
+ * sic_diagnostics, ...).  A held simulation (an error, or a particle past
+ * the refinement length) is left as it is by the remaining steps: check
+ * sic_diagnostics' step count, or use sic_run.
  */
 int sic_step(sic_sim *sim, int32_t n_steps);
 
@@ -356,12 +381,17 @@ typedef struct {
     int64_t segment_updates; /* of completed requests */
     int64_t ticks;
     double busy_s;           /* device time of the steps the ticks launched (CUDA events) */
+    int64_t waits_slots;     /* ticks whose admission stopped at the max_active limit */
+    int64_t waits_memory;    /* ticks whose admission stopped at the device-memory budget */
+    int64_t refinements;     /* refinement holds the server resolved (Sec. 2.6) */
 } sic_server_info;
 
 int sic_server_create(const sic_server_config *cfg, sic_server **out);
 
 /* Queue a request; the inputs are copied (host arrays as for sic_create /
- * sic_create_horizontal).  cfg->stream and cfg->history_len are ignored. */
+ * sic_create_horizontal).  cfg->stream is ignored; cfg->history_len rows of
+ * per-step diagnostics (at least 1) are kept, for a caller that keeps the
+ * simulation (keep != 0) and reads them with sic_history. */
 int sic_server_submit(sic_server *srv, const sic_config *cfg, const double *x_host, const double *v_host,
                       const double *w_host, int32_t n_steps, int32_t keep, int64_t *id);
 int sic_server_submit_horizontal(sic_server *srv, const sic_config *cfg, int32_t n_template,

@@ -77,6 +77,15 @@ def _load():
                                     ip, bp, ip, ctypes.c_long, dp, dp, dp,
                                     ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.orc_run.restype = ctypes.c_int
+            lp = ctypes.POINTER(ctypes.c_long)
+            ip_mut = ctypes.POINTER(ctypes.c_int32)
+            lib.orc_refine.argtypes = [ctypes.c_double, ctypes.c_int, ip_mut, bp, ip, ctypes.c_long,
+                                       dp, dp, dp, ctypes.c_double]
+            lib.orc_refine.restype = ctypes.c_long
+            lib.orc_run_refined.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int, ip_mut, bp, ip, ctypes.c_long, dp, dp, dp,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, lp]
+            lib.orc_run_refined.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -282,6 +291,53 @@ def run_refined(nx, L, dt, counts, closed, winding, x, v, qseg, n_steps, l_ref, 
             counts, x, v, qseg = refine(L, counts, closed, winding, x, v, qseg, l_ref)
         charge = deposit_seg(nx, L, counts, closed, winding, x, qseg)
     return dict(counts=counts, x=x, v=v, qseg=qseg, W=np.array(W))
+
+
+def refine_c(L, counts, closed, winding, x, v, qseg, l_ref):
+    """``refine`` done by the C oracle (orc_refine); same arguments and result."""
+    lib = _load()
+    counts, closed, winding = _sheets(counts, closed, winding)
+    counts = counts.copy()
+    n = int(counts.sum())
+    cap = 2 * n
+    xb = np.zeros(cap); vb = np.zeros(cap); qb = np.zeros(cap)
+    xb[:n], vb[:n], qb[:n] = x, v, qseg
+    added = lib.orc_refine(float(L), counts.size, _ptr(counts, ctypes.c_int32), _ptr(closed, ctypes.c_uint8),
+                           _ptr(winding, ctypes.c_int32), cap, _ptr(xb, ctypes.c_double),
+                           _ptr(vb, ctypes.c_double), _ptr(qb, ctypes.c_double), float(l_ref))
+    m = n + int(added)
+    return counts, xb[:m].copy(), vb[:m].copy(), qb[:m].copy()
+
+
+def run_refined_each_step(nx, L, dt, counts, closed, winding, x, v, qseg, n_steps, l_ref, qm=1.0,
+                          max_growth=4.0, l_split=None):
+    """Leapfrog run of box particles with per-particle charges, refined after
+    every step in which a particle is longer than l_ref (Sec. 2.6) by passes
+    that split every particle longer than l_split (default l_ref) until none
+    is, in C (orc_run_refined).  Velocities are v^{-1/2} on entry.  Returns
+    dict(counts, x, v, qseg, W, n) with W the field energy of every step's
+    field before its kick and n the tracer count after every step.  The
+    tracers may grow to max_growth times their number."""
+    if l_split is None:
+        l_split = l_ref
+    lib = _load()
+    counts, closed, winding = _sheets(counts, closed, winding)
+    counts = counts.copy()
+    n0 = int(counts.sum())
+    cap = int(max_growth * n0) + 16
+    xb = np.zeros(cap); vb = np.zeros(cap); qb = np.zeros(cap)
+    xb[:n0], vb[:n0], qb[:n0] = _f64(x), _f64(v), _f64(qseg)
+    W = np.zeros(int(n_steps))
+    nn = np.zeros(int(n_steps), dtype=np.int64)
+    rc = lib.orc_run_refined(int(nx), float(L), float(dt), float(qm), counts.size, _ptr(counts, ctypes.c_int32),
+                             _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32), cap,
+                             _ptr(xb, ctypes.c_double), _ptr(vb, ctypes.c_double), _ptr(qb, ctypes.c_double),
+                             int(n_steps), float(l_ref), float(l_split), _ptr(W, ctypes.c_double),
+                             _ptr(nn, ctypes.c_long))
+    if rc:
+        raise ValueError("the refined tracers outgrew max_growth")
+    m = int(counts.sum())
+    return dict(counts=counts, x=xb[:m].copy(), v=vb[:m].copy(), qseg=qb[:m].copy(), W=W, n=nn)
 
 
 def run_problem(p, n_steps=None, record_E=False, order=0):

@@ -563,3 +563,159 @@ done:
     free(ex);
     return rc;
 }
+
+/*
+ * One pass of the refinement of Sec. 2.6 over all sheets, in place: every
+ * particle longer than l_ref gets a new tracer at its centre, with the mean of
+ * its two tracers' velocities, and each half carries half the particle's
+ * charge.  x, v, qseg hold the n tracers of the sheets (counts[], updated)
+ * with room for cap; qseg[i] is the charge of the particle starting at tracer
+ * i (see orc_deposit_seg).  Returns the number of new tracers, or -1 when they
+ * do not fit in cap.
+ */
+long orc_refine(double L, int n_sheets, int32_t *counts, const uint8_t *closed,
+                const int32_t *winding, long cap, double *x, double *v,
+                double *qseg, double l_ref)
+{
+    long n = 0, added = 0;
+    for (int s = 0; s < n_sheets; ++s)
+        n += counts[s];
+    /* count first, so nothing moves when the result would not fit */
+    long base = 0;
+    for (int s = 0; s < n_sheets; ++s) {
+        long c = counts[s];
+        long np = closed[s] ? c : c - 1;
+        for (long k = 0; k < np; ++k) {
+            double xb = k + 1 < c ? x[base + k + 1] : x[base] + (double)winding[s] * L;
+            if (fabs(xb - x[base + k]) > l_ref)
+                ++added;
+        }
+        base += c;
+    }
+    if (added == 0)
+        return 0;
+    if (n + added > cap)
+        return -1;
+    /* build the refined sheets back to front so no tracer is overwritten
+       before it is read */
+    long src_end = n, dst_end = n + added;
+    for (int s = n_sheets - 1; s >= 0; --s) {
+        long c = counts[s];
+        long b = src_end - c;
+        long grow = 0;
+        long np = closed[s] ? c : c - 1;
+        for (long k = 0; k < np; ++k) {
+            double xb = k + 1 < c ? x[b + k + 1] : x[b] + (double)winding[s] * L;
+            if (fabs(xb - x[b + k]) > l_ref)
+                ++grow;
+        }
+        long d = dst_end;
+        for (long k = c - 1; k >= 0; --k) {
+            int split = 0;
+            double xb = 0.0, vb = 0.0;
+            if (k < np) {
+                xb = k + 1 < c ? x[b + k + 1] : x[b] + (double)winding[s] * L;
+                vb = k + 1 < c ? v[b + k + 1] : v[b];
+                split = fabs(xb - x[b + k]) > l_ref;
+            }
+            double xk = x[b + k], vk = v[b + k], qk = qseg[b + k];
+            if (split) {
+                --d;
+                x[d] = 0.5 * (xk + xb);
+                v[d] = 0.5 * (vk + vb);
+                qseg[d] = 0.5 * qk;
+                --d;
+                x[d] = xk;
+                v[d] = vk;
+                qseg[d] = 0.5 * qk;
+            } else {
+                --d;
+                x[d] = xk;
+                v[d] = vk;
+                qseg[d] = qk;
+            }
+        }
+        counts[s] = (int32_t)(c + grow);
+        src_end = b;
+        dst_end = d;
+    }
+    return added;
+}
+
+/* The longest particle of the sheets. */
+static double longest_particle(double L, int n_sheets, const int32_t *counts,
+                               const uint8_t *closed, const int32_t *winding,
+                               const double *x)
+{
+    double m = 0.0;
+    long base = 0;
+    for (int s = 0; s < n_sheets; ++s) {
+        long c = counts[s];
+        long np = closed[s] ? c : c - 1;
+        for (long k = 0; k < np; ++k) {
+            double xb = k + 1 < c ? x[base + k + 1] : x[base] + (double)winding[s] * L;
+            double len = fabs(xb - x[base + k]);
+            if (len > m)
+                m = len;
+        }
+        base += c;
+    }
+    return m;
+}
+
+/*
+ * Leapfrog run of box particles with per-particle charges (qseg, as for
+ * orc_deposit_seg), refined after every step in which a particle is longer
+ * than l_ref (Sec. 2.6: "if at any time any segment becomes larger than the
+ * maximum length, a new tracer is inserted"): orc_refine passes at l_split
+ * (0 < l_split <= l_ref) until a pass adds nothing.  l_ref <= 0 or infinite
+ * never refines.  Velocities are v^{-1/2} on entry.  Each step: field of the
+ * current charge, W[step] = its field energy, kick, drift, refinement when
+ * due, deposit of the new tracers.  x, v, qseg have room for cap tracers;
+ * counts[] is updated.  n_out (may be NULL) gets the tracer count after every
+ * step.  Returns 0, or -1 when the tracers outgrow cap.
+ */
+int orc_run_refined(int nx, double L, double dt, double qm, int n_sheets,
+                    int32_t *counts, const uint8_t *closed, const int32_t *winding,
+                    long cap, double *x, double *v, double *qseg, int n_steps,
+                    double l_ref, double l_split, double *W, long *n_out)
+{
+    double *charge = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *E = (double *)malloc(sizeof(double) * (size_t)nx);
+    int rc = 0;
+    long n = 0;
+    for (int s = 0; s < n_sheets; ++s)
+        n += counts[s];
+    double *ex = (double *)malloc(sizeof(double) * (size_t)cap);
+    orc_deposit_seg(nx, L, n_sheets, counts, closed, winding, x, qseg, charge);
+    for (int step = 0; step < n_steps; ++step) {
+        orc_field(nx, L, charge, NULL, E);
+        if (W)
+            W[step] = orc_field_energy(nx, L, E);
+        orc_gather(nx, L, E, n, x, ex);
+        for (long i = 0; i < n; ++i) {
+            v[i] += dt * qm * ex[i];
+            x[i] += dt * v[i];
+        }
+        if (l_ref > 0.0 && isfinite(l_ref) &&
+            longest_particle(L, n_sheets, counts, closed, winding, x) > l_ref) {
+            long added;
+            do {
+                added = orc_refine(L, n_sheets, counts, closed, winding, cap, x, v, qseg, l_split);
+                if (added > 0)
+                    n += added;
+            } while (added > 0);
+            if (added < 0) {
+                rc = -1;
+                break;
+            }
+        }
+        if (n_out)
+            n_out[step] = n;
+        orc_deposit_seg(nx, L, n_sheets, counts, closed, winding, x, qseg, charge);
+    }
+    free(charge);
+    free(E);
+    free(ex);
+    return rc;
+}

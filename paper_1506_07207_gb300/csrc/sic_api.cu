@@ -113,6 +113,15 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (c->deposit < SIC_DEPOSIT_BOX || c->deposit > SIC_DEPOSIT_PIC_CIC)
         return SIC_EINVAL;
+    // the refinement length: off, or at least 2^-10 of a cell (the hold test
+    // measures particles in 2^-16 cells) with a deposit that has particles
+    if (!is_finite(c->refine_length) || c->refine_length < 0)
+        return SIC_EINVAL;
+    if (c->refine_length > 0 &&
+        (c->refine_length < c->box_length / c->nx / 1024.0 || c->deposit > SIC_DEPOSIT_LINEAR))
+        return SIC_EINVAL;
+    if (!is_finite(c->refine_split) || c->refine_split < 0 || c->refine_split > c->refine_length)
+        return SIC_EINVAL;
     if (need_sheets) {
         if (!c->tracers_per_sheet || !c->sheet_closed)
             return SIC_EINVAL;
@@ -204,6 +213,21 @@ int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
     return SIC_OK;
 }
 
+// Clear the refinement hold of a synchronised simulation (the epilogue sets it
+// again at the next step that leaves a particle longer than the length).
+int clear_refine_hold(sic_sim *sim)
+{
+    SimScalars sc;
+    CK(cudaMemcpyAsync(&sc, sim->h.sc, sizeof(sc), cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    if (sc.hold & SIC_HOLD_REFINE) {
+        const uint32_t hold = sc.hold & ~SIC_HOLD_REFINE;
+        CK(cudaMemcpyAsync(&sim->h.sc->hold, &hold, sizeof(hold), cudaMemcpyHostToDevice, sim->stream));
+        CK(cudaStreamSynchronize(sim->stream));
+    }
+    return SIC_OK;
+}
+
 // Fixed-point charge scale: every segment charge at most 2^28 units (so the
 // sum of a lane's 8 segments fits 32 bits), a power of two.
 double choose_sigma(double max_w)
@@ -261,6 +285,8 @@ int setup(sic_sim *sim, const sic_config *cfg)
     sim->hist_len = cfg->history_len;
     sim->half_step_init = cfg->half_step_init ? 1 : 0;
     sim->deposit = cfg->deposit;
+    sim->refine_length = cfg->refine_length;
+    sim->refine_split = cfg->refine_split > 0 ? cfg->refine_split : cfg->refine_length;
     sim->sheet_off.assign(sim->M, 0);
     int64_t off = 0;
     for (int s = 0; s < sim->M; ++s) {
@@ -323,6 +349,9 @@ int setup(sic_sim *sim, const sic_config *cfg)
     h.ke_scale = vu * vu / (2.0 * sim->sigma * sim->qm);
     h.p_scale = vu / (sim->sigma * sim->qm);
     h.strict = sim->strict;
+    // hold for refinement once the longest cell-crossing particle (2^-16 cells)
+    // exceeds the refinement length
+    h.refine_seg = sim->refine_length > 0 ? (long long)std::floor(sim->refine_length / sim->dx * 65536.0) : 0;
     sic_sim *one[1] = {sim};
     CK(build_plan(sim->plan, one, 1, sim->stream));
     return SIC_OK;
@@ -340,6 +369,35 @@ int initialise(sic_sim *sim)
 }  // namespace
 
 namespace sic_host {
+
+int read_scalars(sic_sim *sim, SimScalars *out) { return check_device_errors(sim, out); }
+
+int64_t segments(const sic_sim *sim)
+{
+    int64_t n = 0;
+    for (int s = 0; s < sim->M; ++s)
+        n += sim->counts[s] - (sim->closed[s] ? 0 : 1);
+    return n;
+}
+
+int refine_held(sic_sim *sim, int64_t *added)
+{
+    int64_t total = 0;
+    int rc = SIC_OK;
+    // one pass splits every particle longer than the length once; a particle
+    // more than twice as long needs another (a bounded number: each pass
+    // halves the longest)
+    for (int pass = 0; pass < 64; ++pass) {
+        int64_t a = 0;
+        rc = sic_refine(sim, sim->refine_split, &a);
+        total += a;
+        if (rc != SIC_OK || a == 0)
+            break;
+    }
+    if (added)
+        *added = total;
+    return rc;
+}
 
 void free_plan(Plan &p, cudaStream_t s)
 {
@@ -737,6 +795,9 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
     int rc = check_device_errors(sim);
     if (rc)
         return rc;
+    rc = clear_refine_hold(sim);
+    if (rc)
+        return rc;
     const double lc = l_ref / sim->L * kPosUnits;  // position units
     if (lc >= 2.0 * kPosUnits)
         return SIC_OK;  // no segment is 2 box lengths long
@@ -929,6 +990,40 @@ int sic_step(sic_sim *sim, int32_t n_steps)
     for (; left > 0; --left)
         CK(launch(sim->plan, MODE_STEP, 1.0f, 1, 1, sim->stream));
     return SIC_OK;
+}
+
+int sic_run(sic_sim *sim, int32_t n_steps, int64_t *n_added)
+{
+    if (!sim || n_steps < 0)
+        return SIC_EINVAL;
+    if (n_added)
+        *n_added = 0;
+    SimScalars sc;
+    int rc = check_device_errors(sim, &sc);
+    if (rc)
+        return rc;
+    const int64_t target = sc.step + n_steps;
+    constexpr int64_t kChunk = 32;  // steps between two looks at the hold flag
+    while (true) {
+        // refine only before a step that follows: a run that ends holding is
+        // refined by the call that continues it
+        if (sc.step >= target)
+            return SIC_OK;
+        if (sc.hold & SIC_HOLD_REFINE) {
+            int64_t a = 0;
+            rc = refine_held(sim, &a);
+            if (n_added)
+                *n_added += a;
+            if (rc)
+                return rc;
+        }
+        rc = sic_step(sim, (int32_t)std::min<int64_t>(kChunk, target - sc.step));
+        if (rc)
+            return rc;
+        rc = check_device_errors(sim, &sc);
+        if (rc)
+            return rc;
+    }
 }
 
 int sic_step_batch(sic_sim *const *sims, int32_t n_sims, const int32_t *n_steps)

@@ -34,6 +34,8 @@ int64_t work_items(const int32_t *counts, int M);
 }  // namespace sic_host
 
 struct sic_sim {
+    double refine_length = 0.0;       // Sec. 2.6 refinement length, 0 = never
+    double refine_split = 0.0;        // length particles are split to at a hold
     int nx = 0;
     double L = 0, dt = 0, dx = 0, qm = 1;
     int strict = 0, hist_len = 1, half_step_init = 0;
@@ -64,6 +66,15 @@ struct sic_sim {
 
 
 namespace sic_host {
+// The simulation's device scalars (after synchronising its stream) and the
+// SIC_E* code of any device error they hold.
+int read_scalars(sic_sim *sim, SimScalars *out);
+// Refine until no particle is longer than the simulation's refinement length
+// (sic_refine passes) and clear its refinement hold; *added gets the tracers
+// added.
+int refine_held(sic_sim *sim, int64_t *added);
+// Particles (segments) of the simulation now.
+int64_t segments(const sic_sim *sim);
 cudaError_t build_plan(Plan &p, sic_sim *const *sims, int n, cudaStream_t s);
 // Scheduling knobs of a built plan (results do not depend on them): the claim
 // divisor D (a claim takes 1 / (D warps) of what is left) and the staging

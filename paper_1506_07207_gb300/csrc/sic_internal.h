@@ -39,10 +39,10 @@
 #define SIC_ALIGN_TRACERS 32
 #define SIC_K1_BLOCK 256
 #ifndef SIC_K1_R
-#define SIC_K1_R 4           // tracers per lane: a work item is 32 R tracers
+#define SIC_K1_R 8           // tracers per lane: a work item is 32 R tracers
 #endif
 #ifndef SIC_K1_MIN_BLOCKS
-#define SIC_K1_MIN_BLOCKS 3  // resident blocks per SM the registers allow
+#define SIC_K1_MIN_BLOCKS 2  // resident blocks per SM the registers allow
 #endif
 #define SIC_K1_WARPS (SIC_K1_BLOCK / 32)
 #define SIC_K1_WARP_TRACERS (32 * SIC_K1_R)
@@ -51,6 +51,11 @@
 #define SIC_ERR_RANGE 1u
 #define SIC_ERR_SEGLONG 2u
 #define SIC_ERR_TIMEOUT 4u
+
+// hold bits (SimScalars::hold): set by a step's field epilogue, they stop the
+// simulation's later steps until the host clears them
+#define SIC_HOLD_ERROR 1u    // an error bit is set: the run ends here
+#define SIC_HOLD_REFINE 2u   // a particle is longer than the refinement length
 
 // Per-warp double-buffered staging of the next work item in shared memory
 // (filled by bulk copies): positions, velocities and, per-tracer charge mode,
@@ -104,6 +109,8 @@ struct SimScalars {
     int64_t maxseg;     // longest segment of the latest deposit crossing a cell edge, 2^-16 cells
     uint32_t err;       // SIC_ERR_* bits
     uint32_t buf;       // which state buffer is current
+    uint32_t hold;      // SIC_HOLD_* bits: while nonzero, steps leave the simulation as it is
+    uint32_t pad;
 };
 
 struct SimDev {
@@ -138,6 +145,8 @@ struct SimDev {
     int32_t ke_u, p_u;          // the sums count units of 2^-ke_u and 2^-p_u
     int32_t strict;
     int32_t pad1;
+    long long refine_seg;       // hold for refinement once the longest segment crossing a
+                                // cell edge exceeds this (2^-16 cells); 0: never
 };
 
 // Everything one launch of the step kernel needs.

@@ -713,6 +713,15 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         // would alias to less than 1.5) in one step unseen
         if (mm >= ((long long)(3 * nx) << 15))
             sc->err |= SIC_ERR_RANGE;
+        // hold the simulation (its later steps leave it as it is) when it
+        // needs the host: an error, or a particle longer than the refinement
+        // length (Sec. 2.6), to be split before the run goes on.  The decision
+        // is the simulation's own, so it stops at the same step alone or in
+        // any batch
+        if (sc->err)
+            sc->hold |= SIC_HOLD_ERROR;
+        if (S.refine_seg > 0 && mm > S.refine_seg)
+            sc->hold |= SIC_HOLD_REFINE;
     }
 }
 
@@ -756,7 +765,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
                                         const float *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, int nx, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, long long &ake, long long &ap, unsigned &mseg,
-                                        const WorkItemPL *pw, int dep, int segq, const MID &mid)
+                                        const WorkItemPL *pw, int dep, int segq, bool track_all, const MID &mid)
 {
     const unsigned *stU = reinterpret_cast<const unsigned *>(st);
     const float *stV = reinterpret_cast<const float *>(st + kStageBytesU);
@@ -1071,6 +1080,31 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
             }
         }
 
+        // a refinement length shorter than a cell: particles inside one cell
+        // count towards the longest one too (the cross-cell ones are measured
+        // where they are deposited)
+        if (track_all) {
+            unsigned longest = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (FULL || r < rn) {
+                    unsigned ub;
+                    bool seg = true;
+                    if (r + 1 < R && (FULL || r + 1 < rn))
+                        ub = u[r + 1 < R ? r + 1 : r];
+                    else if (lane < lane_last)
+                        ub = nu;
+                    else {
+                        ub = hu;
+                        seg = has_halo;
+                    }
+                    if (seg)
+                        longest = max(longest, (unsigned)abs((int)(ub - u[r])));
+                }
+            }
+            mseg = max(mseg, (unsigned)min(((unsigned long long)longest * (unsigned)nx4) >> 16, 0xffffffffull));
+        }
+
         // cross-cell segments: compact them into a task list and let every
         // lane take one in turn; a lane's slot is the count before it, summed
         // from one ballot per bit of the per-lane counts (0..R) when there are any
@@ -1220,7 +1254,17 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         const SimDev &S = A.sims[cur];
         const WorkItem *items = S.items;
         const int n_s = A.slot_begin[cur + 1] - A.slot_begin[cur];
+        // a full step leaves a held simulation (set by an earlier launch's
+        // epilogue, so the same for every block of this one) as it is: its
+        // items are all marked claimed, so no block picks it again in this
+        // launch.  An explicit deposit or push still runs.
+        if (PUSH && DEPOSIT && *(volatile unsigned *)&S.sc->hold) {
+            if (tid == 0)
+                atomicAdd(A.cursor + cur, (unsigned)n_s);
+            __syncthreads();  // the block's own pick below sees it taken
+        } else {
         const int nx = S.nx;
+        const bool track_all = S.refine_seg > 0 && S.refine_seg < (1ll << 16);  // refinement below a cell
         const int src = (int)S.sc->buf;
         const unsigned *Uin = S.U[src];
         const float *Vin = S.V[src];
@@ -1337,11 +1381,11 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     if (W.count == WT)
                         do_item<PUSH, DEPOSIT, PER_Q, true, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
                                                                   nx, ks, drift, rerr, st, tasks, ake, ap, mseg, plw,
-                                                                  S.deposit, S.seg_q, mid);
+                                                                  S.deposit, S.seg_q, track_all, mid);
                     else
                         do_item<PUSH, DEPOSIT, PER_Q, false, true, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
                                                                    nx, ks, drift, rerr, st, tasks, ake, ap, mseg, plw,
-                                                                   S.deposit, S.seg_q, mid);
+                                                                   S.deposit, S.seg_q, track_all, mid);
                     __syncwarp();
                     s ^= 1;
                 } else {
@@ -1349,11 +1393,11 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     if (W.count == WT)
                         do_item<PUSH, DEPOSIT, PER_Q, true, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
                                                                    nx, ks, drift, rerr, my_stage, tasks, ake, ap, mseg,
-                                                                   plw, S.deposit, S.seg_q, mid);
+                                                                   plw, S.deposit, S.seg_q, track_all, mid);
                     else
                         do_item<PUSH, DEPOSIT, PER_Q, false, false, GEN>(W, Uin, Vin, Uout, Vout, Qh, ek, hist, diff, sh,
                                                                     nx, ks, drift, rerr, my_stage, tasks, ake, ap, mseg,
-                                                                    plw, S.deposit, S.seg_q, mid);
+                                                                    plw, S.deposit, S.seg_q, track_all, mid);
                 }
             }
             if (!took) {
@@ -1436,6 +1480,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 A.tickets[cur] = 0u;
             }
         }
+        }  // not held
 
         // ---- next: the simulation with the most unclaimed items, if any
         int best = -1, most = 0;

@@ -8,7 +8,10 @@
 // mode is the one-simulation-per-launch baseline: one request at a time, run
 // to completion with sic_step.  A simulation gives the same bits alone and in
 // any batch, because every per-simulation result is an integer sum or a
-// fixed-order reduction.
+// fixed-order reduction.  A request with a refinement length (Sec. 2.6) holds
+// after the step that leaves a particle longer than it; the server then
+// refines it (its device memory grows) and it goes on in the next chunk, so it
+// is refined at the same steps alone and in the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,6 +50,8 @@ struct Active {
     sic_sim *sim = nullptr;
     int32_t left = 0;
     double t_admit = 0;
+    int64_t steps_seen = 0;       // the simulation's step count at the last look
+    int64_t segment_updates = 0;  // segments x steps, with the segments refinement added
 };
 
 }  // namespace
@@ -64,6 +69,7 @@ struct sic_server {
     bool plan_valid = false;
     Clock::time_point t0;
     int64_t completed = 0, segment_updates = 0, ticks = 0;
+    int64_t waits_slots = 0, waits_memory = 0, refinements = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // around each tick's steps
     double busy_s = 0;
 
@@ -84,14 +90,14 @@ size_t request_bytes(const sic_config &cfg, const int32_t *counts, int M, bool p
 {
     const int64_t n_alloc = sic_host::padded_tracers(counts, M);
     const int64_t n_items = sic_host::work_items(counts, M);
-    return sic_host::sim_layout(cfg.nx, n_alloc, n_items, per_q, 1, cfg.deposit).total;
+    return sic_host::sim_layout(cfg.nx, n_alloc, n_items, per_q, std::max(1, cfg.history_len), cfg.deposit).total;
 }
 
 int make_sim(sic_server *s, Request &r, sic_sim **out)
 {
     sic_config cfg = r.cfg;
     cfg.stream = s->stream;
-    cfg.history_len = 1;
+    cfg.history_len = std::max(1, cfg.history_len);
     if (r.horizontal)
         return sic_create_horizontal(&cfg, r.n_template, r.a.data(), r.b.data(), r.c.data(), out);
     cfg.tracers_per_sheet = r.counts.data();
@@ -114,14 +120,25 @@ void finish(sic_server *s, Active &a, int status, double t_done)
         if (status == SIC_OK)
             res.status = rc;
         res.steps = d.step;
-        res.segment_updates = a.req.segments * d.step;
+        res.segment_updates = a.segment_updates;
         res.field_energy = d.field_energy;
         res.kinetic_energy = d.kinetic_energy;
         res.momentum = d.momentum;
         res.charge_fixed = d.charge_fixed;
         s->used -= a.sim->dbytes;
         if (a.req.keep && res.status == SIC_OK) {
-            res.sim = a.sim;
+            // the caller owns it now: it gets a stream of its own, since the
+            // server's may be destroyed with the server
+            cudaStream_t own = nullptr;
+            if (cudaStreamSynchronize(s->stream) == cudaSuccess &&
+                cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) == cudaSuccess) {
+                a.sim->stream = own;
+                a.sim->own_stream = true;
+                res.sim = a.sim;
+            } else {
+                res.status = SIC_ECUDA;
+                sic_destroy(a.sim);
+            }
         } else {
             sic_destroy(a.sim);
         }
@@ -130,6 +147,27 @@ void finish(sic_server *s, Active &a, int status, double t_done)
     s->completed += 1;
     s->segment_updates += res.segment_updates;
     s->done.push_back(res);
+}
+
+// Account a simulation's steps since the last look (at its segments before any
+// refinement that follows) and refine it if it holds for that; its device
+// memory may grow.  Returns a SIC_E* code.
+int look(sic_server *srv, Active &a)
+{
+    SimScalars sc;
+    int st = sic_host::read_scalars(a.sim, &sc);
+    a.segment_updates += (sc.step - a.steps_seen) * sic_host::segments(a.sim);
+    a.steps_seen = sc.step;
+    a.left = a.req.n_steps - (int32_t)sc.step;
+    if (st == SIC_OK && (sc.hold & SIC_HOLD_REFINE) && a.left > 0) {
+        srv->refinements += 1;
+        const size_t before = a.sim->dbytes;
+        st = sic_host::refine_held(a.sim, nullptr);
+        srv->used += a.sim->dbytes - before;
+        srv->peak = std::max(srv->peak, srv->used);
+        srv->plan_valid = false;
+    }
+    return st;
 }
 
 int queue_request(sic_server *srv, Request &&r, int64_t *id)
@@ -259,8 +297,14 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
             finish(srv, a, SIC_EBUSY, srv->now());
             continue;
         }
-        if ((int)srv->active.size() >= srv->cfg.max_active || (int64_t)(srv->used + r.bytes) > srv->cfg.hbm_budget)
+        if ((int)srv->active.size() >= srv->cfg.max_active) {
+            srv->waits_slots += 1;
             break;
+        }
+        if ((int64_t)(srv->used + r.bytes) > srv->cfg.hbm_budget) {
+            srv->waits_memory += 1;
+            break;
+        }
         Active a;
         a.t_admit = srv->now();
         const int rc = make_sim(srv, r, &a.sim);
@@ -284,9 +328,13 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
         bool timed = false;
         if (srv->cfg.plain) {
             timed = cudaEventRecord(srv->ev[0], srv->stream) == cudaSuccess;
+            // the whole request, refining whenever it holds for that (Sec. 2.6)
             Active &a = srv->active.front();
-            rc = sic_step(a.sim, a.left);
-            a.left = 0;
+            while (rc == SIC_OK && a.left > 0) {
+                rc = sic_step(a.sim, std::min(a.left, srv->cfg.chunk_steps));
+                if (rc == SIC_OK)
+                    rc = look(srv, a);
+            }
         } else {
             int32_t k = srv->cfg.chunk_steps;
             for (const Active &a : srv->active)
@@ -312,8 +360,6 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
                             sic_host::launch(srv->plan[g], sic::MODE_STEP, 1.0f, 1, 1, srv->stream) != cudaSuccess)
                             rc = SIC_ECUDA;
             }
-            for (Active &a : srv->active)
-                a.left -= k;
         }
         if (timed)
             timed = cudaEventRecord(srv->ev[1], srv->stream) == cudaSuccess;
@@ -322,11 +368,20 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
         float ms = 0.f;
         if (timed && cudaEventElapsedTime(&ms, srv->ev[0], srv->ev[1]) == cudaSuccess)
             srv->busy_s += 1e-3 * ms;
+        // each simulation's own step count (a held one took fewer than the
+        // chunk); one that holds for refinement (Sec. 2.6) is refined here,
+        // its device memory growing, and goes on in the next chunk
+        std::vector<int> status(srv->active.size(), SIC_OK);
+        if (rc == SIC_OK && !srv->cfg.plain)
+            for (size_t i = 0; i < srv->active.size(); ++i)
+                status[i] = look(srv, srv->active[i]);
         const double t = srv->now();
         std::vector<Active> keep;
-        for (Active &a : srv->active) {
-            if (a.left <= 0 || rc != SIC_OK)
-                finish(srv, a, rc, t);
+        for (size_t i = 0; i < srv->active.size(); ++i) {
+            Active &a = srv->active[i];
+            const int st = rc != SIC_OK ? rc : status[i];
+            if (a.left <= 0 || st != SIC_OK)
+                finish(srv, a, st, t);
             else
                 keep.push_back(std::move(a));
         }
@@ -368,6 +423,9 @@ int sic_server_stats(sic_server *srv, sic_server_info *out)
     out->segment_updates = srv->segment_updates;
     out->ticks = srv->ticks;
     out->busy_s = srv->busy_s;
+    out->waits_slots = srv->waits_slots;
+    out->waits_memory = srv->waits_memory;
+    out->refinements = srv->refinements;
     return SIC_OK;
 }
 

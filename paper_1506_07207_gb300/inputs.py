@@ -51,6 +51,8 @@ class Problem:
     winding: np.ndarray           # int32 [M] closure offset in box lengths
     qm: float = 1.0
     half_step_init: bool = True
+    refine_length: float = 0.0    # Sec. 2.6 refinement length; 0: the run never refines
+    refine_split: float = 0.0     # length particles are split to when it refines; 0: refine_length
     # full per-tracer arrays (float64), or None when built from the template
     x_full: Optional[np.ndarray] = None
     v_full: Optional[np.ndarray] = None
@@ -303,6 +305,12 @@ class Request:
                               p["n_tracers"], eps=p["eps"], dt=dt, t_end=steps * dt,
                               name=f"req{self.index}")
         prob.n_steps = steps
+        # a served run refines once a particle passes half the box length, so
+        # it can go on past the point where a particle would outgrow the box
+        # (Sec. 3.2, Sec. 2.6); it then splits every particle longer than an
+        # eighth of the box, so it stops for refinement rarely
+        prob.refine_length = 0.5 * prob.L
+        prob.refine_split = 0.125 * prob.L
         return prob
 
 

@@ -16,8 +16,11 @@ from .sic import Server
 
 
 def run_trace(problems, arrivals, plain=False, hbm_budget=64 << 30, max_active=64, chunk_steps=32,
-              stream=None, keep=False):
-    """problems: list of ``inputs.Problem`` (horizontal sheets); arrivals: seconds, ascending."""
+              stream=None, keep=False, history=False):
+    """problems: list of ``inputs.Problem`` (horizontal sheets); arrivals: seconds, ascending.
+    history: every request keeps its per-step diagnostics [W_E, KE, P, Q] and
+    they are read back when it finishes (``results[i]["history"]``)."""
+    from .sic import adopt_sim
     order = np.argsort(np.asarray(arrivals, dtype=np.float64), kind="stable")
     srv = Server(hbm_budget=hbm_budget, max_active=max_active, chunk_steps=chunk_steps, plain=plain,
                  stream=stream)
@@ -30,11 +33,20 @@ def run_trace(problems, arrivals, plain=False, hbm_budget=64 << 30, max_active=6
         now = srv.sic_server_clock() - t0
         while nxt < n and arrivals[order[nxt]] <= now:
             i = int(order[nxt])
-            ids[srv.sic_server_submit_horizontal(problems[i], keep=keep)] = i
+            p = problems[i]
+            ids[srv.sic_server_submit_horizontal(p, keep=keep or history,
+                                                 history_len=p.n_steps if history else 1)] = i
             nxt += 1
         pending = srv.sic_server_tick()
         for r in srv.sic_server_results():
-            results[ids[r["id"]]] = r
+            i = ids[r["id"]]
+            if history and r["sim"]:
+                sim = adopt_sim(r["sim"], problems[i].nx, problems[i].counts)
+                r["history"] = sim.sic_history(problems[i].n_steps)
+                if not keep:
+                    sim.sic_destroy()
+                    r["sim"] = None
+            results[i] = r
         if pending == 0 and nxt < n:
             wait = arrivals[order[nxt]] - (srv.sic_server_clock() - t0)
             if wait > 0:
@@ -56,4 +68,8 @@ def run_trace(problems, arrivals, plain=False, hbm_budget=64 << 30, max_active=6
         "bytes_peak": int(stats["bytes_peak"]),
         "ticks": int(stats["ticks"]),
         "busy_s": float(stats["busy_s"]),
+        "failed": int(sum(1 for i in range(n) if results[i]["status"] != 0)),
+        "waits_slots": int(stats["waits_slots"]),
+        "waits_memory": int(stats["waits_memory"]),
+        "refinements": int(stats["refinements"]),
     }

@@ -33,6 +33,7 @@ EXPORTS = [
     "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
     "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
     "sic_step_batch_static", "sic_moments", "sic_refine", "sic_sheet_counts", "sic_batch_autotune",
+    "sic_run",
 ]
 
 
@@ -51,6 +52,8 @@ class sic_config(ctypes.Structure):
         ("history_len", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("deposit", ctypes.c_int32),
+        ("refine_length", ctypes.c_double),
+        ("refine_split", ctypes.c_double),
     ]
 
 
@@ -106,6 +109,9 @@ class sic_server_info(ctypes.Structure):
         ("segment_updates", ctypes.c_int64),
         ("ticks", ctypes.c_int64),
         ("busy_s", ctypes.c_double),
+        ("waits_slots", ctypes.c_int64),
+        ("waits_memory", ctypes.c_int64),
+        ("refinements", ctypes.c_int64),
     ]
 
 
@@ -123,6 +129,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_field": ([simp, dp], ctypes.c_int),
         "sic_push": ([simp], ctypes.c_int),
         "sic_step": ([simp, ctypes.c_int32], ctypes.c_int),
+        "sic_run": ([simp, ctypes.c_int32, lp], ctypes.c_int),
         "sic_step_batch": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_step_batch_static": ([P(simp), ctypes.c_int32, ip], ctypes.c_int),
         "sic_moments": ([simp, ctypes.c_int32, dp, dp], ctypes.c_int),
@@ -186,7 +193,8 @@ def sic_launch_count() -> int:
 
 
 def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
-            half_step_init=True, strict=False, history_len=1, stream=None, order=0):
+            half_step_init=True, strict=False, history_len=1, stream=None, order=0, refine=0.0,
+            refine_split=0.0):
     cfg = sic_config()
     cfg.nx = int(nx)
     cfg.box_length = float(L)
@@ -207,6 +215,8 @@ def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
     cfg.history_len = int(history_len)
     cfg.stream = ctypes.c_void_p(int(stream) if stream else 0)
     cfg.deposit = int(order)
+    cfg.refine_length = float(refine)
+    cfg.refine_split = float(refine_split) if refine else 0.0
     return cfg, keep
 
 
@@ -222,10 +232,10 @@ class Sim:
     # -- construction -------------------------------------------------------
     @classmethod
     def sic_create(cls, nx, L, dt, counts, closed, winding, x, v, w, qm=1.0, half_step_init=True,
-                   strict=False, history_len=1, stream=None, order=0):
+                   strict=False, history_len=1, stream=None, order=0, refine=0.0, refine_split=0.0):
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         cfg, keep = _config(nx, L, dt, counts.size, counts, closed, winding, qm, half_step_init,
-                            strict, history_len, stream, order)
+                            strict, history_len, stream, order, refine, refine_split)
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -239,34 +249,41 @@ class Sim:
 
     @classmethod
     def sic_create_horizontal(cls, nx, L, dt, x_template, v_sheet, w_sheet, qm=1.0,
-                              half_step_init=True, strict=False, history_len=1, stream=None, order=0):
+                              half_step_init=True, strict=False, history_len=1, stream=None, order=0,
+                              refine=0.0, refine_split=0.0):
         xt = np.ascontiguousarray(x_template, dtype=np.float64)
         vs = np.ascontiguousarray(v_sheet, dtype=np.float64)
         ws = np.ascontiguousarray(w_sheet, dtype=np.float64)
         if vs.shape != ws.shape:
             raise ValueError("v_sheet and w_sheet need one entry per sheet")
         cfg, keep = _config(nx, L, dt, vs.size, None, None, None, qm, half_step_init, strict,
-                            history_len, stream, order)
+                            history_len, stream, order, refine, refine_split)
         h = ctypes.c_void_p()
         _check(_lib.sic_create_horizontal(ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs), _dptr(ws),
                                           ctypes.byref(h)), "sic_create_horizontal")
         return cls(h, nx, xt.size * vs.size, np.full(vs.size, xt.size))
 
     @classmethod
-    def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None, order=0):
+    def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None, order=0,
+                     refine=None):
         """Create from an ``inputs.Problem`` (compact form when it has one); order
         is the deposit (SIC_DEPOSIT_*): 0 box particles, 1 piecewise linear
-        (Sec. 2.5), 2 and 3 PIC nearest grid point and cloud in cell."""
+        (Sec. 2.5), 2 and 3 PIC nearest grid point and cloud in cell; refine is
+        the refinement length (default: the problem's own)."""
         hl = history_len if history_len is not None else max(1, p.n_steps)
+        if refine is None:
+            refine = p.refine_length if order in (0, 1) else 0.0
+        split = p.refine_split if refine == p.refine_length else 0.0
         if horizontal is None:
             horizontal = p.is_horizontal
         if horizontal:
             return cls.sic_create_horizontal(p.nx, p.L, p.dt, p.x_template, p.v_sheet, p.w_sheet,
                                              qm=p.qm, half_step_init=p.half_step_init, strict=strict,
-                                             history_len=hl, stream=stream, order=order)
+                                             history_len=hl, stream=stream, order=order, refine=refine,
+                                             refine_split=split)
         return cls.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
                               qm=p.qm, half_step_init=p.half_step_init, strict=strict,
-                              history_len=hl, stream=stream, order=order)
+                              history_len=hl, stream=stream, order=order, refine=refine, refine_split=split)
 
     # -- the C ABI, one method per entry point ------------------------------
     @property
@@ -312,6 +329,21 @@ class Sim:
 
     def sic_step(self, n_steps: int):
         _check(_lib.sic_step(self.handle, int(n_steps)), "sic_step")
+
+    def sic_run(self, n_steps: int):
+        """n_steps steps, refining whenever a particle outgrows the refinement
+        length (Sec. 2.6); returns the number of tracers added."""
+        added = ctypes.c_int64()
+        _check(_lib.sic_run(self.handle, int(n_steps), ctypes.byref(added)), "sic_run")
+        self._update_counts()
+        return int(added.value)
+
+    def _update_counts(self):
+        counts = np.zeros(self.counts.size, dtype=np.int32)
+        _check(_lib.sic_sheet_counts(self.handle, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "sic_sheet_counts")
+        self.counts = counts.astype(np.int64)
+        self.n_tracers = int(counts.sum())
 
     def sic_diagnostics(self) -> dict:
         d = sic_diag()
@@ -444,12 +476,13 @@ class Server:
             raise ValueError("server destroyed")
         return self._h
 
-    def sic_server_submit_horizontal(self, p, n_steps=None, keep=False):
+    def sic_server_submit_horizontal(self, p, n_steps=None, keep=False, history_len=1):
         """Queue an ``inputs.Problem`` with horizontal sheets; returns the request id."""
         xt = np.ascontiguousarray(p.x_template, dtype=np.float64)
         vs = np.ascontiguousarray(p.v_sheet, dtype=np.float64)
         ws = np.ascontiguousarray(p.w_sheet, dtype=np.float64)
-        cfg, keepalive = _config(p.nx, p.L, p.dt, vs.size, None, None, None, p.qm, p.half_step_init)
+        cfg, keepalive = _config(p.nx, p.L, p.dt, vs.size, None, None, None, p.qm, p.half_step_init,
+                                 history_len=history_len, refine=p.refine_length, refine_split=p.refine_split)
         rid = ctypes.c_int64()
         _check(_lib.sic_server_submit_horizontal(self.handle, ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs),
                                                  _dptr(ws), int(p.n_steps if n_steps is None else n_steps),
@@ -463,7 +496,7 @@ class Server:
         v = np.ascontiguousarray(p.v, dtype=np.float64)
         w = np.ascontiguousarray(p.w, dtype=np.float64)
         cfg, keepalive = _config(p.nx, p.L, p.dt, p.counts.size, p.counts, p.closed, p.winding, p.qm,
-                                 p.half_step_init)
+                                 p.half_step_init, refine=p.refine_length, refine_split=p.refine_split)
         rid = ctypes.c_int64()
         _check(_lib.sic_server_submit(self.handle, ctypes.byref(cfg), _dptr(x), _dptr(v), _dptr(w),
                                       int(p.n_steps if n_steps is None else n_steps), int(bool(keep)),

@@ -143,3 +143,53 @@ def test_trace_replay_latencies(sic):
     assert np.all(out["latency_s"] > 0)
     assert out["segment_updates"] == sum(p.n_segments * p.n_steps for p in probs)
     assert out["p99_ms"] >= out["p50_ms"] > 0
+
+
+def test_refining_requests_equal_alone_and_plain(sic):
+    """Requests whose sheets stretch past their refinement length (Sec. 2.6)
+    hold at their own step, are refined by the server and go on; each ends
+    with the same bits as the same request run alone with sic_run, batched or
+    plain, and its segment-updates count the segments it had at every step."""
+    probs = []
+    for i, (v0, k) in enumerate([(1.5, 0.4), (1.2, 0.5), (2.0, 0.3)]):
+        p = inputs.two_stream(v0, 0.05, k, nx=128, n_sheets=16, n_tracers=512, eps=0.05, t_end=25.0 + 2 * i)
+        p.refine_length = 2.0 * p.L / p.nx
+        probs.append(p)
+    probs += _mix(3, seed=13)
+    alone = []
+    for p in probs:
+        sim = sic.Sim.from_problem(p, history_len=1)
+        try:
+            added = sim.sic_run(p.n_steps)
+            alone.append((_key(sim.sic_diagnostics()), sim.sic_get_state(), added))
+        finally:
+            sim.sic_destroy()
+    assert all(a[2] > 0 for a in alone[:3])            # the stretched ones did refine
+    for plain in (False, True):
+        srv = sic.Server(hbm_budget=8 << 30, max_active=8, chunk_steps=16, plain=plain)
+        ids = [srv.sic_server_submit_horizontal(p, keep=True) for p in probs]
+        got = {}
+        while srv.sic_server_tick() > 0:
+            for r in srv.sic_server_results():
+                got[r["id"]] = r
+        for r in srv.sic_server_results():
+            got[r["id"]] = r
+        st = srv.sic_server_stats()
+        srv.sic_server_destroy()
+        for rid, p, (key, (x, v), added) in zip(ids, probs, alone):
+            r = got[rid]
+            assert r["status"] == 0 and r["steps"] == p.n_steps
+            assert (r["field_energy"], r["kinetic_energy"], r["momentum"], r["charge_fixed"]) == key
+            kept = sic.adopt_sim(r["sim"], p.nx, np.full(p.n_sheets, 1))
+            try:
+                kept._update_counts()
+                xg, vg = kept.sic_get_state()
+                np.testing.assert_array_equal(xg, x)
+                np.testing.assert_array_equal(vg, v)
+            finally:
+                kept.sic_destroy()
+            if added == 0:
+                assert r["segment_updates"] == p.n_segments * p.n_steps
+            else:
+                assert r["segment_updates"] > p.n_segments * p.n_steps
+        assert st["bytes_in_use"] == 0

@@ -700,3 +700,71 @@ def test_fit_helpers_on_closed_forms():
     nx = 16
     E = np.cos(2 * np.pi * 3 * np.arange(nx) / nx)[None, :]
     assert abs(fits.mode(E, 3)[0] - 0.5) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_c_refinement_equals_the_python_one(seed):
+    """orc_refine (C) against oracle.refine (the Sec. 2.6 rule written out in
+    Python, pinned above): same counts, tracers, velocities and charges."""
+    L, counts, closed, winding, x, v, q = _refine_case(seed)
+    for l_ref in (0.05, 0.3, 5.0):
+        a = oracle.refine(L, counts, closed, winding, x, v, q, l_ref)
+        b = oracle.refine_c(L, counts, closed, winding, x, v, q, l_ref)
+        for u, w in zip(a, b):
+            np.testing.assert_array_equal(u, w)
+
+
+def _refined_run_by_hand(p, x, v, q, n_steps, l_ref, l_split):
+    """The refinement rule of Sec. 2.6 as a plain Python loop over the oracle's
+    pinned pieces: after each kick and drift, if a particle is longer than
+    l_ref, split (oracle.refine, pinned above) at l_split until none is."""
+    counts = np.array(p.counts, dtype=np.int32)
+    x, v, q = x.copy(), v.copy(), q.copy()
+    W = []
+    charge = oracle.deposit_seg(p.nx, p.L, counts, p.closed, p.winding, x, q)
+    for _ in range(n_steps):
+        _, E = oracle.field(p.nx, p.L, charge)
+        W.append(oracle.field_energy(p.nx, p.L, E))
+        v = v + p.dt * 1.0 * oracle.gather(p.nx, p.L, E, x)
+        x = x + p.dt * v
+        base, longest = 0, 0.0
+        for n, c, wd in zip(counts, p.closed, p.winding):
+            xs = x[base:base + n]
+            ends = np.r_[xs[1:], xs[0] + wd * p.L] if c else xs[1:]
+            longest = max(longest, np.abs(ends - xs[:len(ends)]).max())
+            base += n
+        if longest > l_ref:
+            while True:
+                c2, x, v, q = oracle.refine(p.L, counts, p.closed, p.winding, x, v, q, l_split)
+                added = c2.sum() - counts.sum()
+                counts = c2
+                if added == 0:
+                    break
+        charge = oracle.deposit_seg(p.nx, p.L, counts, p.closed, p.winding, x, q)
+    return counts, x, v, q, np.array(W)
+
+
+def test_refined_run_in_c_reduces_to_the_known_loops():
+    """orc_run_refined with no particle longer than l_ref is orc_run bit for
+    bit; with refinement it equals the rule written out as a Python loop over
+    the pinned oracle pieces, bit for bit, with the split length equal to the
+    hold length and with a shorter one (splitting ahead)."""
+    p = inputs.tiny_problem(5, n_sheets=4, max_tracers=60, nx=24, L=2.0, dt=0.05)
+    q = oracle.particle_charges(p.counts, p.closed, p.w)
+    steps = 12
+    r = oracle.run(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w, steps, half_step_init=False)
+    c = oracle.run_refined_each_step(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, q, steps,
+                                     l_ref=np.inf)
+    np.testing.assert_array_equal(c["x"], r["x"])
+    np.testing.assert_array_equal(c["v"], r["v"])
+    np.testing.assert_array_equal(c["W"], r["hist"][:-1, 0])
+    p = inputs.tiny_problem(8, n_sheets=3, max_tracers=40, nx=32, L=1.0, dt=0.05, spread=0.8)
+    q = oracle.particle_charges(p.counts, p.closed, p.w)
+    for l_ref, l_split in ((0.1, 0.1), (0.1, 0.03)):
+        hand = _refined_run_by_hand(p, p.x, p.v, q, 10, l_ref, l_split)
+        c = oracle.run_refined_each_step(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, q, 10,
+                                         l_ref=l_ref, l_split=l_split, max_growth=64.0)
+        assert c["counts"].sum() > 2 * p.counts.sum()
+        for got, want in zip((c["counts"], c["x"], c["v"], c["qseg"], c["W"]), hand):
+            np.testing.assert_array_equal(got, want)
+        assert c["n"][-1] == c["counts"].sum() and np.all(np.diff(c["n"]) >= 0)
