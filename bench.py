@@ -312,7 +312,7 @@ def main():
     ap.add_argument("--presteps", type=int, default=0,
                     help="advance the resident batch this many steps before the warm-up (evolved, filamented states)")
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate / batched capacity")
-    ap.add_argument("--overload", type=float, default=2.0,
+    ap.add_argument("--overload", type=float, default=0.0,
                     help="a second replay at this load (0: none): requests queue up")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

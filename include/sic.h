@@ -69,6 +69,7 @@ extern "C" {
 #define SIC_ESEGMENT_LONG (-5) /* strict mode: a segment is longer than the box */
 #define SIC_ETIMEOUT (-6)      /* a bounded device wait gave up */
 #define SIC_EBUSY (-7)         /* server: budget or slots exhausted */
+#define SIC_ELIMIT (-8)        /* a refinement would take the simulation past its tracer limit */
 
 /* Largest mesh the deposit kernels stage in shared memory. */
 #define SIC_NX_MAX 8192
@@ -130,6 +131,11 @@ typedef struct {
                                           longer than this is split (passes until none is): 0 =
                                           refine_length, else 0 < refine_split <= refine_length.
                                           A shorter one splits ahead, so holds come less often */
+    int64_t max_tracers;               /* refinement may grow the simulation to this many tracers:
+                                          0 = SIC_TRACERS_MAX.  A refinement that would pass it
+                                          is not done and the call returns SIC_ELIMIT (Sec. 2.6:
+                                          the tracer count grows about exponentially once the
+                                          sheets fold, so a run's length is bounded by memory) */
 } sic_config;
 
 /* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum

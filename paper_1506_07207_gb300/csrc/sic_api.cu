@@ -122,6 +122,8 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (!is_finite(c->refine_split) || c->refine_split < 0 || c->refine_split > c->refine_length)
         return SIC_EINVAL;
+    if (c->max_tracers < 0 || c->max_tracers > SIC_TRACERS_MAX)
+        return SIC_EINVAL;
     if (need_sheets) {
         if (!c->tracers_per_sheet || !c->sheet_closed)
             return SIC_EINVAL;
@@ -197,6 +199,12 @@ void plan_items(sic_sim *sim)
     }
 }
 
+}  // namespace
+namespace sic_host {
+int scalars_status(const SimScalars &sc);
+}
+namespace {
+
 int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
 {
     SimScalars sc;
@@ -204,13 +212,7 @@ int check_device_errors(sic_sim *sim, SimScalars *out = nullptr)
     CK(cudaStreamSynchronize(sim->stream));
     if (out)
         *out = sc;
-    if (sc.err & SIC_ERR_RANGE)
-        return SIC_ERANGE;
-    if (sc.err & SIC_ERR_SEGLONG)
-        return SIC_ESEGMENT_LONG;
-    if (sc.err & SIC_ERR_TIMEOUT)
-        return SIC_ETIMEOUT;
-    return SIC_OK;
+    return sic_host::scalars_status(sc);
 }
 
 // Clear the refinement hold of a synchronised simulation (the epilogue sets it
@@ -287,6 +289,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     sim->deposit = cfg->deposit;
     sim->refine_length = cfg->refine_length;
     sim->refine_split = cfg->refine_split > 0 ? cfg->refine_split : cfg->refine_length;
+    sim->max_tracers = cfg->max_tracers > 0 ? cfg->max_tracers : SIC_TRACERS_MAX;
     sim->sheet_off.assign(sim->M, 0);
     int64_t off = 0;
     for (int s = 0; s < sim->M; ++s) {
@@ -371,6 +374,17 @@ int initialise(sic_sim *sim)
 namespace sic_host {
 
 int read_scalars(sic_sim *sim, SimScalars *out) { return check_device_errors(sim, out); }
+
+int scalars_status(const SimScalars &sc)
+{
+    if (sc.err & SIC_ERR_RANGE)
+        return SIC_ERANGE;
+    if (sc.err & SIC_ERR_SEGLONG)
+        return SIC_ESEGMENT_LONG;
+    if (sc.err & SIC_ERR_TIMEOUT)
+        return SIC_ETIMEOUT;
+    return SIC_OK;
+}
 
 int64_t segments(const sic_sim *sim)
 {
@@ -832,10 +846,10 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
             added += counts[s] - sim->counts[s];
         }
     }
-    if (added == 0 || sim->n_tracers + added > SIC_TRACERS_MAX) {
+    if (added == 0 || sim->n_tracers + added > sim->max_tracers) {
         cudaFreeAsync(scratch, sim->stream);
         cudaStreamSynchronize(sim->stream);
-        return added == 0 ? SIC_OK : SIC_EINVAL;
+        return added == 0 ? SIC_OK : SIC_ELIMIT;
     }
     std::vector<int64_t> off(sim->M);
     int64_t n_alloc = 0;
@@ -1412,6 +1426,8 @@ const char *sic_strerror(int code)
         return "device wait timed out";
     case SIC_EBUSY:
         return "no capacity";
+    case SIC_ELIMIT:
+        return "refinement would pass the simulation's tracer limit";
     default:
         return "unknown error";
     }

@@ -36,6 +36,7 @@ int64_t work_items(const int32_t *counts, int M);
 struct sic_sim {
     double refine_length = 0.0;       // Sec. 2.6 refinement length, 0 = never
     double refine_split = 0.0;        // length particles are split to at a hold
+    int64_t max_tracers = 0;          // refinement limit (SIC_TRACERS_MAX when not given)
     int nx = 0;
     double L = 0, dt = 0, dx = 0, qm = 1;
     int strict = 0, hist_len = 1, half_step_init = 0;
@@ -69,6 +70,8 @@ namespace sic_host {
 // The simulation's device scalars (after synchronising its stream) and the
 // SIC_E* code of any device error they hold.
 int read_scalars(sic_sim *sim, SimScalars *out);
+// The SIC_E* code of the device error bits in a simulation's scalars.
+int scalars_status(const SimScalars &sc);
 // Refine until no particle is longer than the simulation's refinement length
 // (sic_refine passes) and clear its refinement hold; *added gets the tracers
 // added.

@@ -72,6 +72,8 @@ struct sic_server {
     int64_t waits_slots = 0, waits_memory = 0, refinements = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // around each tick's steps
     double busy_s = 0;
+    SimScalars *scal = nullptr;             // pinned: the active simulations' scalars
+    int scal_cap = 0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -126,7 +128,7 @@ void finish(sic_server *s, Active &a, int status, double t_done)
         res.momentum = d.momentum;
         res.charge_fixed = d.charge_fixed;
         s->used -= a.sim->dbytes;
-        if (a.req.keep && res.status == SIC_OK) {
+        if (a.req.keep && (res.status == SIC_OK || res.status == SIC_ELIMIT)) {
             // the caller owns it now: it gets a stream of its own, since the
             // server's may be destroyed with the server
             cudaStream_t own = nullptr;
@@ -151,11 +153,11 @@ void finish(sic_server *s, Active &a, int status, double t_done)
 
 // Account a simulation's steps since the last look (at its segments before any
 // refinement that follows) and refine it if it holds for that; its device
-// memory may grow.  Returns a SIC_E* code.
-int look(sic_server *srv, Active &a)
+// memory may grow.  sc: its scalars, read after its steps.  Returns a SIC_E*
+// code.
+int look(sic_server *srv, Active &a, const SimScalars &sc)
 {
-    SimScalars sc;
-    int st = sic_host::read_scalars(a.sim, &sc);
+    int st = sic_host::scalars_status(sc);
     a.segment_updates += (sc.step - a.steps_seen) * sic_host::segments(a.sim);
     a.steps_seen = sc.step;
     a.left = a.req.n_steps - (int32_t)sc.step;
@@ -168,6 +170,27 @@ int look(sic_server *srv, Active &a)
         srv->plan_valid = false;
     }
     return st;
+}
+
+// Read every active simulation's scalars with one synchronisation (they all
+// run on the server's stream) into srv->scal.
+int read_all(sic_server *srv)
+{
+    const int n = (int)srv->active.size();
+    if (n > srv->scal_cap) {
+        if (srv->scal)
+            cudaFreeHost(srv->scal);
+        srv->scal = nullptr;
+        srv->scal_cap = 0;
+        if (cudaMallocHost(&srv->scal, sizeof(SimScalars) * (size_t)std::max(n, 64)) != cudaSuccess)
+            return SIC_ENOMEM;
+        srv->scal_cap = std::max(n, 64);
+    }
+    for (int i = 0; i < n; ++i)
+        if (cudaMemcpyAsync(&srv->scal[i], srv->active[i].sim->h.sc, sizeof(SimScalars), cudaMemcpyDeviceToHost,
+                            srv->stream) != cudaSuccess)
+            return SIC_ECUDA;
+    return cudaStreamSynchronize(srv->stream) == cudaSuccess ? SIC_OK : SIC_ECUDA;
 }
 
 int queue_request(sic_server *srv, Request &&r, int64_t *id)
@@ -333,7 +356,9 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
             while (rc == SIC_OK && a.left > 0) {
                 rc = sic_step(a.sim, std::min(a.left, srv->cfg.chunk_steps));
                 if (rc == SIC_OK)
-                    rc = look(srv, a);
+                    rc = read_all(srv);
+                if (rc == SIC_OK)
+                    rc = look(srv, a, srv->scal[0]);
             }
         } else {
             int32_t k = srv->cfg.chunk_steps;
@@ -372,9 +397,12 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
         // chunk); one that holds for refinement (Sec. 2.6) is refined here,
         // its device memory growing, and goes on in the next chunk
         std::vector<int> status(srv->active.size(), SIC_OK);
-        if (rc == SIC_OK && !srv->cfg.plain)
-            for (size_t i = 0; i < srv->active.size(); ++i)
-                status[i] = look(srv, srv->active[i]);
+        if (rc == SIC_OK && !srv->cfg.plain) {
+            rc = read_all(srv);
+            if (rc == SIC_OK)
+                for (size_t i = 0; i < srv->active.size(); ++i)
+                    status[i] = look(srv, srv->active[i], srv->scal[i]);
+        }
         const double t = srv->now();
         std::vector<Active> keep;
         for (size_t i = 0; i < srv->active.size(); ++i) {
@@ -445,6 +473,8 @@ void sic_server_destroy(sic_server *srv)
     for (cudaEvent_t e : srv->ev)
         if (e)
             cudaEventDestroy(e);
+    if (srv->scal)
+        cudaFreeHost(srv->scal);
     if (srv->own_stream)
         cudaStreamDestroy(srv->stream);
     delete srv;

@@ -53,6 +53,7 @@ class Problem:
     half_step_init: bool = True
     refine_length: float = 0.0    # Sec. 2.6 refinement length; 0: the run never refines
     refine_split: float = 0.0     # length particles are split to when it refines; 0: refine_length
+    max_tracers: int = 0          # refinement limit on the tracer count; 0: the library's
     # full per-tracer arrays (float64), or None when built from the template
     x_full: Optional[np.ndarray] = None
     v_full: Optional[np.ndarray] = None
@@ -307,10 +308,12 @@ class Request:
         prob.n_steps = steps
         # a served run refines once a particle passes half the box length, so
         # it can go on past the point where a particle would outgrow the box
-        # (Sec. 3.2, Sec. 2.6); it then splits every particle longer than an
-        # eighth of the box, so it stops for refinement rarely
+        # (Sec. 3.2, Sec. 2.6), splitting every particle longer than a quarter
+        # of the box; refinement may grow it to 4 times its tracers (the count
+        # grows about exponentially once the sheets fold, Sec. 2.6)
         prob.refine_length = 0.5 * prob.L
-        prob.refine_split = 0.125 * prob.L
+        prob.refine_split = 0.25 * prob.L
+        prob.max_tracers = 4 * prob.n_tracers
         return prob
 
 

@@ -22,6 +22,7 @@ SIC_ERANGE = -4
 SIC_ESEGMENT_LONG = -5
 SIC_ETIMEOUT = -6
 SIC_EBUSY = -7
+SIC_ELIMIT = -8
 SIC_NX_MAX = 8192
 
 # every symbol include/sic.h declares
@@ -54,6 +55,7 @@ class sic_config(ctypes.Structure):
         ("deposit", ctypes.c_int32),
         ("refine_length", ctypes.c_double),
         ("refine_split", ctypes.c_double),
+        ("max_tracers", ctypes.c_int64),
     ]
 
 
@@ -194,7 +196,7 @@ def sic_launch_count() -> int:
 
 def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
             half_step_init=True, strict=False, history_len=1, stream=None, order=0, refine=0.0,
-            refine_split=0.0):
+            refine_split=0.0, max_tracers=0):
     cfg = sic_config()
     cfg.nx = int(nx)
     cfg.box_length = float(L)
@@ -217,6 +219,7 @@ def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
     cfg.deposit = int(order)
     cfg.refine_length = float(refine)
     cfg.refine_split = float(refine_split) if refine else 0.0
+    cfg.max_tracers = int(max_tracers)
     return cfg, keep
 
 
@@ -232,10 +235,11 @@ class Sim:
     # -- construction -------------------------------------------------------
     @classmethod
     def sic_create(cls, nx, L, dt, counts, closed, winding, x, v, w, qm=1.0, half_step_init=True,
-                   strict=False, history_len=1, stream=None, order=0, refine=0.0, refine_split=0.0):
+                   strict=False, history_len=1, stream=None, order=0, refine=0.0, refine_split=0.0,
+                   max_tracers=0):
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         cfg, keep = _config(nx, L, dt, counts.size, counts, closed, winding, qm, half_step_init,
-                            strict, history_len, stream, order, refine, refine_split)
+                            strict, history_len, stream, order, refine, refine_split, max_tracers)
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -250,14 +254,14 @@ class Sim:
     @classmethod
     def sic_create_horizontal(cls, nx, L, dt, x_template, v_sheet, w_sheet, qm=1.0,
                               half_step_init=True, strict=False, history_len=1, stream=None, order=0,
-                              refine=0.0, refine_split=0.0):
+                              refine=0.0, refine_split=0.0, max_tracers=0):
         xt = np.ascontiguousarray(x_template, dtype=np.float64)
         vs = np.ascontiguousarray(v_sheet, dtype=np.float64)
         ws = np.ascontiguousarray(w_sheet, dtype=np.float64)
         if vs.shape != ws.shape:
             raise ValueError("v_sheet and w_sheet need one entry per sheet")
         cfg, keep = _config(nx, L, dt, vs.size, None, None, None, qm, half_step_init, strict,
-                            history_len, stream, order, refine, refine_split)
+                            history_len, stream, order, refine, refine_split, max_tracers)
         h = ctypes.c_void_p()
         _check(_lib.sic_create_horizontal(ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs), _dptr(ws),
                                           ctypes.byref(h)), "sic_create_horizontal")
@@ -280,10 +284,11 @@ class Sim:
             return cls.sic_create_horizontal(p.nx, p.L, p.dt, p.x_template, p.v_sheet, p.w_sheet,
                                              qm=p.qm, half_step_init=p.half_step_init, strict=strict,
                                              history_len=hl, stream=stream, order=order, refine=refine,
-                                             refine_split=split)
+                                             refine_split=split, max_tracers=p.max_tracers)
         return cls.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
                               qm=p.qm, half_step_init=p.half_step_init, strict=strict,
-                              history_len=hl, stream=stream, order=order, refine=refine, refine_split=split)
+                              history_len=hl, stream=stream, order=order, refine=refine, refine_split=split,
+                              max_tracers=p.max_tracers)
 
     # -- the C ABI, one method per entry point ------------------------------
     @property
@@ -482,7 +487,8 @@ class Server:
         vs = np.ascontiguousarray(p.v_sheet, dtype=np.float64)
         ws = np.ascontiguousarray(p.w_sheet, dtype=np.float64)
         cfg, keepalive = _config(p.nx, p.L, p.dt, vs.size, None, None, None, p.qm, p.half_step_init,
-                                 history_len=history_len, refine=p.refine_length, refine_split=p.refine_split)
+                                 history_len=history_len, refine=p.refine_length, refine_split=p.refine_split,
+                                 max_tracers=p.max_tracers)
         rid = ctypes.c_int64()
         _check(_lib.sic_server_submit_horizontal(self.handle, ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs),
                                                  _dptr(ws), int(p.n_steps if n_steps is None else n_steps),
@@ -496,7 +502,8 @@ class Server:
         v = np.ascontiguousarray(p.v, dtype=np.float64)
         w = np.ascontiguousarray(p.w, dtype=np.float64)
         cfg, keepalive = _config(p.nx, p.L, p.dt, p.counts.size, p.counts, p.closed, p.winding, p.qm,
-                                 p.half_step_init, refine=p.refine_length, refine_split=p.refine_split)
+                                 p.half_step_init, refine=p.refine_length, refine_split=p.refine_split,
+                                 max_tracers=p.max_tracers)
         rid = ctypes.c_int64()
         _check(_lib.sic_server_submit(self.handle, ctypes.byref(cfg), _dptr(x), _dptr(v), _dptr(w),
                                       int(p.n_steps if n_steps is None else n_steps), int(bool(keep)),

@@ -64,7 +64,7 @@ def test_library_is_built_for_sm103a_only(sic):
 
 def test_strerror(sic):
     assert sic.sic_strerror(0) == "ok"
-    for code in range(-7, 0):
+    for code in range(-8, 0):
         assert sic.sic_strerror(code) not in ("ok", "unknown error")
     assert sic.sic_strerror(-99) == "unknown error"
 
@@ -147,3 +147,19 @@ def test_null_handles_are_rejected(sic):
     assert lib.sic_history(None, None, 4, None) == sic.SIC_EINVAL
     assert lib.sic_step(None, 1) == sic.SIC_EINVAL
     assert lib.sic_step_batch_static(None, 1, None) == sic.SIC_EINVAL
+
+
+def test_refinement_settings_are_checked(sic):
+    """refine_length at least 2^-10 of a cell, refine_split within
+    (0, refine_length], max_tracers within [0, SIC_TRACERS_MAX]; rejected
+    before anything reaches the GPU."""
+    a = _base()
+    for kw in (dict(refine=-1.0), dict(refine=float("nan")), dict(refine=1e-7),
+               dict(refine=0.2, refine_split=0.3), dict(refine=0.2, refine_split=-0.1),
+               dict(refine=0.2, max_tracers=-1), dict(refine=0.2, max_tracers=(1 << 28) + 1),
+               dict(refine=0.2, order=2)):
+        with pytest.raises(sic.SicError) as e:
+            sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                               a["x"], a["v"], a["w"], **kw)
+        assert e.value.code == sic.SIC_EINVAL, kw
+    assert sic.sic_strerror(sic.SIC_ELIMIT) != "unknown error"

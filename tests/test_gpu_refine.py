@@ -244,3 +244,25 @@ def test_refinement_factor_of_the_two_stream_setup(sic):
     assert onset(f3) < onset(f1)
     # ... at about the same exponential rate
     assert abs(a3 / a1 - 1) < 0.35, (a1, a3)
+
+
+def test_refinement_stops_at_the_tracer_limit(sic):
+    """A refinement that would take the simulation past its tracer limit is
+    not done: sic_run returns SIC_ELIMIT at the step that needed it, with the
+    state of that step intact (and its charge), so the run's result so far can
+    still be read."""
+    p = _stretching()
+    p.max_tracers = p.n_tracers + 40
+    sim = sic.Sim.from_problem(p, history_len=p.n_steps)
+    try:
+        q0 = sim.sic_diagnostics()["charge_fixed"]
+        with pytest.raises(sic.SicError) as e:
+            sim.sic_run(p.n_steps)
+        assert e.value.code == sic.SIC_ELIMIT
+        d = sim.sic_diagnostics()
+        assert 0 < d["step"] < p.n_steps and d["charge_fixed"] == q0
+        sim._update_counts()
+        assert sim.n_tracers <= p.max_tracers
+        assert sim.sic_history(p.n_steps).shape[0] == d["step"]
+    finally:
+        sim.sic_destroy()

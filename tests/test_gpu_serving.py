@@ -193,3 +193,21 @@ def test_refining_requests_equal_alone_and_plain(sic):
             else:
                 assert r["segment_updates"] > p.n_segments * p.n_steps
         assert st["bytes_in_use"] == 0
+
+
+def test_request_at_its_tracer_limit_ends_with_its_steps(sic):
+    """A served request whose refinement would pass its tracer limit ends
+    there with SIC_ELIMIT and the steps it took; the others are unaffected."""
+    p = inputs.two_stream(1.5, 0.05, 0.4, nx=128, n_sheets=16, n_tracers=512, eps=0.05, t_end=30.0)
+    p.refine_length = 2.0 * p.L / p.nx
+    p.max_tracers = p.n_tracers + 40
+    others = _mix(3, seed=17)
+    srv = sic.Server(hbm_budget=8 << 30, max_active=8, chunk_steps=16)
+    rid = srv.sic_server_submit_horizontal(p)
+    oids = [srv.sic_server_submit_horizontal(q) for q in others]
+    while srv.sic_server_tick() > 0:
+        pass
+    res = {r["id"]: r for r in srv.sic_server_results()}
+    srv.sic_server_destroy()
+    assert res[rid]["status"] == sic.SIC_ELIMIT and 0 < res[rid]["steps"] < p.n_steps
+    assert all(res[i]["status"] == 0 and res[i]["steps"] == q.n_steps for i, q in zip(oids, others))
