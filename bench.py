@@ -302,8 +302,8 @@ def main():
     ap.add_argument("--impl", default="sic", choices=["sic", "reference"])
     ap.add_argument("--workload", default="serving", choices=["serving", "two_stream"],
                     help="serving: the request-mix sample; two_stream: the 8.4M-segment two-stream run alone")
-    ap.add_argument("--deposit", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC")
+    ap.add_argument("--deposit", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="0 box particles (Sec. 2.3), 1 piecewise linear (Sec. 2.5), 2 PIC NGP, 3 PIC CIC, 4 first-order weighting (Sec. 2.4)")
     ap.add_argument("--autotune", type=int, default=1, help="tune the batch schedule before timing (0: default)")
     ap.add_argument("--requests", type=int, default=512,
                     help="leading requests of the seeded 4096-request mix to serve (and hold resident for value)")

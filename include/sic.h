@@ -92,6 +92,12 @@ typedef struct sic_sim sic_sim;
 #define SIC_DEPOSIT_PIC_CIC 3 /* PIC comparison: every tracer a point charge shared
                                  between the two cells whose centres bracket it
                                  (cloud in cell, Sec. 2.4) */
+#define SIC_DEPOSIT_FIRST 4   /* box particles with first-order weighting (Sec. 2.4): each
+                                 slice of a particle shared between the two nodes around
+                                 it by the hat of half-width dx, so the mesh holds charge
+                                 per node x_j = j dx; the field integrates between nodes
+                                 by the trapezoid rule, E_{j+1} = E_j + dx (rho_j +
+                                 rho_{j+1}) / 2, zero mean */
 
 /*
  * Problem statement (Sec. 2.2-2.3): M sheets of ordered tracers on a periodic

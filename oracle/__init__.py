@@ -67,6 +67,11 @@ def _load():
             lib.orc_deposit_pic.restype = ctypes.c_int
             lib.orc_field.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             lib.orc_field.restype = None
+            lib.orc_field_nodes.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
+            lib.orc_field_nodes.restype = None
+            lib.orc_deposit_first.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                              ip, bp, ip, dp, dp, dp]
+            lib.orc_deposit_first.restype = ctypes.c_int
             lib.orc_gather.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_long,
                                        dp, dp]
             lib.orc_gather.restype = None
@@ -112,7 +117,8 @@ def _sheets(counts, closed, winding):
 def deposit(nx, L, counts, closed, winding, x, w, order=0):
     """Charge per cell (Eq. overlap and Eq. rho_sum, times dx); order 1 uses
     the piecewise-linear particles of Sec. 2.5, 2 and 3 the PIC point charges
-    of the tracers (nearest grid point, cloud in cell)."""
+    of the tracers (nearest grid point, cloud in cell), 4 the first-order
+    weighting of the particles onto the nodes (Sec. 2.4; charge per node)."""
     lib = _load()
     counts, closed, winding = _sheets(counts, closed, winding)
     x, w = _f64(x), _f64(w)
@@ -123,7 +129,7 @@ def deposit(nx, L, counts, closed, winding, x, w, order=0):
         lib.orc_deposit_pic(int(nx), float(L), x.size, _ptr(x, ctypes.c_double), _ptr(w, ctypes.c_double),
                             int(order), _ptr(out, ctypes.c_double))
         return out
-    fn = lib.orc_deposit_linear if order == 1 else lib.orc_deposit
+    fn = {1: lib.orc_deposit_linear, 4: lib.orc_deposit_first}.get(order, lib.orc_deposit)
     rc = fn(int(nx), float(L), counts.size, _ptr(counts, ctypes.c_int32),
                          _ptr(closed, ctypes.c_uint8), _ptr(winding, ctypes.c_int32),
                          _ptr(x, ctypes.c_double), _ptr(w, ctypes.c_double),
@@ -157,14 +163,16 @@ def moments(nx, L, counts, closed, winding, x, v, w, weighting=0):
     return n, j
 
 
-def field(nx, L, charge):
-    """(rho, E) from the per-cell charge: neutralised density and node field."""
+def field(nx, L, charge, nodes=False):
+    """(rho, E) from the per-cell charge: neutralised density and node field;
+    nodes=True takes the charge on the nodes (first-order weighting) and
+    integrates between nodes by the trapezoid rule (orc_field_nodes)."""
     lib = _load()
     charge = _f64(charge)
     rho = np.zeros(int(nx))
     E = np.zeros(int(nx))
-    lib.orc_field(int(nx), float(L), _ptr(charge, ctypes.c_double),
-                  _ptr(rho, ctypes.c_double), _ptr(E, ctypes.c_double))
+    fn = lib.orc_field_nodes if nodes else lib.orc_field
+    fn(int(nx), float(L), _ptr(charge, ctypes.c_double), _ptr(rho, ctypes.c_double), _ptr(E, ctypes.c_double))
     return rho, E
 
 

@@ -299,11 +299,21 @@ int orc_deposit_linear_seg(int nx, double L, int n_sheets, const int32_t *counts
 
 /* The deposit of the given kind: 0 box particles (Sec. 2.3), 1 piecewise
  * linear particles (Sec. 2.5), 2 and 3 PIC point charges (NGP, CIC). */
+int orc_moments(int nx, double L, int n_sheets, const int32_t *counts,
+                const uint8_t *closed, const int32_t *winding, const double *x,
+                const double *v, const double *w, int weighting, double *n,
+                double *j);
+int orc_deposit_first(int nx, double L, int n_sheets, const int32_t *counts,
+                      const uint8_t *closed, const int32_t *winding,
+                      const double *x, const double *w, double *charge);
+
 static int deposit_order(int order, int nx, double L, int n_sheets,
                          const int32_t *counts, const uint8_t *closed,
                          const int32_t *winding, const double *x,
                          const double *w, double *charge)
 {
+    if (order == 4)
+        return orc_deposit_first(nx, L, n_sheets, counts, closed, winding, x, w, charge);
     if (order == 1)
         return orc_deposit_linear(nx, L, n_sheets, counts, closed, winding, x, w, charge);
     if (order == 2 || order == 3) {
@@ -449,6 +459,66 @@ void orc_field(int nx, double L, const double *charge, double *rho, double *E)
     free(e);
 }
 
+/*
+ * First-order weighting of the box particles (Sec. 2.4): node X_j = j dx gets
+ * the charge sum_s q_s int b_s(x) W1(x - X_j) dx, each slice of a particle
+ * shared between the two nodes around it by the hat W1 of half-width dx.  This
+ * is the first-order density of orc_moments times dx (computed there, with
+ * the velocities unused).
+ */
+int orc_deposit_first(int nx, double L, int n_sheets, const int32_t *counts,
+                      const uint8_t *closed, const int32_t *winding,
+                      const double *x, const double *w, double *charge)
+{
+    long n = 0;
+    for (int s = 0; s < n_sheets; ++s)
+        n += counts[s];
+    double *v0 = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *j = (double *)malloc(sizeof(double) * (size_t)nx);
+    int rc = orc_moments(nx, L, n_sheets, counts, closed, winding, x, v0, w, 1, charge, j);
+    double dx = L / nx;
+    for (int k = 0; k < nx; ++k)
+        charge[k] *= dx;
+    free(v0);
+    free(j);
+    return rc;
+}
+
+/*
+ * Field solve for charge on the nodes (first-order weighting, Sec. 2.4, with
+ * Sec. 2.1, C = 1): n_j = charge_j / dx, rho_j = n_j - mean(n) at X_j, and
+ * dE/dx = rho integrated from node to node by the trapezoid rule,
+ * E'_0 = 0, E'_{j+1} = E'_j + dx (rho_j + rho_{j+1}) / 2 (rho_nx = rho_0);
+ * E_j = E'_j - mean(E').  rho and E may be NULL.
+ */
+void orc_field_nodes(int nx, double L, const double *charge, double *rho, double *E)
+{
+    double dx = L / nx;
+    double *r = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *e = (double *)malloc(sizeof(double) * (size_t)nx);
+    double nbar = 0.0;
+    for (int j = 0; j < nx; ++j)
+        nbar += charge[j] / dx;
+    nbar /= nx;
+    for (int j = 0; j < nx; ++j)
+        r[j] = charge[j] / dx - nbar;
+    e[0] = 0.0;
+    for (int j = 0; j + 1 < nx; ++j)
+        e[j + 1] = e[j] + dx * 0.5 * (r[j] + r[j + 1]);
+    double emean = 0.0;
+    for (int j = 0; j < nx; ++j)
+        emean += e[j];
+    emean /= nx;
+    for (int j = 0; j < nx; ++j) {
+        if (rho)
+            rho[j] = r[j];
+        if (E)
+            E[j] = e[j] - emean;
+    }
+    free(r);
+    free(e);
+}
+
 /* Linear-weighting gather of the node field at one position (Sec. 2.3). */
 static double gather_one(int nx, double dx, const double *E, double x)
 {
@@ -495,7 +565,9 @@ double orc_field_energy(int nx, double L, const double *E)
  * e_hist (n_steps+1 rows of nx, may be NULL) gets every E^n.
  * On exit x = x^{n_steps}, v = v^{n_steps-1/2}, E_out = E^{n_steps} (may be NULL).
  * order selects the deposit: 0 box particles (Sec. 2.3), 1 piecewise linear
- * (Sec. 2.5), 2 PIC nearest grid point, 3 PIC cloud in cell (Sec. 2.4).
+ * (Sec. 2.5), 2 PIC nearest grid point, 3 PIC cloud in cell (Sec. 2.4),
+ * 4 first-order weighting of the box particles onto the nodes (Sec. 2.4),
+ * whose field comes from orc_field_nodes.
  */
 int orc_run(int nx, double L, double dt, double qm, int half_step_init,
             int n_sheets, const int32_t *counts, const uint8_t *closed,
@@ -509,7 +581,10 @@ int orc_run(int nx, double L, double dt, double qm, int half_step_init,
     int rc = deposit_order(order, nx, L, n_sheets, counts, closed, winding, x, w, charge);
     if (rc)
         goto done;
-    orc_field(nx, L, charge, NULL, E);
+    if (order == 4)
+        orc_field_nodes(nx, L, charge, NULL, E);
+    else
+        orc_field(nx, L, charge, NULL, E);
     if (half_step_init) {
         orc_gather(nx, L, E, n_tracers, x, ex);
         for (long i = 0; i < n_tracers; ++i)
@@ -553,7 +628,10 @@ int orc_run(int nx, double L, double dt, double qm, int half_step_init,
         rc = deposit_order(order, nx, L, n_sheets, counts, closed, winding, x, w, charge);
         if (rc)
             goto done;
-        orc_field(nx, L, charge, NULL, E);
+        if (order == 4)
+            orc_field_nodes(nx, L, charge, NULL, E);
+        else
+            orc_field(nx, L, charge, NULL, E);
     }
     if (E_out)
         memcpy(E_out, E, sizeof(double) * (size_t)nx);

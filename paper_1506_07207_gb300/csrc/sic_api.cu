@@ -111,14 +111,14 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (c->history_len < 1)
         return SIC_EINVAL;
-    if (c->deposit < SIC_DEPOSIT_BOX || c->deposit > SIC_DEPOSIT_PIC_CIC)
+    if (c->deposit < SIC_DEPOSIT_BOX || c->deposit > SIC_DEPOSIT_FIRST)
         return SIC_EINVAL;
     // the refinement length: off, or at least 2^-10 of a cell (the hold test
     // measures particles in 2^-16 cells) with a deposit that has particles
     if (!is_finite(c->refine_length) || c->refine_length < 0)
         return SIC_EINVAL;
-    if (c->refine_length > 0 &&
-        (c->refine_length < c->box_length / c->nx / 1024.0 || c->deposit > SIC_DEPOSIT_LINEAR))
+    if (c->refine_length > 0 && (c->refine_length < c->box_length / c->nx / 1024.0 ||
+                                 c->deposit == SIC_DEPOSIT_PIC_NGP || c->deposit == SIC_DEPOSIT_PIC_CIC))
         return SIC_EINVAL;
     if (!is_finite(c->refine_split) || c->refine_split < 0 || c->refine_split > c->refine_length)
         return SIC_EINVAL;
@@ -802,7 +802,7 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
 {
     if (!sim || !is_finite(l_ref) || l_ref <= 0)
         return SIC_EINVAL;
-    if (sim->deposit != SIC_DEPOSIT_BOX && sim->deposit != SIC_DEPOSIT_LINEAR)
+    if (sim->deposit == SIC_DEPOSIT_PIC_NGP || sim->deposit == SIC_DEPOSIT_PIC_CIC)
         return SIC_EINVAL;
     if (n_added)
         *n_added = 0;

@@ -237,6 +237,85 @@ __device__ __forceinline__ void emit_cross(long long ua, int ja, long long ub, i
     acc.add(jb, (long long)q - F - inner);
 }
 
+// First-order weighting of a box particle (Sec. 2.4), between 32.32 cell
+// coordinates ua and ub (any order, the lower end's cell possibly outside
+// [0, nx)), q units.  Its zero-order piece in each cell (the pieces of
+// emit_cross: first, whole cells inside, the rest) is shared between the
+// cell's two nodes by the piece's centroid: the upper node gets round(piece
+// (s0 + s1) / 2) of a piece over [s0, s1] of the cell, the lower one the
+// rest.  That is the hat weighting of a uniform density exactly, up to the
+// rounding of each share, and the node charges sum to q.
+__device__ __forceinline__ int wrap_near(int c, int nx)
+{
+    while (c < 0)
+        c += nx;
+    while (c >= nx)
+        c -= nx;
+    return c;
+}
+
+template <class ACC>
+__device__ __forceinline__ void emit_first(long long ua, long long ub, int q, int nx, ACC &acc,
+                                           unsigned long long *diff, int *diff_used, unsigned &maxseg)
+{
+    if (ub < ua) {
+        const long long t = ua;
+        ua = ub;
+        ub = t;
+    }
+    const int ja = wrap_near(cell_of(ua), nx);
+    const int ja1 = (ja + 1 == nx) ? 0 : ja + 1;
+    const unsigned la = frac_of(ua), lb = frac_of(ub);
+    const long long ncut = (long long)cell_of(ub) - (long long)cell_of(ua);
+    const long long span = ub - ua;
+    maxseg = max(maxseg, (unsigned)min((unsigned long long)span >> 16, 0xffffffffull));
+    if (ncut == 0) {  // inside one cell (or a point): centroid (la + lb) / 2
+        const long long Y =
+            (long long)(((unsigned long long)q * ((unsigned long long)la + lb) + (1ull << 32)) >> 33);
+        acc.add(ja, (long long)q - Y);
+        acc.add(ja1, Y);
+        return;
+    }
+    const float df = la ? __uint2float_rn(0u - la) : 4294967296.0f;  // a to the first edge
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(span_to_float(span)));
+    long long F = __float2int_rn(__fmul_rn(__fmul_rn(df, inv), __int2float_rn(q)));
+    F = min(max(F, 0ll), (long long)q);
+    const long long nint = ncut - 1;
+    const long long P = nint > 0 ? (long long)(((unsigned long long)q << 32) / (unsigned long long)span) : 0;
+    const long long inner = nint * P;
+    if (F > (long long)q - inner)
+        F = (long long)q - inner;
+    const long long Lr = (long long)q - F - inner;  // the last cell's piece
+    // shares of the upper nodes: first piece over [la, 1], whole cells 1/2,
+    // last piece over [0, lb]
+    const long long YF = (long long)(((unsigned long long)F * ((1ull << 32) + la) + (1ull << 32)) >> 33);
+    const long long YP = (P + 1) >> 1;
+    const long long YL = (long long)(((unsigned long long)Lr * lb + (1ull << 32)) >> 33);
+    const int jb = wrap_near(cell_of(ub), nx);
+    const int jb1 = (jb + 1 == nx) ? 0 : jb + 1;
+    acc.add(ja, F - YF);
+    if (nint == 0) {  // first and last cells adjacent: node ja + 1 is jb
+        acc.add(jb, YF + Lr - YL);
+    } else {
+        acc.add(ja1, YF + P - YP);
+        // nodes ja + 2 .. ja + nint get P each (the upper share of the cell
+        // below and the lower share of their own)
+        if (nint > 1) {
+            const int js = (ja1 + 1 == nx) ? 0 : ja1 + 1;
+            if (nint - 1 <= 2) {
+                acc.add(js, P);
+                if (nint - 1 == 2)
+                    acc.add((js + 1 == nx) ? 0 : js + 1, P);
+            } else {
+                range_add(js, nint - 1, P, nx, diff, diff_used);
+            }
+        }
+        acc.add(jb, YP + Lr - YL);
+    }
+    acc.add(jb1, YL);
+}
+
 // Piecewise-linear particles (Sec. 2.5).  The particle from ua to ub (tracers
 // i, i+1) has neighbours from up (tracer i-1) and to un (tracer i+2) along
 // the sheet, all in 32.32 cell coordinates, with charges qp, qs, qn.  Its
@@ -660,7 +739,21 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         sumD += make_i128(sh.hi[w], sh.lo[w]);
 
     float wloc = 0.f;
-    {
+    if (S.deposit == SIC_DEPOSIT_FIRST) {
+        // charge on the nodes: the trapezoid rule between nodes makes the node
+        // field the mean of K at j and j + 1 (K_nx = K_0), 2 E_j = K_j + K_{j+1}
+        long long run = run0;
+        __int128 K = (__int128)nx * ((__int128)nx * run - (__int128)j0 * qtot) - sumD;
+        for (int j = j0; j < j1; ++j) {
+            run += (long long)sm[j];
+            const __int128 Kn = (__int128)nx * ((__int128)nx * run - (__int128)(j + 1) * qtot) - sumD;
+            const __int128 K2 = K + Kn;
+            sE[j] = __fmul_rn(i128_to_float(K2, S.ek_exp - 1), S.ek_mant);
+            const float kn = i128_to_float(K2, -61);
+            wloc = __fmaf_rn(kn, kn, wloc);
+            K = Kn;
+        }
+    } else {
         long long run = run0;
         for (int j = j0; j < j1; ++j) {
             const __int128 d = (__int128)nx * run - (__int128)j * qtot;
@@ -936,7 +1029,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
         }
     }
 
-    if (GEN && DEPOSIT && dep >= SIC_DEPOSIT_PIC_NGP) {
+    if (GEN && DEPOSIT && (dep == SIC_DEPOSIT_PIC_NGP || dep == SIC_DEPOSIT_PIC_CIC)) {
         // PIC comparison deposits (Sec. 2.4): every tracer a point charge of
         // 2 Qh units, in its cell (nearest grid point) or shared between the
         // two cells whose centres bracket it (cloud in cell: the second gets
@@ -1005,6 +1098,36 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
         const int qs_sheet = 2 * W.qh;
         __syncwarp();
 
+        if (GEN && dep == SIC_DEPOSIT_FIRST) {
+            // first-order weighting (Sec. 2.4): every particle shared out to
+            // nodes by emit_first, straight into the block's mesh
+            DirectAdd acc{hist};
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (FULL || r < rn) {
+                    unsigned ub;
+                    int qb;
+                    bool seg = true;
+                    if (r + 1 < R && (FULL || r + 1 < rn)) {
+                        ub = u[r + 1 < R ? r + 1 : r];
+                        qb = q[r + 1 < R ? r + 1 : r];
+                    } else if (lane < lane_last) {
+                        ub = nu;
+                        qb = nq;
+                    } else {
+                        ub = hu;
+                        qb = hq;
+                        seg = has_halo;
+                    }
+                    if (seg) {
+                        const long long ua64 = cell_coord(u[r], nx);
+                        emit_first(ua64, ua64 + seg_span(u[r], ub, nx4),
+                                   PER_Q ? (segq ? q[r] : q[r] + qb) : qs_sheet, nx, acc, diff, &sh.diff_used,
+                                   mseg);
+                    }
+                }
+            }
+        } else {
         // segments inside one cell: whole charges summed per lane into three
         // buckets for the cells c0, c0 + 1, c0 + 2 of its first tracer (a lane
         // that reaches other cells falls back to run merging); the segments
@@ -1189,6 +1312,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
                 }
             }
         }
+        }  // not first-order
         __syncwarp();  // pts and tasks are rewritten by the next item
     }
 
@@ -1630,10 +1754,17 @@ __global__ void __launch_bounds__(1024) k_field_out(const SimDev S)
     for (int w = 0; w < NWW; ++w)
         sumD += make_i128(s_hi[w], s_lo[w]);
     run = run0;
+    const bool nodes = S.deposit == SIC_DEPOSIT_FIRST;  // E_j = (K_j + K_{j+1}) / 2
     for (int j = j0; j < j1; ++j) {
         const long long mj = S.mesh_last[j];
         const __int128 d = (__int128)nx * run - (__int128)j * qtot;
-        S.E64[j] = i128_to_double((__int128)nx * d - sumD) * S.E_scale;
+        const __int128 K = (__int128)nx * d - sumD;
+        if (nodes) {
+            const __int128 Kn = (__int128)nx * ((__int128)nx * (run + mj) - (__int128)(j + 1) * qtot) - sumD;
+            S.E64[j] = i128_to_double(K + Kn) * (0.5 * S.E_scale);
+        } else {
+            S.E64[j] = i128_to_double(K) * S.E_scale;
+        }
         S.rho64[j] = i128_to_double((__int128)nx * mj - qtot) * S.rho_scale;
         run += mj;
     }

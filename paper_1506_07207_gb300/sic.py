@@ -276,7 +276,7 @@ class Sim:
         the refinement length (default: the problem's own)."""
         hl = history_len if history_len is not None else max(1, p.n_steps)
         if refine is None:
-            refine = p.refine_length if order in (0, 1) else 0.0
+            refine = p.refine_length if order in (0, 1, 4) else 0.0
         split = p.refine_split if refine == p.refine_length else 0.0
         if horizontal is None:
             horizontal = p.is_horizontal
@@ -410,7 +410,7 @@ def sic_step_batch(sims, n_steps):
 
 SIC_STATIC_MAX_SIMS = 64
 SIC_AUTOTUNE_CANDIDATES = 10
-SIC_DEPOSIT_BOX, SIC_DEPOSIT_LINEAR, SIC_DEPOSIT_PIC_NGP, SIC_DEPOSIT_PIC_CIC = 0, 1, 2, 3
+SIC_DEPOSIT_BOX, SIC_DEPOSIT_LINEAR, SIC_DEPOSIT_PIC_NGP, SIC_DEPOSIT_PIC_CIC, SIC_DEPOSIT_FIRST = 0, 1, 2, 3, 4
 
 
 def sic_step_batch_static(sims, n_steps):

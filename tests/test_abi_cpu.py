@@ -124,7 +124,7 @@ def test_server_rejects_bad_config(sic):
 
 def test_bad_deposit_scheme(sic):
     a = _base()
-    for dep in (-1, 4, 99):
+    for dep in (-1, 5, 99):
         with pytest.raises(sic.SicError) as e:
             sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
                                a["x"], a["v"], a["w"], order=dep)

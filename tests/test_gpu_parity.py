@@ -36,7 +36,7 @@ def sic():
 def _oracle_fields(p, x, order=0):
     charge = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, x, p.w, order=order)
     n = charge / (p.L / p.nx)
-    rho, E = oracle.field(p.nx, p.L, charge)
+    rho, E = oracle.field(p.nx, p.L, charge, nodes=(order == 4))   # first order: charge on nodes
     return n, rho, E
 
 

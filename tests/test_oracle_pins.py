@@ -768,3 +768,69 @@ def test_refined_run_in_c_reduces_to_the_known_loops():
         for got, want in zip((c["counts"], c["x"], c["v"], c["qseg"], c["W"]), hand):
             np.testing.assert_array_equal(got, want)
         assert c["n"][-1] == c["counts"].sum() and np.all(np.diff(c["n"]) >= 0)
+
+
+# ------------------------------------------- first-order weighting (NEXT-3) ----
+# Sec. 2.4: each slice of a particle shared between the two nodes around it by
+# the hat of half-width dx; the field of the node charges by the trapezoid rule.
+
+def test_node_field_by_hand():
+    """Trapezoid integration between nodes, worked by hand: one unit of extra
+    charge on node 0 of four nodes (dx = 1, mean 1/4 per node).  rho =
+    (3/4, -1/4, -1/4, -1/4); E' = 0, (3/4 - 1/4)/2, that - 1/4, that - 1/4 =
+    0, 1/4, 0, -1/4 (mean 0)."""
+    rho, E = oracle.field(4, 4.0, [1.0, 0.0, 0.0, 0.0], nodes=True)
+    np.testing.assert_allclose(rho, [0.75, -0.25, -0.25, -0.25], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(E, [0.0, 0.25, 0.0, -0.25], rtol=0, atol=1e-15)
+
+
+def test_first_order_field_of_a_cosine_density():
+    """A density 1 + A cos(kx) weighted to the nodes by the hat gives node
+    charge dx (1 + A s^2 cos(k X_j)), s = sinc(k dx / 2); the trapezoid rule
+    integrates A s^2 cos(k X) between nodes to E_j = (A / k) s^2 (h / tan h)
+    sin(k X_j), h = k dx / 2 (sum the differences of sines).  The tracers
+    resolve the density to O(1/N^2)."""
+    from scipy.optimize import brentq
+    L, nx, A, N = 1.0, 16, 0.4, 4000
+    k = 2 * np.pi / L
+    dx = L / nx
+
+    def cdf(x):
+        return x + A / k * np.sin(k * x)
+
+    xs = np.array([brentq(lambda t: cdf(t) - L * i / N, -1e-9, L + 1e-9) for i in range(N)])
+    w = np.full(N, L / N)
+    charge = oracle.deposit(nx, L, [N], [1], [1], xs, w, order=4)
+    assert math.isclose(charge.sum(), w.sum(), rel_tol=1e-13)
+    X = np.arange(nx) * dx
+    s2 = np.sinc(k * dx / 2 / np.pi) ** 2
+    np.testing.assert_allclose(charge / dx, 1 + A * s2 * np.cos(k * X), atol=2e-6)
+    _, E = oracle.field(nx, L, charge, nodes=True)
+    h = k * dx / 2
+    np.testing.assert_allclose(E, (A / k) * s2 * (h / np.tan(h)) * np.sin(k * X), atol=2e-7)
+
+
+def test_first_order_uniform_sheet_and_charge():
+    """A closed sheet of evenly spaced tracers puts the same charge on every
+    node (zero field); on random sheets the node charges sum to the charge."""
+    nx, L, n = 8, 2.0, 64
+    x = (np.arange(n) + 0.3) * (L / n)
+    c = oracle.deposit(nx, L, [n], [1], [1], x, np.full(n, L / n), order=4)
+    np.testing.assert_allclose(c, L / nx, rtol=1e-13)
+    _, E = oracle.field(nx, L, c, nodes=True)
+    assert np.abs(E).max() < 1e-13
+    p = inputs.tiny_problem(9, n_sheets=5, max_tracers=50, nx=12, L=2.0)
+    c = oracle.deposit(p.nx, p.L, p.counts, p.closed, p.winding, p.x, p.w, order=4)
+    q = oracle.particle_charges(p.counts, p.closed, p.w)
+    assert math.isclose(c.sum(), q.sum(), rel_tol=1e-13)
+
+
+def test_first_order_run_keeps_charge_and_oscillates():
+    """A Langmuir run with first-order weighting: total charge constant and
+    the leapfrog plasma frequency (as for the other deposits)."""
+    p = inputs.langmuir(nx=128)
+    r = oracle.run_problem(p, record_E=True, order=4)
+    assert np.ptp(r["hist"][:, 3]) <= 1e-12 * r["hist"][0, 3]
+    t = np.arange(p.n_steps + 1) * p.dt
+    w = fits.oscillation_omega(t, fits.mode(r["E_hist"], 1).imag)
+    assert abs(w / theory.leapfrog_omega(p.dt) - 1) < 2e-3
