@@ -142,6 +142,12 @@ typedef struct {
                                           is not done and the call returns SIC_ELIMIT (Sec. 2.6:
                                           the tracer count grows about exponentially once the
                                           sheets fold, so a run's length is bounded by memory) */
+    double charge_unit;                /* charge of one fixed-point unit: 0 = chosen from the
+                                          largest weight; else > 0, and every particle's charge
+                                          must fit 2^28 units (SIC_ERANGE otherwise).  Simulations
+                                          that hold parts of one set of sheets (split over GPUs)
+                                          give the same unit so that their integer meshes add up
+                                          to the whole one's bit for bit */
 } sic_config;
 
 /* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum

@@ -124,6 +124,8 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (c->max_tracers < 0 || c->max_tracers > SIC_TRACERS_MAX)
         return SIC_EINVAL;
+    if (!is_finite(c->charge_unit) || c->charge_unit < 0)
+        return SIC_EINVAL;
     if (need_sheets) {
         if (!c->tracers_per_sheet || !c->sheet_closed)
             return SIC_EINVAL;
@@ -623,7 +625,11 @@ int sic_create(const sic_config *cfg, const double *x_host, const double *v_host
             base += sim->counts[s];
         }
     }
-    sim->sigma = choose_sigma(max_w);
+    sim->sigma = cfg->charge_unit > 0 ? 1.0 / cfg->charge_unit : choose_sigma(max_w);
+    if (std::llround(max_w * sim->sigma * 0.5) * 2 > (1LL << 28)) {
+        delete sim;
+        return SIC_ERANGE;  // a particle's charge would not fit 2^28 units
+    }
     sim->sheet_qh.assign(sim->M, 0);
     {
         int64_t base = 0;
@@ -717,7 +723,11 @@ int sic_create_horizontal(const sic_config *cfg, int32_t n_template, const doubl
     sim->winding.assign(sim->M, 1);
     sim->n_tracers = (int64_t)n_template * sim->M;
     sim->per_q = false;
-    sim->sigma = choose_sigma(max_w);
+    sim->sigma = cfg->charge_unit > 0 ? 1.0 / cfg->charge_unit : choose_sigma(max_w);
+    if (std::llround(max_w * sim->sigma * 0.5) * 2 > (1LL << 28)) {
+        delete sim;
+        return SIC_ERANGE;  // a particle's charge would not fit 2^28 units
+    }
     sim->sheet_qh.assign(sim->M, 0);
     for (int s = 0; s < sim->M; ++s)
         sim->sheet_qh[s] = (int32_t)std::llround(w_sheet_host[s] * sim->sigma * 0.5);

@@ -56,6 +56,7 @@ class sic_config(ctypes.Structure):
         ("refine_length", ctypes.c_double),
         ("refine_split", ctypes.c_double),
         ("max_tracers", ctypes.c_int64),
+        ("charge_unit", ctypes.c_double),
     ]
 
 
@@ -196,7 +197,7 @@ def sic_launch_count() -> int:
 
 def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
             half_step_init=True, strict=False, history_len=1, stream=None, order=0, refine=0.0,
-            refine_split=0.0, max_tracers=0):
+            refine_split=0.0, max_tracers=0, charge_unit=0.0):
     cfg = sic_config()
     cfg.nx = int(nx)
     cfg.box_length = float(L)
@@ -220,6 +221,7 @@ def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
     cfg.refine_length = float(refine)
     cfg.refine_split = float(refine_split) if refine else 0.0
     cfg.max_tracers = int(max_tracers)
+    cfg.charge_unit = float(charge_unit)
     return cfg, keep
 
 
@@ -236,10 +238,10 @@ class Sim:
     @classmethod
     def sic_create(cls, nx, L, dt, counts, closed, winding, x, v, w, qm=1.0, half_step_init=True,
                    strict=False, history_len=1, stream=None, order=0, refine=0.0, refine_split=0.0,
-                   max_tracers=0):
+                   max_tracers=0, charge_unit=0.0):
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         cfg, keep = _config(nx, L, dt, counts.size, counts, closed, winding, qm, half_step_init,
-                            strict, history_len, stream, order, refine, refine_split, max_tracers)
+                            strict, history_len, stream, order, refine, refine_split, max_tracers, charge_unit)
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)

@@ -163,3 +163,17 @@ def test_refinement_settings_are_checked(sic):
                                a["x"], a["v"], a["w"], **kw)
         assert e.value.code == sic.SIC_EINVAL, kw
     assert sic.sic_strerror(sic.SIC_ELIMIT) != "unknown error"
+
+
+def test_charge_unit_is_checked(sic):
+    """A given fixed-point unit must be positive and coarse enough that every
+    particle's charge fits 2^28 units; checked before the GPU is touched."""
+    a = _base()
+    with pytest.raises(sic.SicError) as e:
+        sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                           a["x"], a["v"], a["w"], charge_unit=-1.0)
+    assert e.value.code == sic.SIC_EINVAL
+    with pytest.raises(sic.SicError) as e:
+        sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                           a["x"], a["v"], a["w"], charge_unit=1e-12)
+    assert e.value.code == sic.SIC_ERANGE
