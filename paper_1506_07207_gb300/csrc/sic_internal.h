@@ -94,10 +94,13 @@ struct WorkItemPL {
 // energy and momentum terms as 128-bit fixed-point integers (units of
 // 2^-ke_u and 2^-p_u set per simulation, each item's FP32 partial truncated
 // to them), so the totals do not depend on the order of the additions; the
-// longest segment by atomicMax.
+// longest segment by atomicMax.  A block adds each 32-bit limb of its
+// 128-bit (two's complement) sum into its own 64-bit word, with atomics that
+// return nothing; the sum modulo 2^128 is sum_i limb_i 2^(32 i).  The words
+// cannot overflow: fewer than 2^32 blocks add to them between epilogues.
 struct SimAccum {
-    unsigned long long ke[2];   // sum Qh (v_old^2 + v_new^2)  ((cells/step)^2 2^-ke_u), lo/hi
-    unsigned long long p[2];    // sum Qh (v_old + v_new)  (cells/step 2^-p_u)     , lo/hi
+    unsigned long long ke[4];   // sum Qh (v_old^2 + v_new^2)  ((cells/step)^2 2^-ke_u), limbs
+    unsigned long long p[4];    // sum Qh (v_old + v_new)  (cells/step 2^-p_u), limbs
     unsigned long long maxseg;  // longest segment crossing a cell edge, 2^-16 cells
     unsigned long long pad[3];
 };

@@ -504,6 +504,14 @@ __device__ __forceinline__ double i128_words_to_double(unsigned long long lo, un
     return __fma_rn((double)(long long)hi, 18446744073709551616.0, __ull2double_rn(lo));
 }
 
+// ---- programmatic dependent launch: a step launched with it may start while
+// the step before it in the stream finishes; it waits for that step's end
+// (and its memory) before it reads anything that step writes, and lets the
+// next one start once it has no more items to begin.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- bulk-copy staging (cp.async.bulk into shared memory, mbarrier completion)
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -534,12 +542,24 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+// The tracer state is read once per step and is larger than L2: its copies
+// are marked first to be evicted, so the kernel's code, the simulation
+// tables and the meshes stay in L2 from step to step.
+__device__ __forceinline__ unsigned long long l2_evict_first()
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
+                                         unsigned long long pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
 }
 
 // A bounded wait on a stage barrier: true once the phase of this parity has
@@ -595,13 +615,15 @@ __device__ __forceinline__ void stage_issue(const WorkItem &W, const unsigned *U
     const unsigned b = (unsigned)(n * 4 + 15) & ~15u;  // the same for positions, velocities, charges
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, (PER_Q ? 3u : 2u) * b);
-    bulk_g2s(st, Uin + W.t0, b, bar);
-    bulk_g2s(st + kStageBytesU, Vin + W.t0, b, bar);
+    const unsigned long long pol = l2_evict_first();
+    bulk_g2s(st, Uin + W.t0, b, bar, pol);
+    bulk_g2s(st + kStageBytesU, Vin + W.t0, b, bar, pol);
     if (PER_Q)
-        bulk_g2s(st + kStageBytesU + kStageBytesV, Qh + W.t0, b, bar);
+        bulk_g2s(st + kStageBytesU + kStageBytesV, Qh + W.t0, b, bar, pol);
 }
 
 struct Shared {
+    SimDev sim;              // the current simulation's descriptor
     unsigned long long mbar[NW][2];
     struct alignas(16) Slot {
         WorkItem w;
@@ -612,11 +634,19 @@ struct Shared {
     int pl_prevq[NW];
     int taken;               // items of the current simulation the block's warps took
     int pick_n[NW], pick_s[NW];  // per warp: most unclaimed items, in which slot
-    unsigned long long ke[2], p[2], maxseg;
+    unsigned long long ke[2], p[2];          // 128-bit sums of the rare path (sum_add)
+    long long wke[NW][2], wp[NW][2];         // each warp's KE and P sums (lo, hi)
+    unsigned wmseg[NW];                      // each warp's longest segment
+    unsigned hold, buf;                      // the simulation's scalars at entry
     long long w64[NW];
     long long hi[NW], lo[NW];
-    double da[NW], db[NW], dc[NW];
-    long long dm[NW];
+    double da[NW];
+    // the epilogue's inputs, read in one round trip with the mesh: the sums'
+    // limbs (ke 0-3, p 4-7), the longest segment (8), and the scalars
+    unsigned long long pre[9];
+    long long pre_step;
+    double pre_we;
+    unsigned pre_err, pre_hold;
 };
 
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
@@ -661,45 +691,99 @@ __device__ __forceinline__ float pow2f(int e)
     return __uint_as_float((unsigned)(e + 127) << 23);
 }
 
-__device__ __forceinline__ float i128_to_float(__int128 v, int e2)
+// |v| normalised to its top 32 bits t (|v| = t 2^(e - 96) up to the bits
+// below them), once for several scalings
+struct Norm128 {
+    unsigned t;
+    int e;  // 96 - leading zeros
+    bool neg, zero;
+};
+
+__device__ __forceinline__ Norm128 norm128(__int128 v)
 {
-    if (v == 0)
-        return 0.f;
-    const bool neg = v < 0;
-    const unsigned __int128 m = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    Norm128 r;
+    r.zero = v == 0;
+    r.neg = v < 0;
+    const unsigned __int128 m = r.neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
     const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
-    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-    const unsigned t = (unsigned)((m << lz) >> 96);
-    const int e = 96 - lz + e2;  // |v| * 2^e2 = t * 2^e
+    const int lz = hi ? __clzll((long long)hi) : (lo ? 64 + __clzll((long long)lo) : 0);
+    r.t = (unsigned)((m << lz) >> 96);
+    r.e = 96 - lz;
+    return r;
+}
+
+// v 2^e2 as a float from its normalised form
+__device__ __forceinline__ float norm_to_float(const Norm128 &n, int e2)
+{
+    if (n.zero)
+        return 0.f;
+    const int e = n.e + e2;  // |v| 2^e2 = t 2^e
     const int e_a = e / 2, e_b = e - e / 2;
-    const float f = __fmul_rn(__fmul_rn(__uint2float_rn(t), pow2f(e_a)), pow2f(e_b));
-    return neg ? -f : f;
+    const float f = __fmul_rn(__fmul_rn(__uint2float_rn(n.t), pow2f(e_a)), pow2f(e_b));
+    return n.neg ? -f : f;
+}
+
+__device__ __forceinline__ float i128_to_float(__int128 v, int e2) { return norm_to_float(norm128(v), e2); }
+
+// x 2^k exactly (x 2^k a normal double or zero)
+__device__ __forceinline__ double times_pow2(double x, int k)
+{
+    return x * __hiloint2double((1023 + k) << 20, 0);
 }
 
 // Field solve of one simulation (Sec. 2.1 with C = 1) by the block holding
 // its last ticket: sm (nx u64) and sE (nx floats) are this block's scratch.
 //   P_j = sum_{i<j} mesh_i, D_j = nx P_j - j Q (= nx sigma E'_j exactly),
-//   K_j = nx D_j - sum_j D_j (= nx^2 sigma E_j, zero mean), all integers;
+//   K_j = nx D_j - sum_j D_j (= nx^2 sigma E_j, zero mean), all integers,
+//   with sum_j D_j = nx (nx - 1) Q / 2 - nx sum_i i mesh_i (from
+//   sum_j P_j = sum_i (nx - 1 - i) mesh_i), so it needs no pass of its own;
 //   kick table Ek_j = K_j e_scale rounded once to FP32, field energy from
-//   the squares of K_j 2^-60 summed in FP32 per thread and FP64 across.
+//   the squares of K_j 2^-60 summed in FP32 within a warp and FP64 across.
+// Everything it reads from global memory (the mesh, the step's sums, the
+// scalars) is requested at once, so it waits for memory once.
 // The double-precision field and density for the host are recomputed from
 // mesh_last on request (k_field_out), so this path has no FP64 per cell.
 __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *sm, float *sE, Shared &sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = S.nx;
-    for (int j = tid; j < nx; j += B) {
-        const unsigned long long mv = __ldcg(S.mesh + j);
-        sm[j] = mv;
-        S.mesh[j] = 0ull;
-        S.mesh_last[j] = (long long)mv;
+    if (tid >= 32 && tid < 41) {
+        const unsigned long long *src = tid < 36 ? &S.acc->ke[tid - 32] : tid < 40 ? &S.acc->p[tid - 36] : &S.acc->maxseg;
+        sh.pre[tid - 32] = __ldcg(src);
+    } else if (tid == 64) {
+        sh.pre_step = __ldcg(&S.sc->step);
+    } else if (tid == 65) {
+        sh.pre_we = __ldcg(&S.sc->we);
+    } else if (tid == 66) {
+        sh.pre_err = __ldcg(&S.sc->err);
+    } else if (tid == 67) {
+        sh.pre_hold = __ldcg(&S.sc->hold);
+    }
+    for (int j = tid; j < nx; j += 4 * B) {
+        unsigned long long mv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            mv[k] = j + k * B < nx ? __ldcg(S.mesh + j + k * B) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (j + k * B < nx) {
+                sm[j + k * B] = mv[k];
+                S.mesh[j + k * B] = 0ull;
+                S.mesh_last[j + k * B] = (long long)mv[k];
+            }
+        }
     }
     __syncthreads();
     const int per = (nx + B - 1) / B;
     const int j0 = min(tid * per, nx), j1 = min(j0 + per, nx);
     long long lsum = 0;
-    for (int j = j0; j < j1; ++j)
-        lsum += (long long)sm[j];
+    __int128 m1 = 0;  // sum_j j mesh_j over this thread's cells
+#pragma unroll 1
+    for (int j = j0; j < j1; ++j) {
+        const long long mv = (long long)sm[j];
+        lsum += mv;
+        m1 += (__int128)j * mv;
+    }
     long long incl = lsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -707,114 +791,123 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         if (lane >= o)
             incl += t;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        m1 += shfl_down_i128(m1, o);
     if (lane == 31)
         sh.w64[warp] = incl;
+    if (lane == 0) {
+        sh.hi[warp] = (long long)(m1 >> 64);
+        sh.lo[warp] = (long long)(unsigned long long)m1;
+    }
     __syncthreads();
     long long before = 0, qtot = 0;
+    __int128 M1 = 0;
     for (int w = 0; w < NW; ++w) {
         if (w < warp)
             before += sh.w64[w];
         qtot += sh.w64[w];
+        M1 += make_i128(sh.hi[w], sh.lo[w]);
     }
     const long long run0 = incl - lsum + before;
+    const __int128 sumD = (__int128)((long long)nx * (nx - 1) / 2) * qtot - (__int128)nx * M1;
 
-    __int128 dsum = 0;
-    {
-        long long run = run0;
-        for (int j = j0; j < j1; ++j) {
-            dsum += (__int128)nx * run - (__int128)j * qtot;
-            run += (long long)sm[j];
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        dsum += shfl_down_i128(dsum, o);
-    if (lane == 0) {
-        sh.hi[warp] = (long long)(dsum >> 64);
-        sh.lo[warp] = (long long)(unsigned long long)dsum;
-    }
-    __syncthreads();
-    __int128 sumD = 0;
-    for (int w = 0; w < NW; ++w)
-        sumD += make_i128(sh.hi[w], sh.lo[w]);
-
+    // K from cell to cell: D_{j+1} = D_j + nx mesh_j - Q
     float wloc = 0.f;
+    __int128 D = (__int128)nx * run0 - (__int128)j0 * qtot;
+    __int128 K = (__int128)nx * D - sumD;
     if (S.deposit == SIC_DEPOSIT_FIRST) {
         // charge on the nodes: the trapezoid rule between nodes makes the node
         // field the mean of K at j and j + 1 (K_nx = K_0), 2 E_j = K_j + K_{j+1}
-        long long run = run0;
-        __int128 K = (__int128)nx * ((__int128)nx * run - (__int128)j0 * qtot) - sumD;
+#pragma unroll 1
         for (int j = j0; j < j1; ++j) {
-            run += (long long)sm[j];
-            const __int128 Kn = (__int128)nx * ((__int128)nx * run - (__int128)(j + 1) * qtot) - sumD;
-            const __int128 K2 = K + Kn;
-            sE[j] = __fmul_rn(i128_to_float(K2, S.ek_exp - 1), S.ek_mant);
-            const float kn = i128_to_float(K2, -61);
+            D += (__int128)nx * (long long)sm[j] - qtot;
+            const __int128 Kn = (__int128)nx * D - sumD;
+            const Norm128 n2 = norm128(K + Kn);
+            sE[j] = __fmul_rn(norm_to_float(n2, S.ek_exp - 1), S.ek_mant);
+            const float kn = norm_to_float(n2, -61);
             wloc = __fmaf_rn(kn, kn, wloc);
             K = Kn;
         }
     } else {
-        long long run = run0;
+#pragma unroll 2
         for (int j = j0; j < j1; ++j) {
-            const __int128 d = (__int128)nx * run - (__int128)j * qtot;
-            const __int128 K = (__int128)nx * d - sumD;
-            sE[j] = __fmul_rn(i128_to_float(K, S.ek_exp), S.ek_mant);
-            const float kn = i128_to_float(K, -60);
+            const Norm128 nk = norm128(K);
+            sE[j] = __fmul_rn(norm_to_float(nk, S.ek_exp), S.ek_mant);
+            const float kn = norm_to_float(nk, -60);
             wloc = __fmaf_rn(kn, kn, wloc);
-            run += (long long)sm[j];
+            D += (__int128)nx * (long long)sm[j] - qtot;
+            K = (__int128)nx * D - sumD;
         }
     }
-    double wd = (double)wloc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-        wd += __shfl_down_sync(0xffffffffu, wd, o);
+        wloc = __fadd_rn(wloc, __shfl_down_sync(0xffffffffu, wloc, o));
     if (lane == 0)
-        sh.da[warp] = wd;
+        sh.da[warp] = (double)wloc;
     __syncthreads();
     for (int j = tid; j < nx; j += B) {
         const int j1n = (j + 1 == nx) ? 0 : j + 1;
         S.Ek[j] = make_float2(sE[j], sE[j1n] - sE[j]);
     }
-    if (tid == 0) {
+    // the scalars: four threads, each one chain of (slow) FP64 arithmetic
+    SimScalars *sc = S.sc;
+    const long long step = sh.pre_step;
+    double *row = nullptr;
+    if (record && (tid == 0 || tid == 32 || tid == 64))
+        row = S.hist + 4 * (step % S.hist_len);
+    auto limbs = [](const unsigned long long *l) -> double {
+        const unsigned __int128 u = (unsigned __int128)l[0] + ((unsigned __int128)l[1] << 32) +
+                                    ((unsigned __int128)l[2] << 64) + ((unsigned __int128)l[3] << 96);
+        return i128_words_to_double((unsigned long long)u, (unsigned long long)(u >> 64));
+    };
+    if (tid == 32 && record)
+        row[1] = S.ke_scale * times_pow2(limbs(sh.pre), -S.ke_u);
+    if (tid == 64 && record)
+        row[2] = S.p_scale * times_pow2(limbs(sh.pre + 4), -S.p_u);
+    if (tid == 96) {
         double w = 0.0;
         for (int i = 0; i < NW; ++i)
             w += sh.da[i];
+        sc->we = w * S.we_scale;
+    }
+    if (tid == 0) {
         SimAccum *ac = S.acc;
-        const double kk = ldexp(i128_words_to_double(__ldcg(&ac->ke[0]), __ldcg(&ac->ke[1])), -S.ke_u);
-        const double pp = ldexp(i128_words_to_double(__ldcg(&ac->p[0]), __ldcg(&ac->p[1])), -S.p_u);
-        const long long mm = (long long)__ldcg(&ac->maxseg);
-        ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
-        SimScalars *sc = S.sc;
+        const long long mm = (long long)sh.pre[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            ac->ke[k] = ac->p[k] = 0ull;
+        ac->maxseg = 0ull;
         if (record) {
-            const long long step = sc->step;
-            double *row = S.hist + 4 * (step % S.hist_len);
-            row[0] = sc->we;
-            row[1] = S.ke_scale * kk;
-            row[2] = S.p_scale * pp;
-            row[3] = (double)sc->q_total;
+            row[0] = sh.pre_we;
+            row[3] = (double)qtot;
             sc->step = step + 1;
         }
-        sc->we = w * S.we_scale;
         sc->q_total = qtot;
         sc->maxseg = mm;
+        unsigned err = sh.pre_err, hold = sh.pre_hold;
         if (S.strict && mm > ((long long)nx << 16))
-            sc->err |= SIC_ERR_SEGLONG;
+            err |= SIC_ERR_SEGLONG;
         // the position format holds a segment exactly while it is shorter than
         // 2 box lengths; one of 1.5 or more ends the run with a range error.
         // Each end moves less than half a box per step, so a segment cannot
         // get from below 1.5 box lengths to 2.5 or more (where its difference
         // would alias to less than 1.5) in one step unseen
         if (mm >= ((long long)(3 * nx) << 15))
-            sc->err |= SIC_ERR_RANGE;
+            err |= SIC_ERR_RANGE;
         // hold the simulation (its later steps leave it as it is) when it
         // needs the host: an error, or a particle longer than the refinement
         // length (Sec. 2.6), to be split before the run goes on.  The decision
         // is the simulation's own, so it stops at the same step alone or in
         // any batch
-        if (sc->err)
-            sc->hold |= SIC_HOLD_ERROR;
+        if (err)
+            hold |= SIC_HOLD_ERROR;
         if (S.refine_seg > 0 && mm > S.refine_seg)
-            sc->hold |= SIC_HOLD_REFINE;
+            hold |= SIC_HOLD_REFINE;
+        if (err != sh.pre_err)
+            sc->err = err;
+        if (hold != sh.pre_hold)
+            sc->hold = hold;
     }
 }
 
@@ -911,20 +1004,22 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
         const int *pqq = STAGED ? stQ + l0 : Qh + base + l0;
 #pragma unroll
         for (int k = 0; k < R / 4; ++k) {
-            const uint4 t = reinterpret_cast<const uint4 *>(pu)[k];
+            // from global memory (unstaged): streaming loads, first out of L2
+            const uint4 t = STAGED ? reinterpret_cast<const uint4 *>(pu)[k] : __ldcs(reinterpret_cast<const uint4 *>(pu) + k);
             u[4 * k] = t.x;
             u[4 * k + 1] = t.y;
             u[4 * k + 2] = t.z;
             u[4 * k + 3] = t.w;
             if (PUSH) {
-                const float4 f = reinterpret_cast<const float4 *>(pvv)[k];
+                const float4 f =
+                    STAGED ? reinterpret_cast<const float4 *>(pvv)[k] : __ldcs(reinterpret_cast<const float4 *>(pvv) + k);
                 v[4 * k] = f.x;
                 v[4 * k + 1] = f.y;
                 v[4 * k + 2] = f.z;
                 v[4 * k + 3] = f.w;
             }
             if (PER_Q) {
-                const int4 c = reinterpret_cast<const int4 *>(pqq)[k];
+                const int4 c = STAGED ? reinterpret_cast<const int4 *>(pqq)[k] : __ldcs(reinterpret_cast<const int4 *>(pqq) + k);
                 q[4 * k] = c.x;
                 q[4 * k + 1] = c.y;
                 q[4 * k + 2] = c.z;
@@ -1372,30 +1467,22 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     }
     unsigned rerr = 0, mseg = 0;
     long long ake = 0, ap = 0;  // this lane's KE and P sums (units 2^-ke_u, 2^-p_u)
+    bool first = true;          // the block's first simulation of the launch
+    bool triggered = false;     // the next launch in the stream may start
+    unsigned seen = 0;          // lane 0: the simulation's claim cursor as last seen
+    unsigned done_old = 0;      // thread 0: blocks counted out before this one
+    bool done_early = false;
 
     while (cur >= 0) {
-        // ---- enter simulation cur
-        const SimDev &S = A.sims[cur];
+        // ---- enter simulation cur: its descriptor into shared memory (the
+        // launch's table does not change while it runs)
+        for (int i = tid; i < (int)(sizeof(SimDev) / 4); i += B)
+            reinterpret_cast<unsigned *>(&sh.sim)[i] = reinterpret_cast<const unsigned *>(A.sims + cur)[i];
+        __syncthreads();
+        const SimDev &S = sh.sim;
         const WorkItem *items = S.items;
         const int n_s = A.slot_begin[cur + 1] - A.slot_begin[cur];
-        // a full step leaves a held simulation (set by an earlier launch's
-        // epilogue, so the same for every block of this one) as it is: its
-        // items are all marked claimed, so no block picks it again in this
-        // launch.  An explicit deposit or push still runs.
-        if (PUSH && DEPOSIT && *(volatile unsigned *)&S.sc->hold) {
-            if (tid == 0)
-                atomicAdd(A.cursor + cur, (unsigned)n_s);
-            __syncthreads();  // the block's own pick below sees it taken
-        } else {
         const int nx = S.nx;
-        const bool track_all = S.refine_seg > 0 && S.refine_seg < (1ll << 16);  // refinement below a cell
-        const int src = (int)S.sc->buf;
-        const unsigned *Uin = S.U[src];
-        const float *Vin = S.V[src];
-        unsigned *Uout = S.U[src ^ 1];
-        float *Vout = S.V[src ^ 1];
-        const int32_t *Qh = S.Qh;
-        unsigned *cursor = A.cursor + cur;
         if (DEPOSIT) {
             for (int j = tid; j < nx; j += B) {
                 hist.lo[j] = 0u;
@@ -1407,7 +1494,19 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         if (tid == 0) {
             sh.diff_used = 0;
             sh.taken = 0;
-            sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = sh.maxseg = 0ull;
+            sh.ke[0] = sh.ke[1] = sh.p[0] = sh.p[1] = 0ull;
+        }
+        if (first) {
+            // a launch that may start before the previous one in its stream
+            // has finished waits here: everything below may be its output
+            griddep_wait();
+            first = false;
+        }
+        // one round trip: the hold and buffer words, the kick table and each
+        // warp's first claim
+        if (tid == 0) {
+            sh.hold = *(volatile unsigned *)&S.sc->hold;
+            sh.buf = *(volatile unsigned *)&S.sc->buf;
         }
         if (PUSH) {
             for (int j = tid; j < nx; j += B)
@@ -1415,7 +1514,6 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             if (tid == 0)
                 ek[nx] = S.Ek[0].x;
         }
-        __syncthreads();
 
         // ---- each warp claims runs of consecutive items (guided: a claim is
         // the fraction claim_q of what it saw left, at least claim_min items)
@@ -1424,11 +1522,10 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         // whole run to arrive when it is needed.  With staging, an item's
         // descriptor is copied into shared memory while the item before it is
         // pushed, and its data copies start halfway through that item.
+        unsigned *cursor = A.cursor + cur;
         const float q = A.claim_q;
         const int claim_min = max(1, A.claim_min);
-        unsigned seen = 0, c_old = 0, c_want = 0;  // lane 0: cursor as last seen; claim in flight
-        if (lane == 0)
-            seen = *(volatile unsigned *)cursor;
+        unsigned c_old = 0, c_want = 0;  // lane 0: the claim in flight
         auto claim_issue = [&]() {
             if (lane == 0) {
                 const int left = n_s - (int)min(seen, (unsigned)n_s);
@@ -1444,8 +1541,26 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             a = (int)o;
             n = (int)o < n_s ? min((int)w, n_s - (int)o) : 0;
         };
+        claim_issue();  // before the hold is known: a held simulation drops it
+        __syncthreads();
+
+        // a full step leaves a held simulation (set by an earlier launch's
+        // epilogue, so the same for every block of this one) as it is: its
+        // items are all marked claimed, so no block picks it again in this
+        // launch.  An explicit deposit or push still runs.
+        if (PUSH && DEPOSIT && sh.hold) {
+            if (tid == 0)
+                atomicAdd(cursor, (unsigned)n_s);
+            __syncthreads();  // the block's own pick below sees it taken
+        } else {
+        const bool track_all = S.refine_seg > 0 && S.refine_seg < (1ll << 16);  // refinement below a cell
+        const int src = (int)sh.buf;
+        const unsigned *Uin = S.U[src];
+        const float *Vin = S.V[src];
+        unsigned *Uout = S.U[src ^ 1];
+        float *Vout = S.V[src ^ 1];
+        const int32_t *Qh = S.Qh;
         int a, n;
-        claim_issue();
         claim_take(a, n);
         claim_issue();  // the next run's claim, in flight through this run
         int count = 0;
@@ -1533,6 +1648,12 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         }
         if (lane == 0)
             atomicAdd(&sh.taken, count);
+        if (!triggered) {
+            // this block has no more items to start: the next launch in the
+            // stream may begin (it waits for this one's end before it reads)
+            griddep_launch_dependents();
+            triggered = true;
+        }
 
         // ---- leave: fold the block's mesh and sums into the simulation's,
         // take an item ticket, run the field epilogue if it completes it
@@ -1540,8 +1661,10 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             const Acc128 k2 = acc_warp_sum(Acc128{(unsigned long long)ake, ake >> 63});
             const Acc128 p2 = acc_warp_sum(Acc128{(unsigned long long)ap, ap >> 63});
             if (lane == 0) {
-                atomic_add_i128(sh.ke, (__int128)(((unsigned __int128)(unsigned long long)k2.hi << 64) | k2.lo));
-                atomic_add_i128(sh.p, (__int128)(((unsigned __int128)(unsigned long long)p2.hi << 64) | p2.lo));
+                sh.wke[warp][0] = (long long)k2.lo;
+                sh.wke[warp][1] = k2.hi;
+                sh.wp[warp][0] = (long long)p2.lo;
+                sh.wp[warp][1] = p2.hi;
             }
             ake = 0;
             ap = 0;
@@ -1550,8 +1673,8 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 mseg = max(mseg, __shfl_down_sync(0xffffffffu, mseg, o));
-            if (lane == 0 && mseg)
-                atomicMax(&sh.maxseg, (unsigned long long)mseg);
+            if (lane == 0)
+                sh.wmseg[warp] = mseg;
             mseg = 0;
         }
         __syncthreads();
@@ -1571,10 +1694,32 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
             atomicOr(&S.sc->err, SIC_ERR_TIMEOUT);
         if (tid == 0) {
             SimAccum *ac = S.acc;
-            atomic_add_i128(ac->ke, (__int128)(((unsigned __int128)sh.ke[1] << 64) | sh.ke[0]));
-            atomic_add_i128(ac->p, (__int128)(((unsigned __int128)sh.p[1] << 64) | sh.p[0]));
-            if (sh.maxseg)
-                atomicMax(&ac->maxseg, sh.maxseg);
+            if (PUSH) {
+                // the block's 128-bit sums, added limb by limb
+                Acc128 k{sh.ke[0], (long long)sh.ke[1]}, pm{sh.p[0], (long long)sh.p[1]};
+                for (int w = 0; w < NW; ++w) {
+                    acc_add(k, Acc128{(unsigned long long)sh.wke[w][0], sh.wke[w][1]});
+                    acc_add(pm, Acc128{(unsigned long long)sh.wp[w][0], sh.wp[w][1]});
+                }
+                const unsigned kl[4] = {(unsigned)k.lo, (unsigned)(k.lo >> 32), (unsigned)k.hi,
+                                        (unsigned)((unsigned long long)k.hi >> 32)};
+                const unsigned pl[4] = {(unsigned)pm.lo, (unsigned)(pm.lo >> 32), (unsigned)pm.hi,
+                                        (unsigned)((unsigned long long)pm.hi >> 32)};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (kl[i])
+                        atomicAdd(&ac->ke[i], (unsigned long long)kl[i]);
+                    if (pl[i])
+                        atomicAdd(&ac->p[i], (unsigned long long)pl[i]);
+                }
+            }
+            if (DEPOSIT) {
+                unsigned m = 0;
+                for (int w = 0; w < NW; ++w)
+                    m = max(m, sh.wmseg[w]);
+                if (m)
+                    atomicMax(&ac->maxseg, (unsigned long long)m);
+            }
         }
         __threadfence();
         __syncthreads();
@@ -1588,6 +1733,12 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 const unsigned t = atomicAdd(A.tickets + cur, taken);
                 sh.last = (t + taken == (unsigned)n_s) ? 1 : 0;
             }
+            // a launch of one simulation: this block claims nothing more, so
+            // it counts itself out now and reads the count after the epilogue
+            if (A.n_slots == 1) {
+                done_old = atomicAdd(A.done, 1u);
+                done_early = true;
+            }
         }
         __syncthreads();
         if (sh.last) {
@@ -1599,7 +1750,9 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                     S.sc->buf = (unsigned)(src ^ 1);
                 if (!DEPOSIT) {  // the epilogue did not consume the sums: drop them
                     SimAccum *ac = S.acc;
-                    ac->ke[0] = ac->ke[1] = ac->p[0] = ac->p[1] = ac->maxseg = 0ull;
+                    for (int k = 0; k < 4; ++k)
+                        ac->ke[k] = ac->p[k] = 0ull;
+                    ac->maxseg = 0ull;
                 }
                 A.tickets[cur] = 0u;
             }
@@ -1607,42 +1760,51 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         }  // not held
 
         // ---- next: the simulation with the most unclaimed items, if any
-        int best = -1, most = 0;
-        for (int j = tid; j < A.n_slots; j += B) {
-            const int left = (A.slot_begin[j + 1] - A.slot_begin[j]) - (int)*(volatile unsigned *)(A.cursor + j);
-            if (left > most) {
-                most = left;
-                best = j;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const int m2 = __shfl_down_sync(0xffffffffu, most, o);
-            const int b2 = __shfl_down_sync(0xffffffffu, best, o);
-            if (m2 > most) {
-                most = m2;
-                best = b2;
-            }
-        }
-        if (lane == 0) {
-            sh.pick_n[warp] = most;
-            sh.pick_s[warp] = best;
-        }
-        __syncthreads();
-        most = 0;
+        // (a launch of one simulation has none)
+        int most = 0;
         cur = -1;
-        for (int w = 0; w < NW; ++w)
-            if (sh.pick_n[w] > most) {
-                most = sh.pick_n[w];
-                cur = sh.pick_s[w];
+        if (A.n_slots > 1) {
+            int best = -1;
+            for (int j = tid; j < A.n_slots; j += B) {
+                const int left = (A.slot_begin[j + 1] - A.slot_begin[j]) - (int)*(volatile unsigned *)(A.cursor + j);
+                if (left > most) {
+                    most = left;
+                    best = j;
+                }
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int m2 = __shfl_down_sync(0xffffffffu, most, o);
+                const int b2 = __shfl_down_sync(0xffffffffu, best, o);
+                if (m2 > most) {
+                    most = m2;
+                    best = b2;
+                }
+            }
+            if (lane == 0) {
+                sh.pick_n[warp] = most;
+                sh.pick_s[warp] = best;
+            }
+            __syncthreads();
+            most = 0;
+            for (int w = 0; w < NW; ++w)
+                if (sh.pick_n[w] > most) {
+                    most = sh.pick_n[w];
+                    cur = sh.pick_s[w];
+                }
+            if (cur >= 0)  // its cursor as the search saw it
+                seen = (unsigned)(A.slot_begin[cur + 1] - A.slot_begin[cur] - most);
+        }
         __syncthreads();  // the picks and the epilogue's scratch are free again
     }
 
     // the last block out rewinds the claim cursors for the next launch
     if (tid == 0) {
-        __threadfence();
-        sh.last = (atomicAdd(A.done, 1u) + 1 == gridDim.x) ? 1 : 0;
+        if (!done_early) {
+            __threadfence();
+            done_old = atomicAdd(A.done, 1u);
+        }
+        sh.last = (done_old + 1 == gridDim.x) ? 1 : 0;
     }
     __syncthreads();
     if (sh.last) {
@@ -1674,9 +1836,19 @@ cudaError_t run(const LaunchArgs &a, int grid, cudaStream_t s)
     cudaError_t e = prep<P, D, Q, G, L>(smem);
     if (e != cudaSuccess)
         return e;
-    k_step<P, D, Q, G, L><<<grid, B, smem, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(B);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e2 = cudaLaunchKernelEx(&cfg, k_step<P, D, Q, G, L>, a);
     count_launches(1);
-    return cudaGetLastError();
+    return e2 != cudaSuccess ? e2 : cudaGetLastError();
 }
 
 template <bool P, bool D, bool Q, bool G>
