@@ -1233,7 +1233,9 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
         unsigned cross = 0;
         {
             const int c0 = jn[0];
-            unsigned b0 = 0, b1 = 0, b2 = 0;
+            unsigned b0 = 0, b1 = 0, b2 = 0;  // charges per tracer: charge per bucket
+            unsigned cnt = 0;                 // one charge per sheet: byte k counts the segments in cell c0 + k
+            int nsame = 0;
             bool wide = false;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -1257,24 +1259,44 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
                     }
                     const bool shrt = (ub - u[r] + (1u << 29)) < (1u << 30);
                     const bool same = seg && shrt && jn[r] == jb;
-                    const unsigned qv = (unsigned)(PER_Q ? (segq ? q[r] : q[r] + qb) : qs_sheet);
                     const int d = jn[r] - c0;
-                    b0 += (same && d == 0) ? qv : 0u;
-                    b1 += (same && d == 1) ? qv : 0u;
-                    b2 += (same && d == 2) ? qv : 0u;
-                    wide = wide || (same && (unsigned)d > 2u);
+                    if (PER_Q) {
+                        const unsigned qv = (unsigned)(segq ? q[r] : q[r] + qb);
+                        b0 += (same && d == 0) ? qv : 0u;
+                        b1 += (same && d == 1) ? qv : 0u;
+                        b2 += (same && d == 2) ? qv : 0u;
+                        wide = wide || (same && (unsigned)d > 2u);
+                    } else {
+                        // 2^(8 d), or 0 for d outside [0, 3] (the funnel shift
+                        // clamps its count at 32; a negative d is a huge count)
+                        cnt += same ? __funnelshift_lc(0u, 1u, (unsigned)d << 3) : 0u;
+                        nsame += same ? 1 : 0;
+                    }
                     cross |= (seg && !same) ? (1u << r) : 0u;
                 }
             }
+            // every inside segment of the lane in one of the four bytes (the
+            // bytes cannot carry: each counts at most R)
+            if (!PER_Q)
+                wide = ((cnt * 0x01010101u) >> 24) != (unsigned)nsame;
             if (__builtin_expect(!wide, 1)) {
-                const int j1 = (c0 + 1 == nx) ? 0 : c0 + 1;
-                const int j2 = (j1 + 1 == nx) ? 0 : j1 + 1;
-                if (b0)
-                    hist.add(c0, b0);
-                if (b1)
-                    hist.add(j1, b1);
-                if (b2)
-                    hist.add(j2, b2);
+                // the cells c0 + k (k <= 3) of non-empty buckets are below nx
+                if (PER_Q) {
+                    if (b0)
+                        hist.add(c0, b0);
+                    if (b1)
+                        hist.add(c0 + 1, b1);
+                    if (b2)
+                        hist.add(c0 + 2, b2);
+                } else {
+                    const long long qs = qs_sheet;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const unsigned c = (cnt >> (8 * k)) & 0xffu;
+                        if (c)
+                            hist.add(c0 + k, (long long)c * qs);
+                    }
+                }
             } else {
                 RunAcc acc(hist);
 #pragma unroll
