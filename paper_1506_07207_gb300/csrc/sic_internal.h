@@ -20,8 +20,8 @@
 //   mesh_last     int64  charge of the latest completed deposit.
 //   Ek[nx]        float2 (Ek_j, Ek_{j+1} - Ek_j): the kick per step
 //                        qm E_j dt^2 / L 2^30 at node j and its difference to the
-//                        next node (the step kernel stages Ek_j alone in
-//                        shared memory and forms the same difference).
+//                        next node (the step kernel copies the pairs into
+//                        shared memory).
 //   E64[nx]       double the node field E_j in physical units.
 //   rho64[nx]     double the neutralised density of the latest deposit.
 // Charge unit: a segment between tracers of weights w_i, w_{i+1} carries

@@ -75,22 +75,22 @@ __device__ __forceinline__ float frac_float(unsigned lo)
 }
 
 // gather (linear weighting between nodes j and j+1), kick, drift; j is the
-// cell of the new position on return.  The drift adds the velocity rounded
-// to whole position units (exact integer arithmetic, wrapping modulo 4 box
-// lengths); a step of half a box or more sets bit 30 or 31 of rerr.
-__device__ __forceinline__ void push_one(unsigned &p, float &v, int &j, const float *ek, int nx, float ks,
-                                         int drift, unsigned &rerr)
+// cell of the new position on return.  ek[j] = (Ek_j, Ek_{j+1} - Ek_j).  The
+// drift adds the velocity rounded to whole position units (exact integer
+// arithmetic, wrapping modulo 4 box lengths); vmax keeps the largest |v|, and
+// a step of half a box (2^29 units) or more is an error.
+__device__ __forceinline__ void push_one(unsigned &p, float &v, int &j, const float2 *ek, int nx, float ks,
+                                         int drift, float &vmax)
 {
     const long long c = cell_coord(p, nx);
     j = cell_of(c);
-    const float e0 = ek[j], e1 = ek[j + 1];  // ek[nx] repeats ek[0]
-    const float a = __fmaf_rn(frac_float(frac_of(c)), __fsub_rn(e1, e0), e0);
+    const float2 e = ek[j];
+    const float a = __fmaf_rn(frac_float(frac_of(c)), e.y, e.x);
     const float vn = __fmaf_rn(ks, a, v);
     v = vn;
     if (drift) {
-        const int d = __float2int_rn(vn);
-        rerr |= (unsigned)(d + (1 << 29));
-        p += (unsigned)d;
+        vmax = fmaxf(vmax, fabsf(vn));
+        p += (unsigned)__float2int_rn(vn);
         j = cell_of(cell_coord(p, nx));
     }
 }
@@ -652,11 +652,11 @@ struct Shared {
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
 constexpr int kWarpCuts = 8;  // piecewise-linear particles this many cells long use the whole warp
 
-// shared head, mesh lo/hi [nx], diff [nx + 2], E [nx + 1]; staging starts on a
-// 128-byte boundary (bulk copies need 16)
+// shared head, mesh lo/hi [nx], diff [nx + 2], kick pairs [nx] (float2);
+// staging starts on a 128-byte boundary (bulk copies need 16)
 __host__ __device__ __forceinline__ size_t stage_offset(int nx_max)
 {
-    const size_t end = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)4 * (nx_max + 1);
+    const size_t end = kSharedHead + (size_t)8 * nx_max + (size_t)8 * (nx_max + 2) + (size_t)8 * nx_max;
     return (end + 127) / 128 * 128;
 }
 
@@ -948,7 +948,7 @@ template <bool PUSH, bool DEPOSIT, bool PER_Q, bool FULL, bool STAGED, bool GEN,
 __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__restrict__ Uin,
                                         const float *__restrict__ Vin, unsigned *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
-                                        const float *ek, const Hist &hist, unsigned long long *diff,
+                                        const float2 *ek, const Hist &hist, unsigned long long *diff,
                                         Shared &sh, int nx, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, long long &ake, long long &ap, unsigned &mseg,
                                         const WorkItemPL *pw, int dep, int segq, bool track_all, const MID &mid)
@@ -1041,11 +1041,12 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
 
     float acc_a = 0.f, acc_b = 0.f;
     if (PUSH) {
+        float vmax = 0.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (FULL || r < rn) {
                 const float vo = v[r];
-                push_one(u[r], v[r], jn[r], ek, nx, ks, drift, rerr);
+                push_one(u[r], v[r], jn[r], ek, nx, ks, drift, vmax);
                 const float vn = v[r];
                 if (PER_Q) {
                     const float qq = __int2float_rn(q[r]);
@@ -1057,8 +1058,10 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
                 }
             }
         }
+        if (!(vmax < 536870912.0f))  // a step of half a box or more
+            rerr |= 1u << 30;
         if (has_halo) {
-            unsigned ignore = 0;
+            float ignore = 0.f;
             push_one(hu, hv, hj, ek, nx, ks, drift, ignore);
         }
         if (FULL || rn == R) {
@@ -1105,7 +1108,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
             if (PUSH) {
                 float pv = Vin[ip];
                 int pj;
-                unsigned ignore = 0;
+                float ignore = 0.f;
                 push_one(pu, pv, pj, ek, nx, ks, drift, ignore);
             }
             pu -= pw->prev_shift;
@@ -1117,7 +1120,7 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
             if (PUSH) {
                 float nv = Vin[in2];
                 int nj;
-                unsigned ignore = 0;
+                float ignore = 0.f;
                 push_one(nu2, nv, nj, ek, nx, ks, drift, ignore);
             }
             nu2 += pw->next2_shift;
@@ -1345,18 +1348,33 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
             mseg = max(mseg, (unsigned)min(((unsigned long long)longest * (unsigned)nx4) >> 16, 0xffffffffull));
         }
 
-        // cross-cell segments: compact them into a task list and let every
-        // lane take one in turn; a lane's slot is the count before it, summed
-        // from one ballot per bit of the per-lane counts (0..R) when there are any
+        // cross-cell segments of box particles, at most one per lane (the
+        // usual case): each lane deposits its own
         const int cnt = __popc(cross);
+        const bool boxes = !(GEN && pw != nullptr);
+        if (boxes && !__any_sync(0xffffffffu, cnt > 1)) {
+            if (cross) {
+                const int idx = l0 + __ffs(cross) - 1;
+                const unsigned pa = pts[idx], pb = pts[idx + 1];
+                const long long ua = cell_coord(pa, nx);
+                const long long ub = ua + seg_span(pa, pb, nx4);
+                const int qs = PER_Q ? qpts[idx] + (segq ? 0 : qpts[idx + 1]) : qs_sheet;
+                DirectAdd acc{hist};
+                emit_cross(ua, cell_of(ua), ub, cell_of(cell_coord(pb, nx)), qs, nx, acc, diff, &sh.diff_used, mseg);
+            }
+            cross = 0;
+        }
+        // the others: compact them into a task list and let every lane take
+        // one in turn; a lane's slot is the count before it, summed from one
+        // ballot per bit of the per-lane counts (0..R) when there are any
         unsigned lt;
         asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-        const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);  // tasks of the warp
+        const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(cross));  // tasks of the warp
         int excl = 0;
         if (total) {
 #pragma unroll
             for (int bit = 0; (1 << bit) <= R; ++bit) {
-                const unsigned bb = __ballot_sync(0xffffffffu, (cnt >> bit) & 1);
+                const unsigned bb = __ballot_sync(0xffffffffu, (__popc(cross) >> bit) & 1);
                 excl += __popc(bb & lt) << bit;
             }
         }
@@ -1454,7 +1472,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     hist.lo = reinterpret_cast<unsigned *>(mesh_region);
     hist.hi = hist.lo + nx_max;
     unsigned long long *diff = mesh_region + nx_max;  // nx_max + 2 entries
-    float *ek = reinterpret_cast<float *>(diff + nx_max + 2);
+    float2 *ek = reinterpret_cast<float2 *>(diff + nx_max + 2);
     char *stage_base = reinterpret_cast<char *>(smem) + stage_offset(nx_max);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1532,9 +1550,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         }
         if (PUSH) {
             for (int j = tid; j < nx; j += B)
-                ek[j] = S.Ek[j].x;
-            if (tid == 0)
-                ek[nx] = S.Ek[0].x;
+                ek[j] = S.Ek[j];
         }
 
         // ---- each warp claims runs of consecutive items (guided: a claim is
@@ -1766,7 +1782,7 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
         if (sh.last) {
             __threadfence();
             if (DEPOSIT)
-                field_epilogue(S, A.record, mesh_region, ek, sh);
+                field_epilogue(S, A.record, mesh_region, reinterpret_cast<float *>(ek), sh);
             if (tid == 0) {
                 if (PUSH)
                     S.sc->buf = (unsigned)(src ^ 1);
