@@ -18,9 +18,10 @@ in log2 (``inputs.serving_mix``, seed 0x5EC5).
   p50/p99 latency.
 * ``e2e``: the batched server fed from host arrays (compact horizontal-sheet
   inputs), every request arriving at t = 0, end to end.
-* ``single_sim``: the two-stream configuration (512 x 16384 = 8,388,608
-  segments, Nx = 1024) stepped alone, L2 flushed by a 256 MB read before
-  every timed step.
+* ``single_sim``: the two-stream (512 x 16384 = 8,388,608 segments, Nx
+  1024) and nonlinear Landau (1024 x 4096, Nx 512) configurations stepped
+  alone: graphs of 8 steps with a 256 MB L2 flush before each, and single
+  steps with a flush before each.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -267,31 +268,46 @@ def run_reference(args, rank):
 
 
 def single_sim(torch, Sim, steps, warmup):
-    """Two-stream configuration alone, L2 flushed before each timed step."""
+    """One simulation alone: the two-stream and the nonlinear Landau
+    configurations.  Two timings each: steps as a user runs them (sic_step of
+    8 steps, one CUDA graph, the L2 flushed before every group of 8), and one
+    step per call with the L2 flushed before every step."""
     from paper_1506_07207_gb300 import inputs
-    p = inputs.two_stream_config()
-    stream = torch.cuda.Stream()
-    sim = Sim.from_problem(p, history_len=8, stream=stream.cuda_stream)
+    peak, _ = peaks()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush.fill_(1.0)
-    for _ in range(warmup):
-        sim.sic_step(1)
-    ev = []
-    for _ in range(steps):
-        with torch.cuda.stream(stream):
-            flush.sum()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.sic_step(1)
-        b.record(stream)
-        ev.append((a, b))
-    torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    sim.sic_destroy()
-    avg = statistics.mean(ms) / 1e3
-    return {"workload": "two-stream 512 x 16384 (8,388,608 segments), Nx 1024, L2 flushed per step",
-            "value": p.n_segments / avg, "unit": UNIT, "ms_per_step": avg * 1e3,
-            "achieved_gbs": algo_bytes([p]) / avg / 1e9}
+    out = {}
+    for name, p in (("two_stream", inputs.two_stream_config()), ("landau_nonlinear", inputs.landau_nonlinear())):
+        stream = torch.cuda.Stream()
+        sim = Sim.from_problem(p, history_len=8, stream=stream.cuda_stream)
+        for _ in range(max(warmup, 2)):
+            sim.sic_step(8)
+
+        def timed(k, reps):
+            ev = []
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.sum()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.sic_step(k)
+                b.record(stream)
+                ev.append((a, b))
+            torch.cuda.synchronize()
+            return statistics.mean(a.elapsed_time(b) for a, b in ev) / 1e3 / k
+
+        g8 = timed(8, max(3, steps // 4))
+        one = timed(1, steps)
+        sim.sic_destroy()
+        gbs = algo_bytes([p]) / g8 / 1e9
+        out[name] = {"workload": f"{name.replace('_', ' ')} {p.n_sheets} x {p.n_tracers} "
+                                 f"({p.n_segments:,} segments), Nx {p.nx}, alone",
+                     "value": p.n_segments / g8, "unit": UNIT, "ms_per_step": g8 * 1e3,
+                     "achieved_gbs": gbs, "roofline_frac": gbs / peak,
+                     "ms_per_step_single_launch": one * 1e3,
+                     "timing": "sic_step(8) (one graph of 8 steps) after a 256 MB L2 flush, per step; "
+                               "single launch: sic_step(1) after a flush"}
+    return out
 
 
 def main():
