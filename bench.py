@@ -300,7 +300,7 @@ def single_sim(torch, Sim, steps, warmup):
         one = timed(1, steps)
         sim.sic_destroy()
         gbs = algo_bytes([p]) / g8 / 1e9
-        out[name] = {"workload": f"{name.replace('_', ' ')} {p.n_sheets} x {p.n_tracers} "
+        out[name] = {"workload": f"{name.replace('_', ' ')} {p.n_sheets} x {p.n_tracers // p.n_sheets} "
                                  f"({p.n_segments:,} segments), Nx {p.nx}, alone",
                      "value": p.n_segments / g8, "unit": UNIT, "ms_per_step": g8 * 1e3,
                      "achieved_gbs": gbs, "roofline_frac": gbs / peak,
