@@ -191,6 +191,35 @@ def field_energy(nx, L, E):
     return _load().orc_field_energy(int(nx), float(L), _ptr(_f64(E), ctypes.c_double))
 
 
+def dft(X, k):
+    """X^_k = sum_j X_j exp(-2 pi i j k / nx) of the mesh values X_j, by the
+    definition (the phase reduced exactly: j k mod nx)."""
+    X = _f64(X)
+    nx = X.size
+    j = np.arange(nx, dtype=np.int64)
+    ph = 2.0 * np.pi * ((j * int(k)) % nx) / nx
+    return complex(np.sum(X * np.cos(ph)), -np.sum(X * np.sin(ph)))
+
+
+def spectrum(X):
+    """|X^_k| for k = 0 .. nx/2 (Sec. 3.2 shows the transform of the charge
+    density during the linear growth of the two-stream instability)."""
+    X = _f64(X)
+    return np.array([abs(dft(X, k)) for k in range(X.size // 2 + 1)])
+
+
+def mode_energy(E, L, k):
+    """Field energy in the Fourier mode pair +-k of the node field E (Sec. 3.2,
+    the energy in the excited mode): W_k = dx / nx |E^_k|^2 for 0 < k < nx/2
+    and half that for k = nx/2, so that for a zero-mean field the W_k of
+    k = 1 .. nx/2 add up to W_E = 1/2 sum_j E_j^2 dx (Parseval)."""
+    E = _f64(E)
+    nx = E.size
+    dx = float(L) / nx
+    a2 = abs(dft(E, k)) ** 2
+    return (0.5 if 2 * int(k) == nx else 1.0) * dx / nx * a2
+
+
 def run(nx, L, dt, counts, closed, winding, x, v, w, n_steps, qm=1.0,
         half_step_init=True, record_E=False, order=0):
     """Leapfrog SIC run; returns dict(x, v, E, hist[, E_hist]).

@@ -834,3 +834,42 @@ def test_first_order_run_keeps_charge_and_oscillates():
     t = np.arange(p.n_steps + 1) * p.dt
     w = fits.oscillation_omega(t, fits.mode(r["E_hist"], 1).imag)
     assert abs(w / theory.leapfrog_omega(p.dt) - 1) < 2e-3
+
+
+# ---- Fourier diagnostics (Sec. 3.2: the energy in the excited mode, the
+# transform of the charge density)
+
+@pytest.mark.parametrize("nx", [16, 17, 64])
+def test_spectrum_matches_the_library_fft(nx):
+    rng = np.random.default_rng(nx)
+    X = rng.normal(size=nx)
+    np.testing.assert_allclose(oracle.spectrum(X), np.abs(np.fft.rfft(X)), rtol=1e-12, atol=1e-12)
+    # the sign of the phase: a sine has X^_1 = -i nx / 2
+    j = np.arange(nx)
+    z = oracle.dft(np.sin(2 * np.pi * j / nx), 1)
+    assert abs(z - (-0.5j * nx)) < 1e-10 * nx
+
+
+@pytest.mark.parametrize("nx", [16, 17, 64])
+def test_mode_energies_add_up_to_the_field_energy(nx):
+    rng = np.random.default_rng(100 + nx)
+    E = rng.normal(size=nx)
+    E -= E.mean()
+    L = 3.7
+    total = sum(oracle.mode_energy(E, L, k) for k in range(1, nx // 2 + 1))
+    assert abs(total - oracle.field_energy(nx, L, E)) <= 1e-12 * oracle.field_energy(nx, L, E)
+
+
+def test_single_cosine_mode_energy():
+    nx, L, A, m = 32, 2.0, 0.3, 3
+    j = np.arange(nx)
+    E = A * np.cos(2 * np.pi * m * j / nx + 0.4)
+    # W_E = 1/2 A^2 (L / 2), all of it in mode m
+    assert abs(oracle.mode_energy(E, L, m) - A * A * L / 4) < 1e-14
+    assert abs(oracle.field_energy(nx, L, E) - A * A * L / 4) < 1e-14
+    for k in range(1, nx // 2 + 1):
+        if k != m:
+            assert oracle.mode_energy(E, L, k) < 1e-28
+    # the Nyquist mode alone: E_j = A (-1)^j carries A^2 L / 2
+    En = A * (-1.0) ** j
+    assert abs(oracle.mode_energy(En, L, nx // 2) - A * A * L / 2) < 1e-14
