@@ -148,6 +148,9 @@ typedef struct {
                                           that hold parts of one set of sheets (split over GPUs)
                                           give the same unit so that their integer meshes add up
                                           to the whole one's bit for bit */
+    int32_t mode_k;                    /* Fourier mode whose field energy every step records
+                                          (Sec. 3.2: the energy in the excited mode), read with
+                                          sic_mode_history: 0 = none, else 1 <= mode_k <= nx/2 */
 } sic_config;
 
 /* Diagnostics of the latest completed step (Sec. 3.1: energies and momentum
@@ -320,6 +323,29 @@ int sic_diagnostics(sic_sim *sim, sic_diag *out);
  * min(max_rows, history_len, steps taken) steps, oldest first, into hist_host
  * (room for max_rows rows, max_rows >= 1); the row count goes to *rows. */
 int sic_history(sic_sim *sim, double *hist_host, int32_t max_rows, int32_t *rows);
+
+/*
+ * Field energy in the Fourier mode pair +-k, k = cfg->mode_k (Sec. 3.2: the
+ * energy in the excited mode of the two-stream instability), of the last
+ * min(max_rows, history_len, steps taken) steps, oldest first, one double per
+ * step into out_host (room for max_rows >= 1); the count goes to *rows.  With
+ * E^_k = sum_j E_j exp(-2 pi i j k / nx) of the node field, the value is
+ * W_k = dx / nx |E^_k|^2 (half that for k = nx/2), so that the W_k of
+ * k = 1 .. nx/2 add up to W_E (Parseval).  Row i belongs to the same step as
+ * row i of sic_history.  Computed on the device by the field solve, in FP32
+ * per thread and FP64 across; SIC_EINVAL when mode_k is 0.
+ */
+int sic_mode_history(sic_sim *sim, double *out_host, int32_t max_rows, int32_t *rows);
+
+/*
+ * Fourier amplitudes |X^_k|, k = 0 .. nx/2 (nx/2 + 1 doubles into out_host),
+ * X^_k = sum_j X_j exp(-2 pi i j k / nx), of the latest deposit's neutralised
+ * density (field = 0, the rho_j of sic_deposit; Sec. 3.2 shows this transform
+ * during the linear growth of the two-stream instability) or of its node
+ * field (field = 1, the E_j of sic_field).  FP64 on the device from the exact
+ * charge mesh.  SIC_EINVAL for another field or a null pointer.
+ */
+int sic_spectrum(sic_sim *sim, int32_t field, double *out_host);
 
 /*
  * Copy the tracers back (the sheets of ordered tracers of Sec. 2.2, in the

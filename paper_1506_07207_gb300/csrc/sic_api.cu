@@ -126,6 +126,8 @@ int validate(const sic_config *c, bool need_sheets)
         return SIC_EINVAL;
     if (!is_finite(c->charge_unit) || c->charge_unit < 0)
         return SIC_EINVAL;
+    if (c->mode_k < 0 || c->mode_k > c->nx / 2)
+        return SIC_EINVAL;
     if (need_sheets) {
         if (!c->tracers_per_sheet || !c->sheet_closed)
             return SIC_EINVAL;
@@ -271,6 +273,9 @@ cudaError_t bind_layout(sic_sim *sim, char *b, const SimLayout &L)
                             cudaMemcpyHostToDevice, sim->stream);
     }
     h.hist = (double *)(b + L.oHist);
+    h.mhist = sim->mode_k > 0 ? (double *)(b + L.oMHist) : nullptr;
+    h.spec = (double *)(b + L.oSpec);
+    h.mode_k = sim->mode_k;
     h.sc = (SimScalars *)(b + L.oSc);
     h.n_items = n_items;
     return e;
@@ -287,6 +292,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     sim->qm = cfg->charge_to_mass;
     sim->strict = cfg->strict_segments ? 1 : 0;
     sim->hist_len = cfg->history_len;
+    sim->mode_k = cfg->mode_k;
     sim->half_step_init = cfg->half_step_init ? 1 : 0;
     sim->deposit = cfg->deposit;
     sim->refine_length = cfg->refine_length;
@@ -327,7 +333,7 @@ int setup(sic_sim *sim, const sic_config *cfg)
     const int n_items = (int)sim->items.size();
 
     const int nx = sim->nx;
-    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len, sim->deposit);
+    const SimLayout L = sim_layout(nx, sim->n_alloc, n_items, sim->per_q, sim->hist_len, sim->deposit, sim->mode_k);
     sim->dbytes = L.total;
     CK(cudaMallocAsync(&sim->dmem, L.total, sim->stream));
     char *b = (char *)sim->dmem;
@@ -510,7 +516,7 @@ cudaError_t launch(const Plan &p, Mode mode, float kick_scale, int drift, int re
 }
 
 
-SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int deposit)
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int deposit, int mode_k)
 {
     Layout lay;
     SimLayout L;
@@ -528,6 +534,8 @@ SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int h
     L.oItems = lay.take(sizeof(WorkItem) * (size_t)n_items);
     L.oPL = deposit == SIC_DEPOSIT_LINEAR ? lay.take(sizeof(WorkItemPL) * (size_t)n_items) : 0;
     L.oHist = lay.take(32 * (size_t)hist_len);
+    L.oMHist = mode_k > 0 ? lay.take(8 * (size_t)hist_len) : 0;
+    L.oSpec = lay.take(8 * (size_t)(nx / 2 + 1));
     L.oSc = lay.take(sizeof(SimScalars));
     L.total = lay.off;
     return L;
@@ -881,7 +889,7 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
         }
     }
     const int64_t new_items = work_items(counts.data(), sim->M);
-    const SimLayout L = sim_layout(sim->nx, n_alloc, new_items, true, sim->hist_len, sim->deposit);
+    const SimLayout L = sim_layout(sim->nx, n_alloc, new_items, true, sim->hist_len, sim->deposit, sim->mode_k);
     void *mem = nullptr;
     e = cudaMemcpyAsync(d_base, base.data(), 8 * (size_t)n_items, cudaMemcpyHostToDevice, sim->stream);
     if (e == cudaSuccess)
@@ -921,6 +929,9 @@ int sic_refine(sic_sim *sim, double l_ref, int64_t *n_added)
         e = cudaMemcpyAsync(b + L.oAcc, sim->h.acc, sizeof(SimAccum), cudaMemcpyDeviceToDevice, sim->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + L.oHist, sim->h.hist, 32 * (size_t)sim->hist_len, cudaMemcpyDeviceToDevice,
+                            sim->stream);
+    if (e == cudaSuccess && sim->mode_k > 0)
+        e = cudaMemcpyAsync(b + L.oMHist, sim->h.mhist, 8 * (size_t)sim->hist_len, cudaMemcpyDeviceToDevice,
                             sim->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + L.oSc, sim->h.sc, sizeof(SimScalars), cudaMemcpyDeviceToDevice, sim->stream);
@@ -1338,6 +1349,33 @@ int sic_history(sic_sim *sim, double *hist_host, int32_t max_rows, int32_t *rows
     }
     *rows = (int32_t)n;
     return SIC_OK;
+}
+
+int sic_mode_history(sic_sim *sim, double *out_host, int32_t max_rows, int32_t *rows)
+{
+    if (!sim || !out_host || !rows || max_rows < 1 || sim->mode_k <= 0)
+        return SIC_EINVAL;
+    SimScalars sc;
+    int rc = check_device_errors(sim, &sc);
+    if (rc)
+        return rc;
+    const int64_t n = std::min<int64_t>(std::min<int64_t>(sc.step, sim->hist_len), max_rows);
+    std::vector<double> ring((size_t)sim->hist_len);
+    CK(cudaMemcpy(ring.data(), sim->h.mhist, 8 * ring.size(), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i)
+        out_host[i] = ring[(size_t)((sc.step - n + i) % sim->hist_len)];
+    *rows = (int32_t)n;
+    return SIC_OK;
+}
+
+int sic_spectrum(sic_sim *sim, int32_t field, double *out_host)
+{
+    if (!sim || !out_host || (field != 0 && field != 1))
+        return SIC_EINVAL;
+    CK(launch_field_out(sim->h, sim->stream));
+    CK(launch_spectrum(sim->h, field, sim->stream));
+    CK(cudaMemcpyAsync(out_host, sim->h.spec, 8 * (size_t)(sim->nx / 2 + 1), cudaMemcpyDeviceToHost, sim->stream));
+    return check_device_errors(sim);
 }
 
 int sic_get_state(sic_sim *sim, double *x_host, double *v_host)

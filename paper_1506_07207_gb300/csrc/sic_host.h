@@ -22,9 +22,9 @@ struct Plan {
 
 // Device bytes of one simulation's allocation (state, meshes, items, ...).
 struct SimLayout {
-    size_t oU0, oU1, oV0, oV1, oQ, oMesh, oLast, oEk, oE64, oRho, oAcc, oItems, oPL, oHist, oSc, total;
+    size_t oU0, oU1, oV0, oV1, oQ, oMesh, oLast, oEk, oE64, oRho, oAcc, oItems, oPL, oHist, oMHist, oSpec, oSc, total;
 };
-SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int deposit);
+SimLayout sim_layout(int nx, int64_t n_alloc, int64_t n_items, bool per_q, int hist_len, int deposit, int mode_k);
 
 // Tracer slots (sheets padded to SIC_ALIGN_TRACERS) and work items of M
 // sheets of n tracers each.
@@ -40,6 +40,7 @@ struct sic_sim {
     int nx = 0;
     double L = 0, dt = 0, dx = 0, qm = 1;
     int strict = 0, hist_len = 1, half_step_init = 0;
+    int mode_k = 0;                   // Fourier mode of the per-step mode-energy history, 0 = none
     bool per_q = false;
     int M = 0;
     std::vector<int32_t> counts;

@@ -114,6 +114,7 @@ struct SimScalars {
     uint32_t buf;       // which state buffer is current
     uint32_t hold;      // SIC_HOLD_* bits: while nonzero, steps leave the simulation as it is
     uint32_t pad;
+    double wk;          // field energy of Fourier mode mode_k of the current field (when recorded)
 };
 
 struct SimDev {
@@ -150,6 +151,10 @@ struct SimDev {
     int32_t pad1;
     long long refine_seg;       // hold for refinement once the longest segment crossing a
                                 // cell edge exceeds this (2^-16 cells); 0: never
+    double *mhist;              // [hist_len] field energy of Fourier mode mode_k per step, or null
+    double *spec;               // [nx / 2 + 1] Fourier amplitudes (sic_spectrum)
+    int32_t mode_k;             // 0: no mode history
+    int32_t pad2;
 };
 
 // Everything one launch of the step kernel needs.
@@ -179,6 +184,7 @@ namespace sic {
 enum Mode { MODE_STEP = 0, MODE_DEPOSIT = 1, MODE_PUSH = 2 };
 cudaError_t launch_step_kernel(const LaunchArgs &a, int grid, Mode mode, bool per_q, cudaStream_t s);
 cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s);
+cudaError_t launch_spectrum(const SimDev &sim, int field, cudaStream_t s);
 cudaError_t launch_refine_count(const SimDev &sim, long long lfix, int32_t *splits, cudaStream_t s);
 cudaError_t launch_refine_scatter(const SimDev &sim, long long lfix, const int64_t *out_base, uint32_t *U2, float *V2,
                                   int32_t *Q2, cudaStream_t s);

@@ -645,8 +645,9 @@ struct Shared {
     // limbs (ke 0-3, p 4-7), the longest segment (8), and the scalars
     unsigned long long pre[9];
     long long pre_step;
-    double pre_we;
+    double pre_we, pre_wk;
     unsigned pre_err, pre_hold;
+    float mre[NW], mim[NW];  // each warp's part of the Fourier mode sum
 };
 
 constexpr size_t kSharedHead = (sizeof(Shared) + 15) / 16 * 16;
@@ -731,6 +732,17 @@ __device__ __forceinline__ double times_pow2(double x, int k)
     return x * __hiloint2double((1023 + k) << 20, 0);
 }
 
+// One term of the Fourier sum sum_j y_j exp(-2 pi i j k / nx) (Sec. 3.2: the
+// energy in the excited mode), the phase reduced exactly to j k mod nx.
+__device__ __noinline__ void mode_add(float y, int j, int k, int nx, float &re, float &im)
+{
+    const int idx = (int)(((long long)j * k) % nx);
+    float sn, cs;
+    sincospif(__fdiv_rn(__int2float_rn(2 * idx), __int2float_rn(nx)), &sn, &cs);
+    re = __fmaf_rn(y, cs, re);
+    im = __fmaf_rn(-y, sn, im);
+}
+
 // Field solve of one simulation (Sec. 2.1 with C = 1) by the block holding
 // its last ticket: sm (nx u64) and sE (nx floats) are this block's scratch.
 //   P_j = sum_{i<j} mesh_i, D_j = nx P_j - j Q (= nx sigma E'_j exactly),
@@ -758,6 +770,8 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         sh.pre_err = __ldcg(&S.sc->err);
     } else if (tid == 67) {
         sh.pre_hold = __ldcg(&S.sc->hold);
+    } else if (tid == 68) {
+        sh.pre_wk = __ldcg(&S.sc->wk);
     }
     for (int j = tid; j < nx; j += 4 * B) {
         unsigned long long mv[4];
@@ -814,6 +828,8 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
 
     // K from cell to cell: D_{j+1} = D_j + nx mesh_j - Q
     float wloc = 0.f;
+    const int mode_k = S.mode_k;
+    float mre = 0.f, mim = 0.f;  // this thread's part of sum_j K_j 2^-60 exp(-2 pi i j k / nx)
     __int128 D = (__int128)nx * run0 - (__int128)j0 * qtot;
     __int128 K = (__int128)nx * D - sumD;
     if (S.deposit == SIC_DEPOSIT_FIRST) {
@@ -827,6 +843,8 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
             sE[j] = __fmul_rn(norm_to_float(n2, S.ek_exp - 1), S.ek_mant);
             const float kn = norm_to_float(n2, -61);
             wloc = __fmaf_rn(kn, kn, wloc);
+            if (mode_k)
+                mode_add(kn, j, mode_k, nx, mre, mim);
             K = Kn;
         }
     } else {
@@ -836,6 +854,8 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
             sE[j] = __fmul_rn(norm_to_float(nk, S.ek_exp), S.ek_mant);
             const float kn = norm_to_float(nk, -60);
             wloc = __fmaf_rn(kn, kn, wloc);
+            if (mode_k)
+                mode_add(kn, j, mode_k, nx, mre, mim);
             D += (__int128)nx * (long long)sm[j] - qtot;
             K = (__int128)nx * D - sumD;
         }
@@ -845,6 +865,17 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         wloc = __fadd_rn(wloc, __shfl_down_sync(0xffffffffu, wloc, o));
     if (lane == 0)
         sh.da[warp] = (double)wloc;
+    if (mode_k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mre = __fadd_rn(mre, __shfl_down_sync(0xffffffffu, mre, o));
+            mim = __fadd_rn(mim, __shfl_down_sync(0xffffffffu, mim, o));
+        }
+        if (lane == 0) {
+            sh.mre[warp] = mre;
+            sh.mim[warp] = mim;
+        }
+    }
     __syncthreads();
     for (int j = tid; j < nx; j += B) {
         const int j1n = (j + 1 == nx) ? 0 : j + 1;
@@ -854,8 +885,11 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
     SimScalars *sc = S.sc;
     const long long step = sh.pre_step;
     double *row = nullptr;
-    if (record && (tid == 0 || tid == 32 || tid == 64))
-        row = S.hist + 4 * (step % S.hist_len);
+    long long slot = 0;
+    if (record && (tid == 0 || tid == 32 || tid == 64 || tid == 128)) {
+        slot = step % S.hist_len;
+        row = S.hist + 4 * slot;
+    }
     auto limbs = [](const unsigned long long *l) -> double {
         const unsigned __int128 u = (unsigned __int128)l[0] + ((unsigned __int128)l[1] << 32) +
                                     ((unsigned __int128)l[2] << 64) + ((unsigned __int128)l[3] << 96);
@@ -870,6 +904,17 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
         for (int i = 0; i < NW; ++i)
             w += sh.da[i];
         sc->we = w * S.we_scale;
+    }
+    if (tid == 128 && mode_k) {
+        // W_k = dx / nx |E^_k|^2 (half at k = nx/2) = (2 or 1) / nx we_scale |Z|^2
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < NW; ++i) {
+            re += (double)sh.mre[i];
+            im += (double)sh.mim[i];
+        }
+        if (record)
+            S.mhist[slot] = sh.pre_wk;
+        sc->wk = (2 * mode_k == nx ? 1.0 : 2.0) / nx * S.we_scale * (re * re + im * im);
     }
     if (tid == 0) {
         SimAccum *ac = S.acc;
@@ -1919,6 +1964,44 @@ int occ_pd(int nx_max, bool per_q)
 
 // The double-precision node field E_j and density rho_j of the latest
 // deposit, recomputed from its exact charge mesh (one block of 1024 threads).
+// Fourier amplitudes |X^_k| = |sum_j X_j exp(-2 pi i j k / nx)| of the FP64
+// density (field 0) or node field (field 1) that k_field_out wrote, one block
+// per k = 0 .. nx/2, in a fixed order of additions (Sec. 3.2).
+__global__ void __launch_bounds__(256) k_spectrum(const SimDev S, int field)
+{
+    __shared__ double s_re[8], s_im[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = S.nx, k = blockIdx.x;
+    const double *X = field ? S.E64 : S.rho64;
+    double re = 0.0, im = 0.0;
+    for (int j = tid; j < nx; j += 256) {
+        const int idx = (int)(((long long)j * k) % nx);
+        double sn, cs;
+        sincospi(2.0 * idx / nx, &sn, &cs);
+        re = fma(X[j], cs, re);
+        im = fma(-X[j], sn, im);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        s_re[warp] = re;
+        s_im[warp] = im;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        re = 0.0;
+        im = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            re += s_re[w];
+            im += s_im[w];
+        }
+        S.spec[k] = hypot(re, im);
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_field_out(const SimDev S)
 {
     constexpr int BB = 1024, NWW = BB / 32;
@@ -2070,6 +2153,13 @@ int step_blocks_per_sm(int nx_max, Mode mode, bool per_q)
 cudaError_t launch_field_out(const SimDev &sim, cudaStream_t s)
 {
     k_field_out<<<1, 1024, 0, s>>>(sim);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const SimDev &sim, int field, cudaStream_t s)
+{
+    k_spectrum<<<sim.nx / 2 + 1, 256, 0, s>>>(sim, field);
     count_launches(1);
     return cudaGetLastError();
 }

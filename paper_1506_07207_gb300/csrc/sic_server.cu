@@ -92,7 +92,8 @@ size_t request_bytes(const sic_config &cfg, const int32_t *counts, int M, bool p
 {
     const int64_t n_alloc = sic_host::padded_tracers(counts, M);
     const int64_t n_items = sic_host::work_items(counts, M);
-    return sic_host::sim_layout(cfg.nx, n_alloc, n_items, per_q, std::max(1, cfg.history_len), cfg.deposit).total;
+    return sic_host::sim_layout(cfg.nx, n_alloc, n_items, per_q, std::max(1, cfg.history_len), cfg.deposit,
+                               cfg.mode_k).total;
 }
 
 int make_sim(sic_server *s, Request &r, sic_sim **out)

@@ -34,7 +34,7 @@ EXPORTS = [
     "sic_server_create", "sic_server_submit", "sic_server_submit_horizontal", "sic_server_tick",
     "sic_server_results", "sic_server_clock", "sic_server_stats", "sic_server_destroy",
     "sic_step_batch_static", "sic_moments", "sic_refine", "sic_sheet_counts", "sic_batch_autotune",
-    "sic_run",
+    "sic_run", "sic_mode_history", "sic_spectrum",
 ]
 
 
@@ -57,6 +57,7 @@ class sic_config(ctypes.Structure):
         ("refine_split", ctypes.c_double),
         ("max_tracers", ctypes.c_int64),
         ("charge_unit", ctypes.c_double),
+        ("mode_k", ctypes.c_int32),
     ]
 
 
@@ -141,6 +142,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sic_sheet_counts": ([simp, ip], ctypes.c_int),
         "sic_diagnostics": ([simp, P(sic_diag)], ctypes.c_int),
         "sic_history": ([simp, dp, ctypes.c_int32, ip], ctypes.c_int),
+        "sic_mode_history": ([simp, dp, ctypes.c_int32, ip], ctypes.c_int),
+        "sic_spectrum": ([simp, ctypes.c_int32, dp], ctypes.c_int),
         "sic_get_state": ([simp, dp, dp], ctypes.c_int),
         "sic_device_state": ([simp, P(vp), P(vp), P(vp)], ctypes.c_int),
         "sic_sync": ([simp], ctypes.c_int),
@@ -197,7 +200,7 @@ def sic_launch_count() -> int:
 
 def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
             half_step_init=True, strict=False, history_len=1, stream=None, order=0, refine=0.0,
-            refine_split=0.0, max_tracers=0, charge_unit=0.0):
+            refine_split=0.0, max_tracers=0, charge_unit=0.0, mode_k=0):
     cfg = sic_config()
     cfg.nx = int(nx)
     cfg.box_length = float(L)
@@ -222,6 +225,7 @@ def _config(nx, L, dt, n_sheets, counts=None, closed=None, winding=None, qm=1.0,
     cfg.refine_split = float(refine_split) if refine else 0.0
     cfg.max_tracers = int(max_tracers)
     cfg.charge_unit = float(charge_unit)
+    cfg.mode_k = int(mode_k)
     return cfg, keep
 
 
@@ -238,10 +242,11 @@ class Sim:
     @classmethod
     def sic_create(cls, nx, L, dt, counts, closed, winding, x, v, w, qm=1.0, half_step_init=True,
                    strict=False, history_len=1, stream=None, order=0, refine=0.0, refine_split=0.0,
-                   max_tracers=0, charge_unit=0.0):
+                   max_tracers=0, charge_unit=0.0, mode_k=0):
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         cfg, keep = _config(nx, L, dt, counts.size, counts, closed, winding, qm, half_step_init,
-                            strict, history_len, stream, order, refine, refine_split, max_tracers, charge_unit)
+                            strict, history_len, stream, order, refine, refine_split, max_tracers, charge_unit,
+                            mode_k)
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -256,14 +261,14 @@ class Sim:
     @classmethod
     def sic_create_horizontal(cls, nx, L, dt, x_template, v_sheet, w_sheet, qm=1.0,
                               half_step_init=True, strict=False, history_len=1, stream=None, order=0,
-                              refine=0.0, refine_split=0.0, max_tracers=0):
+                              refine=0.0, refine_split=0.0, max_tracers=0, mode_k=0):
         xt = np.ascontiguousarray(x_template, dtype=np.float64)
         vs = np.ascontiguousarray(v_sheet, dtype=np.float64)
         ws = np.ascontiguousarray(w_sheet, dtype=np.float64)
         if vs.shape != ws.shape:
             raise ValueError("v_sheet and w_sheet need one entry per sheet")
         cfg, keep = _config(nx, L, dt, vs.size, None, None, None, qm, half_step_init, strict,
-                            history_len, stream, order, refine, refine_split, max_tracers)
+                            history_len, stream, order, refine, refine_split, max_tracers, 0.0, mode_k)
         h = ctypes.c_void_p()
         _check(_lib.sic_create_horizontal(ctypes.byref(cfg), xt.size, _dptr(xt), _dptr(vs), _dptr(ws),
                                           ctypes.byref(h)), "sic_create_horizontal")
@@ -271,11 +276,12 @@ class Sim:
 
     @classmethod
     def from_problem(cls, p, history_len=None, strict=False, stream=None, horizontal=None, order=0,
-                     refine=None):
+                     refine=None, mode_k=0):
         """Create from an ``inputs.Problem`` (compact form when it has one); order
         is the deposit (SIC_DEPOSIT_*): 0 box particles, 1 piecewise linear
         (Sec. 2.5), 2 and 3 PIC nearest grid point and cloud in cell; refine is
-        the refinement length (default: the problem's own)."""
+        the refinement length (default: the problem's own); mode_k the Fourier
+        mode whose field energy every step records (0: none)."""
         hl = history_len if history_len is not None else max(1, p.n_steps)
         if refine is None:
             refine = p.refine_length if order in (0, 1, 4) else 0.0
@@ -286,11 +292,11 @@ class Sim:
             return cls.sic_create_horizontal(p.nx, p.L, p.dt, p.x_template, p.v_sheet, p.w_sheet,
                                              qm=p.qm, half_step_init=p.half_step_init, strict=strict,
                                              history_len=hl, stream=stream, order=order, refine=refine,
-                                             refine_split=split, max_tracers=p.max_tracers)
+                                             refine_split=split, max_tracers=p.max_tracers, mode_k=mode_k)
         return cls.sic_create(p.nx, p.L, p.dt, p.counts, p.closed, p.winding, p.x, p.v, p.w,
                               qm=p.qm, half_step_init=p.half_step_init, strict=strict,
                               history_len=hl, stream=stream, order=order, refine=refine, refine_split=split,
-                              max_tracers=p.max_tracers)
+                              max_tracers=p.max_tracers, mode_k=mode_k)
 
     # -- the C ABI, one method per entry point ------------------------------
     @property
@@ -363,6 +369,21 @@ class Sim:
         rows = ctypes.c_int32()
         _check(_lib.sic_history(self.handle, _dptr(buf), buf.shape[0], ctypes.byref(rows)), "sic_history")
         return buf[: rows.value]
+
+    def sic_mode_history(self, history_len: int):
+        """The last min(history_len, ring length, steps) values of the field
+        energy in Fourier mode mode_k (Sec. 3.2), one per history row."""
+        buf = np.zeros(max(1, int(history_len)), dtype=np.float64)
+        rows = ctypes.c_int32()
+        _check(_lib.sic_mode_history(self.handle, _dptr(buf), buf.size, ctypes.byref(rows)), "sic_mode_history")
+        return buf[: rows.value]
+
+    def sic_spectrum(self, field=0):
+        """|X^_k|, k = 0 .. nx/2, of the latest deposit's density (field 0) or
+        node field (field 1)."""
+        out = np.zeros(self.nx // 2 + 1, dtype=np.float64)
+        _check(_lib.sic_spectrum(self.handle, int(field), _dptr(out)), "sic_spectrum")
+        return out
 
     def sic_get_state(self):
         x = np.zeros(self.n_tracers, dtype=np.float64)
