@@ -8,7 +8,11 @@
 // mode is the one-simulation-per-launch baseline: one request at a time, run
 // to completion with sic_step.  A simulation gives the same bits alone and in
 // any batch, because every per-simulation result is an integer sum or a
-// fixed-order reduction.  A request with a refinement length (Sec. 2.6) holds
+// fixed-order reduction.  The batched mode overlaps its host work with the
+// GPU: a tick collects the chunk in flight, launches the next one, and only
+// then retires finished requests and creates newly admitted ones, on a side
+// stream; those join the launches from the next tick on.  A request with a
+// refinement length (Sec. 2.6) holds
 // after the step that leaves a particle longer than it; the server then
 // refines it (its device memory grows) and it goes on in the next chunk, so it
 // is refined at the same steps alone and in the mix.
@@ -60,8 +64,12 @@ struct sic_server {
     sic_server_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;            // creation and retirement, beside the steps
     std::deque<Request> queue;
     std::vector<Active> active;
+    std::vector<Active> fresh;              // created on the side stream, stepping from the next tick
+    bool inflight = false;                  // a chunk of steps is launched and not yet collected
+    int launch_rc = SIC_OK;                 // a launch of that chunk failed
     std::vector<sic_result> done;
     int64_t next_id = 1;
     size_t used = 0, peak = 0;
@@ -96,10 +104,10 @@ size_t request_bytes(const sic_config &cfg, const int32_t *counts, int M, bool p
                                cfg.mode_k).total;
 }
 
-int make_sim(sic_server *s, Request &r, sic_sim **out)
+int make_sim(Request &r, cudaStream_t stream, sic_sim **out)
 {
     sic_config cfg = r.cfg;
-    cfg.stream = s->stream;
+    cfg.stream = stream;
     cfg.history_len = std::max(1, cfg.history_len);
     if (r.horizontal)
         return sic_create_horizontal(&cfg, r.n_template, r.a.data(), r.b.data(), r.c.data(), out);
@@ -133,7 +141,7 @@ void finish(sic_server *s, Active &a, int status, double t_done)
             // the caller owns it now: it gets a stream of its own, since the
             // server's may be destroyed with the server
             cudaStream_t own = nullptr;
-            if (cudaStreamSynchronize(s->stream) == cudaSuccess &&
+            if (cudaStreamSynchronize(a.sim->stream) == cudaSuccess &&
                 cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) == cudaSuccess) {
                 a.sim->stream = own;
                 a.sim->own_stream = true;
@@ -156,13 +164,20 @@ void finish(sic_server *s, Active &a, int status, double t_done)
 // refinement that follows) and refine it if it holds for that; its device
 // memory may grow.  sc: its scalars, read after its steps.  Returns a SIC_E*
 // code.
-int look(sic_server *srv, Active &a, const SimScalars &sc)
+// With `defer` set, a simulation that holds for refinement is not refined:
+// *defer is left true for it (false otherwise) and the caller refines it.
+int look(sic_server *srv, Active &a, const SimScalars &sc, bool *defer = nullptr)
 {
     int st = sic_host::scalars_status(sc);
     a.segment_updates += (sc.step - a.steps_seen) * sic_host::segments(a.sim);
     a.steps_seen = sc.step;
     a.left = a.req.n_steps - (int32_t)sc.step;
-    if (st == SIC_OK && (sc.hold & SIC_HOLD_REFINE) && a.left > 0) {
+    const bool wants = st == SIC_OK && (sc.hold & SIC_HOLD_REFINE) && a.left > 0;
+    if (defer) {
+        *defer = wants;
+        return st;
+    }
+    if (wants) {
         srv->refinements += 1;
         const size_t before = a.sim->dbytes;
         st = sic_host::refine_held(a.sim, nullptr);
@@ -192,6 +207,174 @@ int read_all(sic_server *srv)
                             srv->stream) != cudaSuccess)
             return SIC_ECUDA;
     return cudaStreamSynchronize(srv->stream) == cudaSuccess ? SIC_OK : SIC_ECUDA;
+}
+
+// Admit queued requests in arrival order while a slot is free and the memory
+// fits, creating each on `stream` into `into`.
+void admit(sic_server *srv, cudaStream_t stream, std::vector<Active> &into)
+{
+    while (!srv->queue.empty()) {
+        Request &r = srv->queue.front();
+        if ((int64_t)r.bytes > srv->cfg.hbm_budget) {
+            Active a;
+            a.req = std::move(r);
+            srv->queue.pop_front();
+            finish(srv, a, SIC_EBUSY, srv->now());
+            continue;
+        }
+        if ((int)(srv->active.size() + srv->fresh.size()) >= srv->cfg.max_active) {
+            srv->waits_slots += 1;
+            break;
+        }
+        if ((int64_t)(srv->used + r.bytes) > srv->cfg.hbm_budget) {
+            srv->waits_memory += 1;
+            break;
+        }
+        Active a;
+        a.t_admit = srv->now();
+        const int rc = make_sim(r, stream, &a.sim);
+        if (rc == SIC_ENOMEM && !(srv->active.empty() && srv->fresh.empty()))
+            break;  // wait for memory to come free
+        a.req = std::move(r);
+        srv->queue.pop_front();
+        if (rc != SIC_OK) {
+            a.sim = nullptr;
+            finish(srv, a, rc, srv->now());
+            continue;
+        }
+        a.left = a.req.n_steps;
+        srv->used += a.sim->dbytes;
+        srv->peak = std::max(srv->peak, srv->used);
+        into.push_back(std::move(a));
+        srv->plan_valid = false;
+    }
+}
+
+// One tick of the batched mode: collect the chunk in flight, let the newly
+// created simulations join, launch the next chunk, and while it runs retire
+// the finished requests and create the newly admitted ones on the side
+// stream.
+int tick_batched(sic_server *srv)
+{
+    int rc = SIC_OK;
+    std::vector<Active> retired, to_refine;
+    std::vector<int> rstatus;
+    if (srv->inflight) {
+        srv->inflight = false;
+        rc = srv->launch_rc;
+        srv->launch_rc = SIC_OK;
+        if (cudaStreamSynchronize(srv->stream) != cudaSuccess)
+            rc = SIC_ECUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, srv->ev[0], srv->ev[1]) == cudaSuccess)
+            srv->busy_s += 1e-3 * ms;
+        // each simulation's own step count (a held one took fewer than the
+        // chunk); one that holds for refinement (Sec. 2.6) is refined here,
+        // its device memory growing, and goes on in the next chunk
+        std::vector<int> status(srv->active.size(), SIC_OK);
+        std::vector<char> held(srv->active.size(), 0);
+        if (rc == SIC_OK) {
+            rc = read_all(srv);
+            if (rc == SIC_OK)
+                for (size_t i = 0; i < srv->active.size(); ++i) {
+                    bool h = false;
+                    status[i] = look(srv, srv->active[i], srv->scal[i], &h);
+                    held[i] = h;
+                }
+        }
+        std::vector<Active> keep;
+        for (size_t i = 0; i < srv->active.size(); ++i) {
+            Active &a = srv->active[i];
+            const int st = rc != SIC_OK ? rc : status[i];
+            if (a.left <= 0 || st != SIC_OK) {
+                retired.push_back(std::move(a));
+                rstatus.push_back(st);
+            } else if (held[i]) {
+                to_refine.push_back(std::move(a));  // refined beside the next chunk
+            } else {
+                keep.push_back(std::move(a));
+            }
+        }
+        if (keep.size() != srv->active.size())
+            srv->plan_valid = false;
+        srv->active.swap(keep);
+        if (rc != SIC_OK)
+            drop_plans(srv);
+    }
+    // the simulations created while the last chunk ran join it
+    if (!srv->fresh.empty()) {
+        const bool ok = cudaStreamSynchronize(srv->side) == cudaSuccess;
+        for (Active &a : srv->fresh) {
+            if (ok) {
+                a.sim->stream = srv->stream;
+                srv->active.push_back(std::move(a));
+            } else {
+                retired.push_back(std::move(a));
+                rstatus.push_back(SIC_ECUDA);
+            }
+        }
+        srv->fresh.clear();
+        srv->plan_valid = false;
+    }
+    // the next chunk: k = min(chunk_steps, steps left of any active request)
+    if (!srv->active.empty()) {
+        int32_t k = srv->cfg.chunk_steps;
+        for (const Active &a : srv->active)
+            k = std::min(k, std::max(a.left, 0));
+        int lrc = SIC_OK;
+        if (k > 0 && !srv->plan_valid) {
+            drop_plans(srv);
+            std::vector<sic_sim *> grp[2];
+            for (const Active &a : srv->active)
+                grp[a.sim->per_q ? 1 : 0].push_back(a.sim);
+            for (int g = 0; g < 2 && lrc == SIC_OK; ++g)
+                if (!grp[g].empty() &&
+                    sic_host::build_plan(srv->plan[g], grp[g].data(), (int)grp[g].size(), srv->stream) != cudaSuccess)
+                    lrc = SIC_ECUDA;
+            srv->plan_valid = (lrc == SIC_OK);
+        }
+        if (k > 0 && lrc != SIC_OK) {
+            srv->inflight = true;  // nothing launched: the next tick retires them with the error
+            srv->launch_rc = lrc;
+            cudaEventRecord(srv->ev[0], srv->stream);
+            cudaEventRecord(srv->ev[1], srv->stream);
+        } else if (k > 0) {
+            cudaEventRecord(srv->ev[0], srv->stream);
+            for (int32_t st = 0; st < k && lrc == SIC_OK; ++st)
+                for (int g = 0; g < 2 && lrc == SIC_OK; ++g)
+                    if (srv->plan[g].mem &&
+                        sic_host::launch(srv->plan[g], sic::MODE_STEP, 1.0f, 1, 1, srv->stream) != cudaSuccess)
+                        lrc = SIC_ECUDA;
+            cudaEventRecord(srv->ev[1], srv->stream);
+            srv->inflight = true;  // collected by the next tick
+            srv->launch_rc = lrc;
+        }
+    }
+    // while it runs: refine the held simulations on the side stream (they are
+    // not in the chunk; they join again from the next tick), retire the
+    // finished ones there too (their steps are done), then admit
+    for (Active &a : to_refine) {
+        a.sim->stream = srv->side;
+        srv->refinements += 1;
+        const size_t before = a.sim->dbytes;
+        const int st = sic_host::refine_held(a.sim, nullptr);
+        srv->used += a.sim->dbytes - before;
+        srv->peak = std::max(srv->peak, srv->used);
+        if (st == SIC_OK) {
+            srv->fresh.push_back(std::move(a));
+        } else {
+            retired.push_back(std::move(a));
+            rstatus.push_back(st);
+        }
+    }
+    const double t = srv->now();
+    for (size_t i = 0; i < retired.size(); ++i) {
+        if (retired[i].sim)
+            retired[i].sim->stream = srv->side;
+        finish(srv, retired[i], rstatus[i], t);
+    }
+    admit(srv, srv->side, srv->fresh);
+    return SIC_OK;
 }
 
 int queue_request(sic_server *srv, Request &&r, int64_t *id)
@@ -226,9 +409,11 @@ int sic_server_create(const sic_server_config *cfg, sic_server **out)
     } else {
         s->own_stream = true;
     }
-    if (cudaEventCreate(&s->ev[0]) != cudaSuccess || cudaEventCreate(&s->ev[1]) != cudaSuccess) {
-        if (s->ev[0])
-            cudaEventDestroy(s->ev[0]);
+    if (cudaEventCreate(&s->ev[0]) != cudaSuccess || cudaEventCreate(&s->ev[1]) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) {
+        for (cudaEvent_t e : s->ev)
+            if (e)
+                cudaEventDestroy(e);
         if (s->own_stream)
             cudaStreamDestroy(s->stream);
         delete s;
@@ -311,114 +496,34 @@ int sic_server_tick(sic_server *srv, int32_t *pending)
     if (!srv)
         return SIC_EINVAL;
     srv->ticks += 1;
-    // admit in arrival order while a slot is free and the memory fits
-    while (!srv->queue.empty()) {
-        Request &r = srv->queue.front();
-        if ((int64_t)r.bytes > srv->cfg.hbm_budget) {
-            Active a;
-            a.req = std::move(r);
-            srv->queue.pop_front();
-            finish(srv, a, SIC_EBUSY, srv->now());
-            continue;
-        }
-        if ((int)srv->active.size() >= srv->cfg.max_active) {
-            srv->waits_slots += 1;
-            break;
-        }
-        if ((int64_t)(srv->used + r.bytes) > srv->cfg.hbm_budget) {
-            srv->waits_memory += 1;
-            break;
-        }
-        Active a;
-        a.t_admit = srv->now();
-        const int rc = make_sim(srv, r, &a.sim);
-        if (rc == SIC_ENOMEM && !srv->active.empty())
-            break;  // wait for memory to come free
-        a.req = std::move(r);
-        srv->queue.pop_front();
-        if (rc != SIC_OK) {
-            a.sim = nullptr;
-            finish(srv, a, rc, srv->now());
-            continue;
-        }
-        a.left = a.req.n_steps;
-        srv->used += a.sim->dbytes;
-        srv->peak = std::max(srv->peak, srv->used);
-        srv->active.push_back(std::move(a));
-        srv->plan_valid = false;
+    if (!srv->cfg.plain) {
+        tick_batched(srv);
+        if (pending)
+            *pending = (int32_t)(srv->queue.size() + srv->active.size() + srv->fresh.size());
+        return SIC_OK;
     }
+    // plain: one request at a time, to completion, refining whenever it holds
+    // for that (Sec. 2.6)
+    admit(srv, srv->stream, srv->active);
     if (!srv->active.empty()) {
         int rc = SIC_OK;
-        bool timed = false;
-        if (srv->cfg.plain) {
-            timed = cudaEventRecord(srv->ev[0], srv->stream) == cudaSuccess;
-            // the whole request, refining whenever it holds for that (Sec. 2.6)
-            Active &a = srv->active.front();
-            while (rc == SIC_OK && a.left > 0) {
-                rc = sic_step(a.sim, std::min(a.left, srv->cfg.chunk_steps));
-                if (rc == SIC_OK)
-                    rc = read_all(srv);
-                if (rc == SIC_OK)
-                    rc = look(srv, a, srv->scal[0]);
-            }
-        } else {
-            int32_t k = srv->cfg.chunk_steps;
-            for (const Active &a : srv->active)
-                k = std::min(k, std::max(a.left, 0));
-            if (k > 0) {
-                if (!srv->plan_valid) {
-                    drop_plans(srv);
-                    std::vector<sic_sim *> grp[2];
-                    for (const Active &a : srv->active)
-                        if (a.left > 0)
-                            grp[a.sim->per_q ? 1 : 0].push_back(a.sim);
-                    for (int g = 0; g < 2 && rc == SIC_OK; ++g)
-                        if (!grp[g].empty() &&
-                            sic_host::build_plan(srv->plan[g], grp[g].data(), (int)grp[g].size(), srv->stream) !=
-                                cudaSuccess)
-                            rc = SIC_ECUDA;
-                    srv->plan_valid = (rc == SIC_OK);
-                }
-                timed = cudaEventRecord(srv->ev[0], srv->stream) == cudaSuccess;
-                for (int32_t st = 0; st < k && rc == SIC_OK; ++st)
-                    for (int g = 0; g < 2 && rc == SIC_OK; ++g)
-                        if (srv->plan[g].mem &&
-                            sic_host::launch(srv->plan[g], sic::MODE_STEP, 1.0f, 1, 1, srv->stream) != cudaSuccess)
-                            rc = SIC_ECUDA;
-            }
+        const bool timed = cudaEventRecord(srv->ev[0], srv->stream) == cudaSuccess;
+        Active &a = srv->active.front();
+        while (rc == SIC_OK && a.left > 0) {
+            rc = sic_step(a.sim, std::min(a.left, srv->cfg.chunk_steps));
+            if (rc == SIC_OK)
+                rc = read_all(srv);
+            if (rc == SIC_OK)
+                rc = look(srv, a, srv->scal[0]);
         }
-        if (timed)
-            timed = cudaEventRecord(srv->ev[1], srv->stream) == cudaSuccess;
+        const bool timed2 = timed && cudaEventRecord(srv->ev[1], srv->stream) == cudaSuccess;
         if (cudaStreamSynchronize(srv->stream) != cudaSuccess && rc == SIC_OK)
             rc = SIC_ECUDA;
         float ms = 0.f;
-        if (timed && cudaEventElapsedTime(&ms, srv->ev[0], srv->ev[1]) == cudaSuccess)
+        if (timed2 && cudaEventElapsedTime(&ms, srv->ev[0], srv->ev[1]) == cudaSuccess)
             srv->busy_s += 1e-3 * ms;
-        // each simulation's own step count (a held one took fewer than the
-        // chunk); one that holds for refinement (Sec. 2.6) is refined here,
-        // its device memory growing, and goes on in the next chunk
-        std::vector<int> status(srv->active.size(), SIC_OK);
-        if (rc == SIC_OK && !srv->cfg.plain) {
-            rc = read_all(srv);
-            if (rc == SIC_OK)
-                for (size_t i = 0; i < srv->active.size(); ++i)
-                    status[i] = look(srv, srv->active[i], srv->scal[i]);
-        }
-        const double t = srv->now();
-        std::vector<Active> keep;
-        for (size_t i = 0; i < srv->active.size(); ++i) {
-            Active &a = srv->active[i];
-            const int st = rc != SIC_OK ? rc : status[i];
-            if (a.left <= 0 || st != SIC_OK)
-                finish(srv, a, st, t);
-            else
-                keep.push_back(std::move(a));
-        }
-        if (keep.size() != srv->active.size())
-            srv->plan_valid = false;
-        srv->active.swap(keep);
-        if (rc != SIC_OK)
-            drop_plans(srv);
+        finish(srv, a, rc, srv->now());
+        srv->active.clear();
     }
     if (pending)
         *pending = (int32_t)(srv->queue.size() + srv->active.size());
@@ -446,7 +551,7 @@ int sic_server_stats(sic_server *srv, sic_server_info *out)
     out->bytes_in_use = (int64_t)srv->used;
     out->bytes_peak = (int64_t)srv->peak;
     out->hbm_budget = srv->cfg.hbm_budget;
-    out->active = (int32_t)srv->active.size();
+    out->active = (int32_t)(srv->active.size() + srv->fresh.size());
     out->queued = (int32_t)srv->queue.size();
     out->completed = srv->completed;
     out->segment_updates = srv->segment_updates;
@@ -463,8 +568,12 @@ void sic_server_destroy(sic_server *srv)
     if (!srv)
         return;
     cudaStreamSynchronize(srv->stream);
+    cudaStreamSynchronize(srv->side);
     drop_plans(srv);
     for (Active &a : srv->active)
+        if (a.sim)
+            sic_destroy(a.sim);
+    for (Active &a : srv->fresh)
         if (a.sim)
             sic_destroy(a.sim);
     for (sic_result &r : srv->done)
@@ -476,6 +585,8 @@ void sic_server_destroy(sic_server *srv)
             cudaEventDestroy(e);
     if (srv->scal)
         cudaFreeHost(srv->scal);
+    cudaStreamSynchronize(srv->side);
+    cudaStreamDestroy(srv->side);
     if (srv->own_stream)
         cudaStreamDestroy(srv->stream);
     delete srv;
