@@ -18,6 +18,9 @@ in log2 (``inputs.serving_mix``, seed 0x5EC5).
   p50/p99 latency.
 * ``e2e``: the batched server fed from host arrays (compact horizontal-sheet
   inputs), every request arriving at t = 0, end to end.
+* ``mid_life``: the same resident batch after every request has run 600 of
+  its own steps (or all of them) alone, refining as it goes: folded,
+  filamented sheets and per-particle charges where refinement split them.
 * ``single_sim``: the two-stream (512 x 16384 = 8,388,608 segments, Nx
   1024) and nonlinear Landau (1024 x 4096, Nx 512) configurations stepped
   alone: graphs of 8 steps with a 256 MB L2 flush before each, and single
@@ -310,6 +313,44 @@ def single_sim(torch, Sim, steps, warmup):
     return out
 
 
+def mid_life(torch, Sim, Batch, probs, presteps, steps, warmup, deposit):
+    """The resident batch after every request has run `presteps` of its own
+    steps (at most its length) alone, refining as its particles pass the
+    refinement length (Sec. 2.6): folded, filamented sheets, more crossings
+    and, for refined requests, per-particle charges (a second launch)."""
+    stream = torch.cuda.Stream()
+    sims = [Sim.from_problem(p, history_len=1, stream=stream.cuda_stream, order=deposit) for p in probs]
+    t0 = time.perf_counter()
+    for sim, p in zip(sims, probs):
+        sim.sic_run(min(presteps, p.n_steps))
+    t_pre = time.perf_counter() - t0
+    batch = Batch(sims)
+    S = batch.sic_batch_segments()
+    for _ in range(warmup):
+        batch.sic_batch_step(1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    steps0 = [s.sic_diagnostics()["step"] for s in sims]
+    for a, b in evs:
+        a.record(stream)
+        batch.sic_batch_step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    done = [s.sic_diagnostics()["step"] - k for s, k in zip(sims, steps0)]
+    segs = [int(s.n_tracers - sum(1 for c in p.closed if not c)) for s, p in zip(sims, probs)]
+    work = sum(n * d for n, d in zip(segs, done))
+    refined = sum(1 for s, p in zip(sims, probs) if s.n_tracers > p.n_tracers)
+    batch.sic_batch_destroy()
+    for s in sims:
+        s.sic_destroy()
+    return {"presteps": presteps, "value": work / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "segments_resident": int(S), "requests_refined": refined,
+            "held_during_timing": sum(1 for d in done if d < steps), "presteps_wall_s": round(t_pre, 1),
+            "note": "every request advanced min(presteps, its length) steps alone first (sic_run, refining); "
+                    "then the same resident batch timed; work counted at each simulation's own steps"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +374,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-single", action="store_true")
+    ap.add_argument("--mid-life", type=int, default=600,
+                    help="also time the resident batch after this many steps of each request (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -519,6 +562,10 @@ def main():
         else:
             line["e2e"] = e2e_single(torch, Sim, probs[0])
     legs["e2e"] = time.perf_counter() - t_leg
+    t_leg = time.perf_counter()
+    if rank == 0 and serving_mode and args.mid_life > 0 and args.presteps == 0:
+        line["mid_life"] = mid_life(torch, Sim, Batch, probs, args.mid_life, args.steps, args.warmup, args.deposit)
+    legs["mid_life"] = time.perf_counter() - t_leg
     t_leg = time.perf_counter()
     if rank == 0 and serving_mode and not args.no_single:
         line["single_sim"] = single_sim(torch, Sim, args.steps, args.warmup)
