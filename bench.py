@@ -22,9 +22,10 @@ in log2 (``inputs.serving_mix``, seed 0x5EC5).
   its own steps (or all of them) alone, refining as it goes: folded,
   filamented sheets and per-particle charges where refinement split them.
 * ``single_sim``: the two-stream (512 x 16384 = 8,388,608 segments, Nx
-  1024) and nonlinear Landau (1024 x 4096, Nx 512) configurations stepped
-  alone: graphs of 8 steps with a 256 MB L2 flush before each, and single
-  steps with a flush before each.
+  1024), nonlinear Landau (1024 x 4096, Nx 512), linear Landau (256 x 1024,
+  Nx 128) and Langmuir (1 x 4096, Nx 64) configurations stepped alone:
+  graphs of 8 steps with a 256 MB L2 flush before each, and single steps
+  with a flush before each.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -271,16 +272,19 @@ def run_reference(args, rank):
 
 
 def single_sim(torch, Sim, steps, warmup):
-    """One simulation alone: the two-stream and the nonlinear Landau
-    configurations.  Two timings each: steps as a user runs them (sic_step of
-    8 steps, one CUDA graph, the L2 flushed before every group of 8), and one
-    step per call with the L2 flushed before every step."""
+    """One simulation alone: the two-stream and nonlinear Landau
+    configurations (the roofline applies), and the linear Landau and Langmuir
+    ones (small: bound by launch and latency, absolute times only).  Two
+    timings each: steps as a user runs them (sic_step of 8 steps, one CUDA
+    graph, the L2 flushed before every group of 8), and one step per call with
+    the L2 flushed before every step."""
     from paper_1506_07207_gb300 import inputs
     peak, _ = peaks()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flush.fill_(1.0)
     out = {}
-    for name, p in (("two_stream", inputs.two_stream_config()), ("landau_nonlinear", inputs.landau_nonlinear())):
+    for name, p in (("two_stream", inputs.two_stream_config()), ("landau_nonlinear", inputs.landau_nonlinear()),
+                    ("landau_linear", inputs.landau_linear()), ("langmuir", inputs.langmuir())):
         stream = torch.cuda.Stream()
         sim = Sim.from_problem(p, history_len=8, stream=stream.cuda_stream)
         for _ in range(max(warmup, 2)):
@@ -306,7 +310,8 @@ def single_sim(torch, Sim, steps, warmup):
         out[name] = {"workload": f"{name.replace('_', ' ')} {p.n_sheets} x {p.n_tracers // p.n_sheets} "
                                  f"({p.n_segments:,} segments), Nx {p.nx}, alone",
                      "value": p.n_segments / g8, "unit": UNIT, "ms_per_step": g8 * 1e3,
-                     "achieved_gbs": gbs, "roofline_frac": gbs / peak,
+                     "achieved_gbs": gbs,
+                     "roofline_frac": gbs / peak if name in ("two_stream", "landau_nonlinear") else None,
                      "ms_per_step_single_launch": one * 1e3,
                      "timing": "sic_step(8) (one graph of 8 steps) after a 256 MB L2 flush, per step; "
                                "single launch: sic_step(1) after a flush"}
