@@ -177,3 +177,20 @@ def test_charge_unit_is_checked(sic):
         sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
                            a["x"], a["v"], a["w"], charge_unit=1e-12)
     assert e.value.code == sic.SIC_ERANGE
+
+
+def test_fourier_mode_is_checked(sic):
+    """mode_k within [0, nx/2], rejected before the GPU is touched; the
+    diagnostic calls reject null handles and unknown fields."""
+    a = _base()
+    for k in (-1, a["nx"] // 2 + 1):
+        with pytest.raises(sic.SicError) as e:
+            sic.Sim.sic_create(a["nx"], a["L"], a["dt"], a["counts"], a["closed"], a["winding"],
+                               a["x"], a["v"], a["w"], mode_k=k)
+        assert e.value.code == sic.SIC_EINVAL, k
+    lib = sic._lib
+    rows = ctypes.c_int32()
+    buf = np.zeros(4)
+    assert lib.sic_mode_history(None, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4,
+                                ctypes.byref(rows)) == sic.SIC_EINVAL
+    assert lib.sic_spectrum(None, 0, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == sic.SIC_EINVAL

@@ -91,3 +91,36 @@ def test_spectrum_matches_oracle(sic, nx):
     # the transform of the device's own field, and the excited mode on top
     np.testing.assert_allclose(s_E, oracle.spectrum(E_gpu), rtol=1e-9, atol=1e-12 * np.abs(E_gpu).sum())
     assert np.argmax(s_rho[1:]) == 0
+
+
+def test_first_order_mode_energy_matches_oracle(sic):
+    p = inputs.two_stream_config(nx=64, n_sheets=16, n_tracers=512, t_end=8.0)
+    n = p.n_steps
+    sim = sic.Sim.from_problem(p, history_len=n, order=4, mode_k=1)
+    try:
+        sim.sic_step(n)
+        wk = sim.sic_mode_history(n)
+    finally:
+        sim.sic_destroy()
+    ref = oracle.run_problem(p, record_E=True, order=4)
+    wk_ref = np.array([oracle.mode_energy(E, p.L, 1) for E in ref["E_hist"][:n]])
+    assert np.abs(wk - wk_ref).max() <= 1e-3 * ref["hist"][:n, 0].max()
+
+
+def test_mode_history_is_the_same_alone_and_in_a_batch(sic):
+    p = _problem()
+    q = inputs.landau(0.1, 0.5, 128, 32, 1024, t_end=5.0)
+    n = 100
+    alone = sic.Sim.from_problem(p, history_len=n, mode_k=2)
+    a2 = sic.Sim.from_problem(p, history_len=n, mode_k=2)
+    other = sic.Sim.from_problem(q, history_len=n, mode_k=1)
+    try:
+        alone.sic_step(n)
+        b = sic.Batch([a2, other])
+        b.sic_batch_step(n)
+        b.sic_batch_destroy()
+        np.testing.assert_array_equal(alone.sic_mode_history(n), a2.sic_mode_history(n))
+        np.testing.assert_array_equal(alone.sic_history(n), a2.sic_history(n))
+    finally:
+        for s in (alone, a2, other):
+            s.sic_destroy()
