@@ -379,10 +379,16 @@ int64_t sic_launch_count(void);
  *
  * A request is a simulation (the arguments of sic_create or
  * sic_create_horizontal) and a step count.  Requests wait in arrival order;
- * each sic_server_tick admits waiting requests while an active slot is free
- * and their device memory fits the budget, advances all active simulations
- * together by up to chunk_steps steps (each step is one kernel launch over all
- * of them), and retires the finished ones.  Results are bit-identical to
+ * the server admits waiting requests while an active slot is free and their
+ * device memory fits the budget, advances all active simulations together by
+ * up to chunk_steps steps (each step is one kernel launch over all of them,
+ * a second one for simulations that carry per-particle charges), and retires
+ * the finished ones.  A request that holds for refinement (Sec. 2.6) is
+ * refined and goes on.  The batched mode overlaps its host work with the
+ * GPU: a tick waits for the chunk launched by the tick before, launches the
+ * next one, and then retires, refines and creates beside it on a second
+ * stream; admitted and refined requests step again from the next tick on.
+ * Results are bit-identical to
  * running each request alone with sic_step.  In plain mode the server runs
  * one request at a time to completion with sic_step, first come first served
  * (the one-simulation-per-launch baseline).  Not thread-safe: one caller
@@ -442,8 +448,11 @@ int sic_server_submit_horizontal(sic_server *srv, const sic_config *cfg, int32_t
                                  const double *x_template_host, const double *v_sheet_host,
                                  const double *w_sheet_host, int32_t n_steps, int32_t keep, int64_t *id);
 
-/* One scheduling round (admit, advance one chunk, retire); blocks until the
- * chunk has run.  *pending (nullable) gets the queued plus active requests. */
+/* One scheduling round.  Batched: collect the chunk launched by the previous
+ * tick (blocking until it has run), launch the next chunk, then retire, refine
+ * and admit while it runs.  Plain: admit one request and run it to completion.
+ * *pending (nullable) gets the queued plus admitted, unfinished requests; the
+ * caller ticks until it is 0. */
 int sic_server_tick(sic_server *srv, int32_t *pending);
 
 /* Move up to max finished requests into out[]; *n gets how many. */
