@@ -316,6 +316,22 @@ int tick_batched(sic_server *srv)
         srv->fresh.clear();
         srv->plan_valid = false;
     }
+    // a request with no steps to take (none asked) is done as it stands
+    {
+        std::vector<Active> keep;
+        for (Active &a : srv->active) {
+            if (a.left <= 0) {
+                retired.push_back(std::move(a));
+                rstatus.push_back(SIC_OK);
+            } else {
+                keep.push_back(std::move(a));
+            }
+        }
+        if (keep.size() != srv->active.size()) {
+            srv->active.swap(keep);
+            srv->plan_valid = false;
+        }
+    }
     // the next chunk: k = min(chunk_steps, steps left of any active request)
     if (!srv->active.empty()) {
         int32_t k = srv->cfg.chunk_steps;

@@ -211,3 +211,36 @@ def test_request_at_its_tracer_limit_ends_with_its_steps(sic):
     srv.sic_server_destroy()
     assert res[rid]["status"] == sic.SIC_ELIMIT and 0 < res[rid]["steps"] < p.n_steps
     assert all(res[i]["status"] == 0 and res[i]["steps"] == q.n_steps for i, q in zip(oids, others))
+
+
+def test_zero_step_and_kept_requests(sic):
+    """In long chunks every request ends at its own length, a request of zero
+    steps is done as it stands, and a kept simulation steps on normally once
+    handed over."""
+    probs = _mix(6, seed=23)
+    srv = sic.Server(hbm_budget=8 << 30, max_active=6, chunk_steps=64)
+    ids = [srv.sic_server_submit_horizontal(p, keep=(i == 0)) for i, p in enumerate(probs)]
+    zero = srv.sic_server_submit_horizontal(probs[1], n_steps=0)
+    got = {}
+    while srv.sic_server_tick() > 0:
+        for r in srv.sic_server_results():
+            got[r["id"]] = r
+    for r in srv.sic_server_results():
+        got[r["id"]] = r
+    srv.sic_server_destroy()
+    assert got[zero]["status"] == 0 and got[zero]["steps"] == 0 and got[zero]["segment_updates"] == 0
+    for rid, p in zip(ids, probs):
+        r = got[rid]
+        assert r["status"] == 0 and r["steps"] == p.n_steps
+        assert (r["field_energy"], r["kinetic_energy"], r["momentum"], r["charge_fixed"]) == _key(_alone(sic, p))
+    kept = sic.adopt_sim(got[ids[0]]["sim"], probs[0].nx, probs[0].counts)
+    ref = sic.Sim.from_problem(probs[0], history_len=1)
+    try:
+        kept.sic_step(5)
+        ref.sic_step(probs[0].n_steps + 5)
+        # (both hold at the same step if a particle passes the refinement length)
+        assert kept.sic_diagnostics()["step"] == ref.sic_diagnostics()["step"] > probs[0].n_steps
+        assert _key(kept.sic_diagnostics()) == _key(ref.sic_diagnostics())
+    finally:
+        kept.sic_destroy()
+        ref.sic_destroy()
