@@ -155,22 +155,24 @@ __device__ __forceinline__ float span_to_float(long long span)
     return __fmaf_rn(__int2float_rn((int)(span >> 32)), 4294967296.0f, __uint2float_rn(frac_of(span)));
 }
 
-// n whole cells starting at cell js (mod nx) each receive p units
-__device__ __noinline__ void range_add(int js, long long n, long long p, int nx, unsigned long long *diff,
-                                       int *diff_used)
+// n whole cells starting at cell js (mod nx) each receive p units: +p at js
+// and -p after the range in the block's difference array (two's complement
+// in the same 32-bit lo/hi form as the mesh, so the adds are native shared
+// atomics), summed into the mesh when the block leaves the simulation
+__device__ __noinline__ void range_add(int js, long long n, long long p, int nx, const Hist &dh, int *diff_used)
 {
     const long long full = n / nx;
     const int rem = (int)(n - full * nx);
     if (full)
-        atomicAdd(diff, (unsigned long long)(full * p));
+        dh.add(0, full * p);
     if (rem) {
         const int e = js + rem;
-        atomicAdd(diff + js, (unsigned long long)p);
+        dh.add(js, p);
         if (e <= nx) {
-            atomicAdd(diff + e, (unsigned long long)(-p));
+            dh.add(e, -p);
         } else {
-            atomicAdd(diff, (unsigned long long)p);
-            atomicAdd(diff + (e - nx), (unsigned long long)(-p));
+            dh.add(0, p);
+            dh.add(e - nx, -p);
         }
     }
     *diff_used = 1;
@@ -192,7 +194,7 @@ struct DirectAdd {
 
 template <class ACC>
 __device__ __forceinline__ void emit_cross(long long ua, int ja, long long ub, int jb, int q, int nx, ACC &acc,
-                                           unsigned long long *diff, int *diff_used, unsigned &maxseg)
+                                           const Hist &diff, int *diff_used, unsigned &maxseg)
 {
     if (ub < ua) {
         const long long t = ua;
@@ -256,7 +258,7 @@ __device__ __forceinline__ int wrap_near(int c, int nx)
 
 template <class ACC>
 __device__ __forceinline__ void emit_first(long long ua, long long ub, int q, int nx, ACC &acc,
-                                           unsigned long long *diff, int *diff_used, unsigned &maxseg)
+                                           const Hist &diff, int *diff_used, unsigned &maxseg)
 {
     if (ub < ua) {
         const long long t = ua;
@@ -957,14 +959,14 @@ __device__ void field_epilogue(const SimDev &S, int record, unsigned long long *
 }
 
 // inclusive prefix sum of diff[0..nx) added into hist (block-wide)
-__device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int nx, Shared &sh)
+__device__ void add_diff_prefix(const Hist &hist, const Hist &diff, int nx, Shared &sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (nx + B - 1) / B;
     const int j0 = min(tid * per, nx), j1 = min(j0 + per, nx);
     long long lsum = 0;
     for (int j = j0; j < j1; ++j)
-        lsum += (long long)diff[j];
+        lsum += (long long)diff.get(j);
     long long incl = lsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -979,7 +981,7 @@ __device__ void add_diff_prefix(const Hist &hist, unsigned long long *diff, int 
     for (int w = 0; w < warp; ++w)
         run += sh.w64[w];
     for (int j = j0; j < j1; ++j) {
-        run += (long long)diff[j];
+        run += (long long)diff.get(j);
         hist.set(j, hist.get(j) + (unsigned long long)run);
     }
     __syncthreads();
@@ -993,7 +995,7 @@ template <bool PUSH, bool DEPOSIT, bool PER_Q, bool FULL, bool STAGED, bool GEN,
 __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__restrict__ Uin,
                                         const float *__restrict__ Vin, unsigned *__restrict__ Uout,
                                         float *__restrict__ Vout, const int32_t *__restrict__ Qh,
-                                        const float2 *ek, const Hist &hist, unsigned long long *diff,
+                                        const float2 *ek, const Hist &hist, const Hist &diff,
                                         Shared &sh, int nx, float ks, int drift, unsigned &rerr,
                                         char *st, unsigned short *tasks, long long &ake, long long &ap, unsigned &mseg,
                                         const WorkItemPL *pw, int dep, int segq, bool track_all, const MID &mid)
@@ -1516,8 +1518,10 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
     Hist hist;
     hist.lo = reinterpret_cast<unsigned *>(mesh_region);
     hist.hi = hist.lo + nx_max;
-    unsigned long long *diff = mesh_region + nx_max;  // nx_max + 2 entries
-    float2 *ek = reinterpret_cast<float2 *>(diff + nx_max + 2);
+    Hist diff;  // the difference array of long particles: nx_max + 2 cells
+    diff.lo = reinterpret_cast<unsigned *>(mesh_region + nx_max);
+    diff.hi = diff.lo + nx_max + 2;
+    float2 *ek = reinterpret_cast<float2 *>(mesh_region + nx_max + nx_max + 2);
     char *stage_base = reinterpret_cast<char *>(smem) + stage_offset(nx_max);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1573,8 +1577,10 @@ __global__ void __launch_bounds__(B, SIC_K1_MIN_BLOCKS) k_step(const LaunchArgs 
                 hist.lo[j] = 0u;
                 hist.hi[j] = 0u;
             }
-            for (int j = tid; j < nx + 2; j += B)
-                diff[j] = 0ull;
+            for (int j = tid; j < nx + 2; j += B) {
+                diff.lo[j] = 0u;
+                diff.hi[j] = 0u;
+            }
         }
         if (tid == 0) {
             sh.diff_used = 0;
