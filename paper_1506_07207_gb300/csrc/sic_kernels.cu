@@ -155,13 +155,41 @@ __device__ __forceinline__ float span_to_float(long long span)
     return __fmaf_rn(__int2float_rn((int)(span >> 32)), 4294967296.0f, __uint2float_rn(frac_of(span)));
 }
 
+// floor(q 2^32 / span) for 0 <= q <= 2^28 and 2^32 < span < 2^46 (a particle
+// that crosses two or more cell edges): the whole-cell charge of a box
+// particle.  The float estimate (relative error below 2^-20, so within 256
+// of the quotient) is corrected once with the exact remainder and then by
+// at most two steps each way; the result is the exact integer floor, with
+// no 64-bit integer division.
+__device__ __forceinline__ long long div_q32(int q, long long span)
+{
+    const long long num = (long long)q << 32;
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(span_to_float(span)));
+    long long P = __float2ll_rz(__fmul_rn(__fmul_rn(__int2float_rn(q), 4294967296.0f), inv));
+    long long r = num - P * span;
+    P += __float2ll_rn(__fmul_rn(__ll2float_rn(r), inv));
+    r = num - P * span;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (r < 0) {
+            P -= 1;
+            r += span;
+        } else if (r >= span) {
+            P += 1;
+            r -= span;
+        }
+    }
+    return P;
+}
+
 // n whole cells starting at cell js (mod nx) each receive p units: +p at js
 // and -p after the range in the block's difference array (two's complement
 // in the same 32-bit lo/hi form as the mesh, so the adds are native shared
 // atomics), summed into the mesh when the block leaves the simulation
 __device__ __noinline__ void range_add(int js, long long n, long long p, int nx, const Hist &dh, int *diff_used)
 {
-    const long long full = n / nx;
+    const long long full = n < nx ? 0 : n / nx;  // 0 or 1 for a particle shorter than 1.5 box lengths
     const int rem = (int)(n - full * nx);
     if (full)
         dh.add(0, full * p);
@@ -221,7 +249,7 @@ __device__ __forceinline__ void emit_cross(long long ua, int ja, long long ub, i
         return;
     }
     const long long nint = ncut - 1;
-    const long long P = span > 0 ? (long long)(((unsigned long long)q << 32) / (unsigned long long)span) : 0;
+    const long long P = div_q32(q, span);  // span > 2^32: two or more edges
     const long long inner = nint * P;
     if ((long long)F > (long long)q - inner)
         F = (int)((long long)q - inner);
@@ -284,7 +312,7 @@ __device__ __forceinline__ void emit_first(long long ua, long long ub, int q, in
     long long F = __float2int_rn(__fmul_rn(__fmul_rn(df, inv), __int2float_rn(q)));
     F = min(max(F, 0ll), (long long)q);
     const long long nint = ncut - 1;
-    const long long P = nint > 0 ? (long long)(((unsigned long long)q << 32) / (unsigned long long)span) : 0;
+    const long long P = nint > 0 ? div_q32(q, span) : 0;
     const long long inner = nint * P;
     if (F > (long long)q - inner)
         F = (long long)q - inner;
