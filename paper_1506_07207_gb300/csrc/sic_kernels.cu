@@ -1455,11 +1455,12 @@ __device__ __forceinline__ void do_item(const WorkItem &W, const unsigned *__res
         }
         if (total) {
             int pos = excl;
-            while (cross) {
-                const int r = __ffs(cross) - 1;
-                tasks[pos++] = (unsigned short)(l0 + r);
-                cross &= cross - 1u;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {  // predicated stores, no loop to diverge on
+                if ((cross >> r) & 1u)
+                    tasks[pos++] = (unsigned short)(l0 + r);
             }
+            cross = 0;
             __syncwarp();
             DirectAdd acc{hist};
             // piecewise-linear particles: kappa of the particle at idx, from
