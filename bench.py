@@ -21,6 +21,9 @@ in log2 (``inputs.serving_mix``, seed 0x5EC5).
 * ``mid_life``: the same resident batch after every request has run 600 of
   its own steps (or all of them) alone, refining as it goes: folded,
   filamented sheets and per-particle charges where refinement split them.
+* ``late_states``: nonlinear Landau at t = 50 and two-stream at t = 60,
+  refined as they stretch: folded sheets, most particles crossing cell
+  edges (``--profile-case`` runs only the ncu case of these).
 * ``single_sim``: the two-stream (512 x 16384 = 8,388,608 segments, Nx
   1024), nonlinear Landau (1024 x 4096, Nx 512), linear Landau (256 x 1024,
   Nx 128) and Langmuir (1 x 4096, Nx 64) configurations stepped alone:
@@ -356,6 +359,65 @@ def mid_life(torch, Sim, Batch, probs, presteps, steps, warmup, deposit):
                     "then the same resident batch timed; work counted at each simulation's own steps"}
 
 
+def late_problem(name):
+    """A late, folded state: nonlinear Landau run to t = 50 or two-stream to
+    t = 60, refining at half a box (splitting to a quarter)."""
+    from paper_1506_07207_gb300 import inputs
+    p = inputs.landau_nonlinear() if name == "landau_nonlinear" else inputs.two_stream_config()
+    p.refine_length = 0.5 * p.L
+    p.refine_split = 0.25 * p.L
+    return p, (1000 if name == "landau_nonlinear" else 1200)
+
+
+def late_states(torch, Sim, groups=4):
+    """Step time of late states (folded sheets: most particles cross cell
+    edges), stepped as a user runs them (sic_run of 8 steps, refining when a
+    particle passes the refinement length), the L2 flushed before each group."""
+    peak, _ = peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name in ("landau_nonlinear", "two_stream"):
+        p, pre = late_problem(name)
+        stream = torch.cuda.Stream()
+        sim = Sim.from_problem(p, history_len=8, stream=stream.cuda_stream)
+        sim.sic_run(pre)
+        sim.sic_run(1)
+        ev = []
+        for _ in range(groups):
+            with torch.cuda.stream(stream):
+                flush.sum()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.sic_run(8)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        s = statistics.median(a.elapsed_time(b) for a, b in ev) / 1e3 / 8
+        segs = sim.n_tracers
+        t = sim.sic_diagnostics()["t"]
+        sim.sic_destroy()
+        out[name] = {"t": t, "segments": segs, "value": segs / s, "unit": UNIT, "ms_per_step": s * 1e3,
+                     "roofline_frac": ALGO_BYTES_TRACER_CHARGE * segs / s / 1e9 / peak,
+                     "timing": "sic_run(8) after a 256 MB L2 flush, per step (refinements included)"}
+    return out
+
+
+def profile_case(torch, Sim, name):
+    """The case of the late-state ncu capture: the state of late_states, then
+    two steps inside an NVTX range named "late"."""
+    p, pre = late_problem(name)
+    sim = Sim.from_problem(p, history_len=8)
+    sim.sic_run(pre)
+    sim.sic_run(1)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("late")
+    sim.sic_step(2)
+    sim.sic_sync()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_case": name, "step": sim.sic_diagnostics()["step"], "tracers": sim.n_tracers}))
+    sim.sic_destroy()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,6 +441,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-single", action="store_true")
+    ap.add_argument("--no-late", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=["landau_nonlinear", "two_stream"],
+                    help="only run the late-state case profiled with ncu (two steps in an NVTX range)")
     ap.add_argument("--mid-life", type=int, default=600,
                     help="also time the resident batch after this many steps of each request (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -404,6 +469,12 @@ def main():
         dist.barrier()
     from paper_1506_07207_gb300 import inputs, ranks, serving
     from paper_1506_07207_gb300.sic import Batch, Sim, sic_launch_count
+    if args.profile_case:
+        if rank == 0:
+            profile_case(torch, Sim, args.profile_case)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
 
     legs = {}
     t_leg = time.perf_counter()
@@ -575,6 +646,10 @@ def main():
     if rank == 0 and serving_mode and not args.no_single:
         line["single_sim"] = single_sim(torch, Sim, args.steps, args.warmup)
     legs["single_sim"] = time.perf_counter() - t_leg
+    t_leg = time.perf_counter()
+    if rank == 0 and serving_mode and not args.no_late:
+        line["late_states"] = late_states(torch, Sim)
+    legs["late_states"] = time.perf_counter() - t_leg
     t_leg = time.perf_counter()
     if rank == 0 and not args.no_cpu_baseline:
         v, upd, el = oracle_rate(probs)
