@@ -269,8 +269,9 @@ int tick_batched(sic_server *srv)
         if (cudaEventElapsedTime(&ms, srv->ev[0], srv->ev[1]) == cudaSuccess)
             srv->busy_s += 1e-3 * ms;
         // each simulation's own step count (a held one took fewer than the
-        // chunk); one that holds for refinement (Sec. 2.6) is refined here,
-        // its device memory growing, and goes on in the next chunk
+        // chunk); one that holds for refinement (Sec. 2.6) sits out the next
+        // chunk, is refined beside it (its device memory growing) and steps
+        // again from the tick after
         std::vector<int> status(srv->active.size(), SIC_OK);
         std::vector<char> held(srv->active.size(), 0);
         if (rc == SIC_OK) {
